@@ -1,0 +1,117 @@
+"""Pins of the oracle's column model (Sec. VI-A): complex-step derivatives,
+the column's mass balance, closed forms of the equilibrium curve, sizes."""
+import numpy as np
+import pytest
+
+from gen.tray import TrayParams, kkt_point
+from oracle import tray
+
+EPS = 1e-30
+
+
+def _dense_jac(p, w):
+    r, c, v = tray.jacobian_coo(p, w)
+    J = np.zeros((p.m, p.n))
+    np.add.at(J, (r, c), v)
+    return J
+
+
+def _dense_sym_lower(n, colptr, rowind, val):
+    A = np.zeros((n, n))
+    for j in range(n):
+        for q in range(colptr[j], colptr[j + 1]):
+            A[rowind[q], j] += val[q]
+            if rowind[q] != j:
+                A[j, rowind[q]] += val[q]
+    return A
+
+
+@pytest.mark.parametrize("k,T", [(4, 2), (32, 2), (6, 3)])
+def test_jacobian_complex_step(k, T):
+    p = TrayParams(k=k, T=T)
+    pt = kkt_point(p, seed=3)
+    J = _dense_jac(p, pt.w)
+    for j in range(p.n):
+        wc = pt.w.astype(complex)
+        wc[j] += 1j * EPS
+        col = tray.constraints(p, wc).imag / EPS
+        assert np.allclose(J[:, j], col, rtol=1e-13, atol=1e-13), j
+
+
+@pytest.mark.parametrize("k,T", [(4, 2), (32, 1), (6, 3)])
+def test_hessian_complex_step(k, T):
+    p = TrayParams(k=k, T=T)
+    pt = kkt_point(p, seed=5)
+    W = _dense_sym_lower(p.n, *tray.hessian_lower_csc(p, pt.w, pt.lam, 0.7))
+    for j in range(p.n):
+        wc = pt.w.astype(complex)
+        wc[j] += 1j * EPS
+        col = tray.lagrangian_grad(p, wc, pt.lam, 0.7).imag / EPS
+        assert np.allclose(W[:, j], col, rtol=1e-12, atol=1e-12), j
+
+
+def test_gradient_complex_step():
+    p = TrayParams(k=5, T=3)
+    pt = kkt_point(p, seed=1)
+    g = tray.objective_grad(p, pt.w)
+    for j in range(p.n):
+        wc = pt.w.astype(complex)
+        wc[j] += 1j * EPS
+        assert abs(tray.objective(p, wc).imag / EPS - g[j]) < 1e-13
+
+
+def test_mass_balance_closed_form():
+    """sum_n M_n xdot_n = F x_f - D x_1 - (F - D) x_k for any state."""
+    p = TrayParams(k=32, T=7)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0, 1, (8, 32))
+    y = rng.uniform(0, 1, (8, 32))
+    u = rng.uniform(1, 5, 8)
+    assert np.max(np.abs(tray.mass_balance_residual(p, x, y, u))) < 1e-14
+
+
+def test_balance_against_hand_values():
+    """Three trays written out by hand: condenser, feed, reboiler."""
+    p = TrayParams(k=4, T=0)          # feed tray is index 2
+    x = np.array([[0.9, 0.7, 0.5, 0.2]])
+    y = np.array([[0.95, 0.8, 0.6, 0.3]])
+    u = np.array([2.0])
+    L, V, S = 0.4, 0.6, 0.8
+    g = tray.balance(p, x, y, u)[0]
+    assert np.isclose(g[0], V * (0.8 - 0.9))
+    assert np.isclose(g[1], L * (0.9 - 0.7) - V * (0.8 - 0.6))
+    assert np.isclose(g[2], 0.4 * 0.5 + L * 0.7 - S * 0.5 - V * (0.6 - 0.3))
+    assert np.isclose(g[3], S * 0.5 - (0.4 - 0.2) * 0.2 - V * 0.3)
+
+
+def test_equilibrium_closed_forms():
+    p = TrayParams()
+    assert tray.vle(p, 0.0) == 0.0 and tray.vle(p, 1.0) == 1.0
+    assert np.isclose(tray.vle_d1(p, 0.0), p.alpha)
+    assert np.isclose(tray.vle_d1(p, 1.0), 1.0 / p.alpha)
+    xs = np.linspace(0.01, 0.99, 50)
+    assert np.all(tray.vle(p, xs) > xs)          # alpha > 1 enriches vapour
+
+
+def test_sizes_and_pattern():
+    p = TrayParams(k=32, T=50)
+    assert p.n == 3315 and p.m == 3264
+    pt = kkt_point(p, 0)
+    rowptr, colind, _ = tray.jacobian_csr(p, pt.w)
+    assert len(colind) == 32 + 64 * 51 + 50 * (4 + 30 * 6 + 5)
+    for r in range(p.m):
+        cols = colind[rowptr[r]:rowptr[r + 1]]
+        assert np.all(np.diff(cols) > 0)
+    colptr, rowind, _ = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    assert colptr[-1] == (4 * 32 + 1) * 51
+    for j in range(p.n):
+        rows = rowind[colptr[j]:colptr[j + 1]]
+        assert rows[0] == j and np.all(np.diff(rows) > 0)
+
+
+def test_table1_structure_is_a_different_variant():
+    """Table I of the paper has n = 67(N+1) (flows kept as variables); this
+    model substitutes L, V, S and has 65 variables per stage, so the
+    paper's nnz column does not apply: structure parity is unpinned."""
+    p = TrayParams(k=32, T=100)
+    assert p.n == 65 * 101 and p.n != 6767

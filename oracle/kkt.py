@@ -28,6 +28,10 @@ Eq. problemrelaxation).  Callers pass r = -F_mu.
   r_gamma = r_x + gamma J^T r_y.  The signs follow from the convention above
   (the printed right-hand side of the recovery step is garbled).
 
+Refinement stops at eta <= tol, after max_refine sweeps, or when eta fails
+to drop below 0.9 times its previous value twice in a row (stagnation; the
+paper only names Richardson iterations, Sec. V-B).
+
 Backward error (Rigal-Gaches, normwise):
     eta = ||b - K_orig v||_inf / (||K_orig||_inf ||v||_inf + ||b||_inf).
 
@@ -178,7 +182,7 @@ def _richardson(precond, K, knorm, b, tol, max_refine, n, info=None):
         info.refine_iters = it
         if eta <= tol:
             break
-        if len(etas) >= 2 and eta > 0.5 * etas[-2]:
+        if len(etas) >= 2 and eta > 0.9 * etas[-2]:
             slow += 1
             if slow >= 2:
                 info.status = "stall"

@@ -1,0 +1,239 @@
+/*
+ * kkt.h -- C ABI of the GB300 KKT library.
+ *
+ * The library computes the Newton (KKT) step of a primal-dual interior-point
+ * method on a dynamic nonlinear program with the two hybrid sparse solvers of
+ * Pacaud & Shin, "GPU-accelerated dynamic nonlinear optimization with
+ * ExaModels and MadNLP" (arXiv 2403.15913):
+ *
+ *   Lifted-KKT (Sec. IV-A, Eq. liftedkkt): Cholesky of the condensed matrix
+ *       K_D = W + Sigma_x + delta_x I + J^T diag(D) J, then Richardson
+ *       refinement on the original system (Sec. V-B);
+ *   HyKKT (Sec. IV-B, Eq. hykkt, Eq. schurcomp): Cholesky of
+ *       K_gamma = W + Sigma_x + delta_x I + gamma J^T J and conjugate
+ *       gradients on S_gamma = J K_gamma^{-1} J^T.
+ *
+ * Every solve returns the solution of
+ *
+ *     [ W + Sigma_x + delta_x I    J^T ] [dx]   [r_x]
+ *     [ J                          -C  ] [dy] = [r_y]          (K_orig)
+ *
+ * i.e. the condensed system Eq. (kkt:condensed) with the variable-bound
+ * barrier terms folded into Sigma_x; C = 0 for the equality-constrained
+ * system and C = D^{-1} for the relaxed problem of Eq. (problemrelaxation).
+ * Callers pass r = -F_mu (Eq. newtonstep).
+ *
+ * Conventions for every function below:
+ *  - Pointers named d_* are DEVICE memory (current CUDA device); all others
+ *    are HOST memory.  The caller owns every buffer it passes; the library
+ *    owns the context and all of its workspace.
+ *  - Integer arrays are int32, floating-point arrays float64 (FP64).
+ *  - Work is enqueued on the given stream; functions that return a value the
+ *    host needs (status, step info) synchronise that stream before returning.
+ *    One context is used by one stream at a time.
+ *  - Functions return a kkt_status; they never abort the process and never
+ *    trap on the device.  kkt_last_error() gives a message for the last error
+ *    of a context.
+ */
+#ifndef KKT_GB300_H
+#define KKT_GB300_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KKT_OK = 0,
+    KKT_ERR_ARG = -1,       /* invalid argument (sizes, NULL, bad pattern)    */
+    KKT_ERR_OOM = -2,       /* device allocation failed                      */
+    KKT_ERR_CUDA = -3,      /* a CUDA runtime call failed                     */
+    KKT_ERR_NOT_SPD = -4,   /* non-positive pivot: kkt_info.failed_col is set */
+    KKT_ERR_MAXIT = -5,     /* CG or refinement hit its iteration limit       */
+    KKT_ERR_STALL = -6,     /* refinement stopped improving (eta stagnated)   */
+    KKT_ERR_TIMEOUT = -7,   /* a bounded device wait gave up                  */
+    KKT_ERR_STATE = -8,     /* call out of order (e.g. solve before factor)   */
+    KKT_ERR_INTERNAL = -9   /* a device-side index check failed               */
+} kkt_status;
+
+typedef enum { KKT_LIFTED = 0, KKT_HYKKT = 1 } kkt_scheme;
+
+typedef struct kkt_ctx kkt_ctx;
+
+/* Options.  Fill with kkt_default_options() and change what you need. */
+typedef struct {
+    int scheme;          /* KKT_LIFTED or KKT_HYKKT                            */
+    /* symbolic analysis (pinned nested dissection, Sec. V-B) */
+    int leaf_size;       /* ND components this small are ordered by minimum
+                            degree (default 64)                               */
+    int relax_cols;      /* relaxed amalgamation: max merged width (48);
+                            0 keeps fundamental supernodes                    */
+    int relax_zeros;     /* max explicit zeros in a merged panel (1024)       */
+    int max_width;       /* supernodes wider than this are cut (64);
+                            0 or anything above 4096 means 4096               */
+    /* numerics */
+    double delta;        /* Lifted-KKT: D = 1/delta when factor gets D = NULL
+                            (default 1e-8)                                    */
+    double gamma;        /* HyKKT gamma (default 1e4; the paper uses 1e7)     */
+    double tol_refine;   /* stop refinement at eta <= tol_refine (1e-10)      */
+    double tol_cg;       /* CG stops at ||res||_2 <= tol_cg ||rhs||_2 (1e-10) */
+    int max_refine;      /* refinement sweeps after the first solve (20)      */
+    int max_cg;          /* CG iterations per inner solve (200)               */
+    int target_relaxed;  /* 0: refine against C = 0 (Eq. kkt:condensed);
+                            1: against C = D^{-1} (relaxed problem, Lifted
+                            only)                                             */
+} kkt_options;
+
+/* Per-call report.  Fields not touched by a call keep their values. */
+typedef struct {
+    int refine_iters;    /* refinement sweeps after the first inner solve     */
+    int cg_iters;        /* total CG iterations of the last solve (HyKKT)     */
+    int failed_col;      /* first column (permuted order) with a non-positive
+                            pivot in the last factor, -1 if none              */
+    int status_detail;   /* reserved                                           */
+    double bwd_err;      /* eta = ||b - K_orig v||_inf /
+                                  (||K_orig||_inf ||v||_inf + ||b||_inf)      */
+    double delta_x;      /* delta_x used by the last factor                    */
+} kkt_info;
+
+void kkt_default_options(kkt_options* opt);
+
+/* Symbolic analysis (Sec. V-B: done once, the pattern of K is fixed across
+ * IPM iterations).  n variables, m constraints.
+ *   W_colptr[n+1], W_rowind[nnzW]: pattern of the LOWER triangle of the
+ *       Hessian W, CSC, row indices >= column index (diagonal optional);
+ *   J_rowptr[m+1], J_colind[nnzJ]: pattern of the Jacobian J (m x n), CSR.
+ * Value arrays passed to kkt_factor follow exactly these entry orders.
+ * On success *out receives a new context (free with kkt_destroy).
+ * Errors: KKT_ERR_ARG on out-of-range or upper-triangular indices,
+ * KKT_ERR_OOM / KKT_ERR_CUDA on device failures. */
+kkt_status kkt_analyse(int n, int m,
+                       const int* W_colptr, const int* W_rowind,
+                       const int* J_rowptr, const int* J_colind,
+                       const kkt_options* opt, kkt_ctx** out);
+
+/* Same analysis, host only: no device memory is touched, so it runs on a
+ * machine without a GPU.  The context serves kkt_symbolic_sizes and
+ * kkt_symbolic_export; kkt_factor on it returns KKT_ERR_STATE. */
+kkt_status kkt_analyse_host(int n, int m,
+                            const int* W_colptr, const int* W_rowind,
+                            const int* J_rowptr, const int* J_colind,
+                            const kkt_options* opt, kkt_ctx** out);
+
+/* Sizes of the symbolic result: supernodes, nonzeros of L, stored panel
+ * entries (nnz(L) plus explicit zeros of relaxed supernodes), total row
+ * indices over supernodes, levels of the supernodal elimination tree, and
+ * the factorisation flop count sum_j cc_j^2 of the exact structure. */
+kkt_status kkt_symbolic_sizes(const kkt_ctx* ctx, int* ns, int64_t* nnz_L,
+                              int64_t* panel_entries, int64_t* row_entries,
+                              int* levels, double* flops);
+
+/* Copy out the symbolic analysis (host arrays, caller-allocated):
+ * perm[n] (new -> old), parent[n] (etree of P K P^T, -1 for roots),
+ * colcount[n], sn_ptr[ns+1], sn_rowptr[ns+1], sn_rows[row_entries]
+ * (supernode row structures in permuted labels).  Any pointer may be NULL. */
+kkt_status kkt_symbolic_export(const kkt_ctx* ctx, int* perm, int* parent,
+                               int* colcount, int* sn_ptr, int* sn_rowptr,
+                               int* sn_rows);
+
+/* Numeric factorisation (refactorisation of Sec. V-B).
+ *   d_Wval[nnzW]  W values in the kkt_analyse order;
+ *   d_Jval[nnzJ]  J values in the kkt_analyse order;
+ *   d_sigma[n]    Sigma_x (barrier diagonal of the variable bounds);
+ *   d_D[m]        Lifted-KKT: the diagonal D (NULL means 1/delta);
+ *                 HyKKT: must be NULL (D = gamma);
+ *   delta_x       primal regularisation (inertia correction, Sec. III-B).
+ * The library copies the values it needs (the residuals of later kkt_solve
+ * calls use them), so the caller may reuse or free its buffers as soon as
+ * the call returns.
+ * Returns KKT_ERR_NOT_SPD with info->failed_col set when a pivot is not
+ * positive (the caller raises delta_x and calls again). */
+kkt_status kkt_factor(kkt_ctx* ctx, const double* d_Wval, const double* d_Jval,
+                      const double* d_sigma, const double* d_D, double delta_x,
+                      cudaStream_t stream, kkt_info* info);
+
+/* Solve K_orig [dx; dy] = [r_x; r_y] with the factor of the last
+ * kkt_factor (scheme per options), refining until eta <= tol_refine.
+ *   d_rx[n], d_ry[m] in; d_dx[n], d_dy[m] out;
+ *   d_ds[m] (may be NULL): relaxed target only, ds = J dx - r_y.
+ * Returns KKT_ERR_MAXIT / KKT_ERR_STALL when the tolerance is not reached
+ * (the best iterate is still written) and KKT_ERR_STATE without a factor. */
+kkt_status kkt_solve(kkt_ctx* ctx, const double* d_rx, const double* d_ry,
+                     double* d_dx, double* d_dy, double* d_ds,
+                     cudaStream_t stream, kkt_info* info);
+
+/* Backsolve with the condensed matrix of the last successful kkt_factor
+ * (the SOLVE column of Table I): d_x[n] = K^{-1} d_b[n], original ordering.
+ * d_b and d_x may alias.  KKT_ERR_STATE without a factor. */
+kkt_status kkt_backsolve(kkt_ctx* ctx, const double* d_b, double* d_x,
+                         cudaStream_t stream);
+
+/* Diagnostic: copy the numeric factor L (permuted order) as CSC with the
+ * panel structure: colptr[n+1], rowind[], val[] sized by the panel entries
+ * below and on the diagonal (lower trapezoid of each supernode panel). */
+kkt_status kkt_factor_export(kkt_ctx* ctx, int64_t* colptr, int* rowind,
+                             double* val);
+
+/* Message of the last error of ctx; with ctx == NULL, of the last call on
+ * this thread that failed before a context existed (e.g. kkt_analyse). */
+const char* kkt_last_error(const kkt_ctx* ctx);
+
+/* Tracing (Table I/II of the paper split the time into symbolic analysis,
+ * refactorisation and backsolve).  With profiling on, CUDA events recorded
+ * on the caller's stream bracket the phases and their device times are
+ * accumulated at the synchronisation that ends each call; the launch
+ * counters are kept always. */
+typedef struct {
+    double assemble_ms;      /* assembly of the condensed matrix          */
+    double factor_ms;        /* supernodal numeric factorisation         */
+    double solve_ms;         /* triangular solves (forward + backward)   */
+    double other_ms;         /* residuals, CG vector work, J/J^T products */
+    int64_t launches;        /* kernels launched by this context          */
+    int64_t factor_launches; /* of which numeric-factorisation kernels    */
+    int64_t factor_calls;    /* kkt_factor calls                          */
+    int64_t kinv_calls;      /* applications of K^{-1} (pairs of solves)  */
+} kkt_stats;
+
+kkt_status kkt_set_profiling(kkt_ctx* ctx, int enable);
+kkt_status kkt_get_stats(const kkt_ctx* ctx, kkt_stats* out);
+kkt_status kkt_reset_stats(kkt_ctx* ctx);
+void kkt_destroy(kkt_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Distillation-column model (Sec. VI-A), per-stage evaluation kernels.
+ * params[16] (host): k, T, h, alpha, D, F, x_f, M, xbar, ubar, rho, xbar_0,
+ * x_lo, x_hi, u_lo, u_hi.  Variables are stage-major
+ * [x_1..x_k, y_1..y_k, u] per stage t = 0..T; constraints per stage are the
+ * initial condition (t = 0) or implicit-Euler dynamics (t >= 1), then the
+ * vapour-liquid equilibrium.
+ * ---------------------------------------------------------------------- */
+
+/* n = (2k+1)(T+1), m = 2k(T+1) and the pattern sizes. */
+kkt_status kkt_tray_sizes(const double* params, int* n, int* m, int* nnzW,
+                          int* nnzJ);
+
+/* Host patterns in the order the evaluation kernels write values:
+ * lower-CSC of W (every diagonal plus (u_t, x_it), (u_t, y_it)) and CSR of J
+ * (columns ascending).  Arrays sized by kkt_tray_sizes. */
+kkt_status kkt_tray_pattern(const double* params, int* W_colptr, int* W_rowind,
+                            int* J_rowptr, int* J_colind);
+
+/* Device evaluation at the primal point d_w[n] with multipliers d_lam[m]:
+ *   d_f[1]        objective (NULL to skip)
+ *   d_grad[n]     gradient of the objective (NULL to skip)
+ *   d_c[m]        constraint values (NULL to skip)
+ *   d_Jval[nnzJ]  Jacobian values (NULL to skip)
+ *   d_Wval[nnzW]  Hessian of obj_weight * f + lam^T c, lower (NULL to skip;
+ *                 d_lam may be NULL only when this is NULL)
+ * Asynchronous on stream. */
+kkt_status kkt_tray_eval(const double* params, const double* d_w,
+                         const double* d_lam, double obj_weight, double* d_f,
+                         double* d_grad, double* d_c, double* d_Jval,
+                         double* d_Wval, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

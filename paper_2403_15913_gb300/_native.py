@@ -1,0 +1,129 @@
+"""ctypes declarations of the C ABI in include/kkt.h (argument marshalling
+only).  Loading fails loudly when the in-tree CUDA library is missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkkt_gb300.so")
+
+KKT_OK = 0
+KKT_ERR_ARG = -1
+KKT_ERR_OOM = -2
+KKT_ERR_CUDA = -3
+KKT_ERR_NOT_SPD = -4
+KKT_ERR_MAXIT = -5
+KKT_ERR_STALL = -6
+KKT_ERR_TIMEOUT = -7
+KKT_ERR_STATE = -8
+KKT_ERR_INTERNAL = -9
+STATUS_NAMES = {0: "ok", -1: "arg", -2: "oom", -3: "cuda", -4: "not_spd", -5: "maxit",
+                -6: "stall", -7: "timeout", -8: "state", -9: "internal"}
+
+KKT_LIFTED = 0
+KKT_HYKKT = 1
+
+EXPORTED = [
+    "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
+    "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_factor_export",
+    "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
+    "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("relax_cols", ctypes.c_int), ("relax_zeros", ctypes.c_int),
+                ("max_width", ctypes.c_int), ("delta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("tol_refine", ctypes.c_double),
+                ("tol_cg", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("refine_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("failed_col", ctypes.c_int), ("status_detail", ctypes.c_int),
+                ("bwd_err", ctypes.c_double), ("delta_x", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("assemble_ms", ctypes.c_double), ("factor_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("factor_launches", ctypes.c_int64),
+                ("factor_calls", ctypes.c_int64), ("kinv_calls", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+P = ctypes.c_void_p
+I32P = ctypes.POINTER(ctypes.c_int)
+I64P = ctypes.POINTER(ctypes.c_int64)
+F64P = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library {LIB_PATH} is missing; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.kkt_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.kkt_default_options.restype = None
+    for name in ("kkt_analyse", "kkt_analyse_host"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int, ctypes.c_int, I32P, I32P, I32P, I32P,
+                      ctypes.POINTER(Options), ctypes.POINTER(P)]
+        f.restype = ctypes.c_int
+    L.kkt_symbolic_sizes.argtypes = [P, I32P, I64P, I64P, I64P, I32P, F64P]
+    L.kkt_symbolic_sizes.restype = ctypes.c_int
+    L.kkt_symbolic_export.argtypes = [P, I32P, I32P, I32P, I32P, I32P, I32P]
+    L.kkt_symbolic_export.restype = ctypes.c_int
+    L.kkt_factor.argtypes = [P, P, P, P, P, ctypes.c_double, P, ctypes.POINTER(Info)]
+    L.kkt_factor.restype = ctypes.c_int
+    L.kkt_solve.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(Info)]
+    L.kkt_solve.restype = ctypes.c_int
+    L.kkt_backsolve.argtypes = [P, P, P, P]
+    L.kkt_backsolve.restype = ctypes.c_int
+    L.kkt_factor_export.argtypes = [P, I64P, I32P, F64P]
+    L.kkt_factor_export.restype = ctypes.c_int
+    L.kkt_last_error.argtypes = [P]
+    L.kkt_last_error.restype = ctypes.c_char_p
+    L.kkt_destroy.argtypes = [P]
+    L.kkt_destroy.restype = None
+    L.kkt_tray_sizes.argtypes = [F64P, I32P, I32P, I32P, I32P]
+    L.kkt_tray_sizes.restype = ctypes.c_int
+    L.kkt_tray_pattern.argtypes = [F64P, I32P, I32P, I32P, I32P]
+    L.kkt_tray_pattern.restype = ctypes.c_int
+    L.kkt_tray_eval.argtypes = [F64P, P, P, ctypes.c_double, P, P, P, P, P, P]
+    L.kkt_tray_eval.restype = ctypes.c_int
+    L.kkt_set_profiling.argtypes = [P, ctypes.c_int]
+    L.kkt_set_profiling.restype = ctypes.c_int
+    L.kkt_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.kkt_get_stats.restype = ctypes.c_int
+    L.kkt_reset_stats.argtypes = [P]
+    L.kkt_reset_stats.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def ptr_i32(a):
+    return a.ctypes.data_as(I32P)
+
+
+def ptr_i64(a):
+    return a.ctypes.data_as(I64P)
+
+
+def ptr_f64(a):
+    return a.ctypes.data_as(F64P)

@@ -1,0 +1,904 @@
+// C ABI of the GB300 KKT library: symbolic analysis, numeric factorisation
+// and the two hybrid solves of Pacaud & Shin (arXiv 2403.15913, Sec. IV-V).
+#include "kkt.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "symbolic.h"
+
+using namespace kktgb;
+
+namespace {
+
+constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct kkt_ctx {
+    kkt_options opt{};
+    std::string err;
+    int n = 0, m = 0, nnzW = 0, nnzJ = 0;
+    Symbolic sym;
+    // host copies of the plan (for exports and launches)
+    std::vector<int> h_sn_f, h_sn_c, h_sn_r, h_sn_rptr;
+    std::vector<long long> h_sn_lptr;
+    std::vector<int> h_lvl_ptr, h_lvl_sn;
+    std::vector<int> lvl_max_c;
+    std::vector<long long> lvl_max_rc;
+    long long panel = 0;
+    long long nk = 0;
+    int nlev = 0;
+    // device allocations (all freed in kkt_destroy)
+    std::vector<void*> allocs;
+    Plan plan{};
+    int* d_lvl_sn = nullptr;
+    int *d_perm = nullptr, *d_iperm = nullptr;
+    long long *d_k_slot = nullptr, *d_k_sptr = nullptr;
+    int2* d_k_src = nullptr;
+    int* d_jrow = nullptr;
+    int *d_wf_ptr = nullptr, *d_wf_col = nullptr, *d_wf_idx = nullptr;
+    int *d_j_ptr = nullptr, *d_j_col = nullptr;
+    int *d_jt_ptr = nullptr, *d_jt_row = nullptr, *d_jt_idx = nullptr;
+    double* d_Lx = nullptr;
+    double* d_sc = nullptr;     // device scalars
+    int* d_fail = nullptr;
+    double* d_part = nullptr;
+    // work vectors
+    double *w_xp = nullptr, *w_t = nullptr, *w_r = nullptr, *w_d = nullptr;
+    double *w_q = nullptr, *w_p = nullptr, *w_sp = nullptr, *w_res = nullptr, *w_cgx = nullptr;
+    double *w_rg = nullptr, *w_tn = nullptr;
+    // private copies of the values of the last kkt_factor (residuals of the
+    // following solves read them, so callers may free their buffers)
+    double *v_W = nullptr, *v_J = nullptr, *v_sigma = nullptr, *v_D = nullptr;
+    double* h_sc = nullptr;     // pinned host scalars
+    // factor inputs of the last kkt_factor
+    bool factored = false;
+    const double *f_W = nullptr, *f_J = nullptr, *f_sigma = nullptr, *f_D = nullptr;
+    double f_delta_x = 0.0, f_Dconst = 0.0;
+    double knorm = 0.0;
+    const double* f_C = nullptr;   // dual block of the target system (device) or NULL
+    DevBuf<double> d_Cbuf;
+    bool device_ready = false;   // false for host-only analyses
+    // tracing
+    bool profiling = false;
+    kkt_stats stats{};
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Span {
+        cudaEvent_t a, b;
+        int kind;   // 0 assemble, 1 factor, 2 solve, 3 other
+    };
+    std::vector<Span> spans;
+};
+
+namespace {
+
+// device scalar slots
+enum { SC_RMAX = 0, SC_VMAX, SC_BMAX, SC_KNORM, SC_DOT0, SC_DOT1, SC_DOT2, SC_DOT3, SC_COUNT };
+
+thread_local std::string g_err;   // last error of calls that have no context
+
+kkt_status set_err(kkt_ctx* c, kkt_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+template <class T>
+kkt_status upload(kkt_ctx* c, T** dst, const std::vector<T>& src) {
+    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    CUDA_TRY(c, cudaMalloc((void**)dst, bytes));
+    c->allocs.push_back(*dst);
+    if (!src.empty()) CUDA_TRY(c, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return KKT_OK;
+}
+
+template <class T>
+kkt_status alloc(kkt_ctx* c, T** dst, size_t count) {
+    CUDA_TRY(c, cudaMalloc((void**)dst, std::max<size_t>(1, count) * sizeof(T)));
+    c->allocs.push_back(*dst);
+    return KKT_OK;
+}
+
+#define TRY(x)                         \
+    do {                               \
+        kkt_status s_ = (x);           \
+        if (s_ != KKT_OK) return s_;   \
+    } while (0)
+
+int grid_for(long long work) {
+    long long g = (work + kThreads - 1) / kThreads;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
+}
+
+// ------------------------------------------------------------- tracing
+cudaEvent_t next_event(kkt_ctx* c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// returns an open span index or -1
+int span_begin(kkt_ctx* c, int kind, cudaStream_t st) {
+    if (!c->profiling) return -1;
+    cudaEvent_t a = next_event(c), b = next_event(c);
+    if (!a || !b) return -1;
+    cudaEventRecord(a, st);
+    c->spans.push_back({a, b, kind});
+    return (int)c->spans.size() - 1;
+}
+
+void span_end(kkt_ctx* c, int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(c->spans[idx].b, st);
+}
+
+// after a stream synchronisation: accumulate and recycle the events
+void spans_collect(kkt_ctx* c) {
+    for (auto& sp : c->spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) != cudaSuccess) continue;
+        double* dst = sp.kind == 0 ? &c->stats.assemble_ms
+                      : sp.kind == 1 ? &c->stats.factor_ms
+                      : sp.kind == 2 ? &c->stats.solve_ms : &c->stats.other_ms;
+        *dst += ms;
+    }
+    c->spans.clear();
+    c->ev_used = 0;
+}
+
+// Build the device plan from the symbolic analysis and the input patterns.
+kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, const int* J_rowptr,
+                      const int* J_colind) {
+    const Symbolic& S = c->sym;
+    const int n = c->n, m = c->m, ns = S.ns();
+    std::vector<int>& sn_f = c->h_sn_f;
+    std::vector<int>& sn_c = c->h_sn_c;
+    std::vector<int>& sn_r = c->h_sn_r;
+    std::vector<long long>& sn_lptr = c->h_sn_lptr;
+    sn_f.resize(ns);
+    sn_c.resize(ns);
+    sn_r.resize(ns);
+    sn_lptr.resize(ns + 1);
+    c->h_sn_rptr = S.sn_rowptr;
+    std::vector<int> snode(n);
+    long long off = 0;
+    for (int s = 0; s < ns; ++s) {
+        sn_f[s] = S.sn_ptr[s];
+        sn_c[s] = S.sn_ptr[s + 1] - S.sn_ptr[s];
+        sn_r[s] = S.sn_rowptr[s + 1] - S.sn_rowptr[s];
+        sn_lptr[s] = off;
+        off += (long long)sn_r[s] * sn_c[s];
+        for (int j = sn_f[s]; j < S.sn_ptr[s + 1]; ++j) snode[j] = s;
+    }
+    sn_lptr[ns] = off;
+    c->panel = off;
+
+    // position of every row inside rows(s), computed on demand
+    std::vector<int> pos(n, -1);
+    auto fill_pos = [&](int s) {
+        for (int q = S.sn_rowptr[s]; q < S.sn_rowptr[s + 1]; ++q) pos[S.sn_rows[q]] = q - S.sn_rowptr[s];
+    };
+    auto clear_pos = [&](int s) {
+        for (int q = S.sn_rowptr[s]; q < S.sn_rowptr[s + 1]; ++q) pos[S.sn_rows[q]] = -1;
+    };
+
+    // ---- assembly sources, grouped by panel slot
+    struct Src {
+        long long slot;
+        int a, b;
+    };
+    std::vector<Src> srcs;
+    // collect (new row, new col) for every source, then resolve slots per supernode
+    struct Raw {
+        int i, j, a, b;
+    };
+    std::vector<Raw> raw;
+    raw.reserve((size_t)W_colptr[n] + n + 16 * (size_t)J_rowptr[m]);
+    for (int col = 0; col < n; ++col)
+        for (int p = W_colptr[col]; p < W_colptr[col + 1]; ++p) {
+            int a = S.iperm[W_rowind[p]], b = S.iperm[col];
+            raw.push_back({std::max(a, b), std::min(a, b), p, -1});
+        }
+    for (int v = 0; v < n; ++v) raw.push_back({S.iperm[v], S.iperm[v], v, -2});
+    std::vector<int> jrow(std::max(1, J_rowptr[m]));
+    for (int r = 0; r < m; ++r)
+        for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p) {
+            jrow[p] = r;
+            for (int q = p; q < J_rowptr[r + 1]; ++q) {
+                int a = S.iperm[J_colind[p]], b = S.iperm[J_colind[q]];
+                raw.push_back({std::max(a, b), std::min(a, b), p, q});
+            }
+        }
+    // bucket by supernode of the column, then resolve the slot
+    std::vector<long long> bucket_ptr(ns + 1, 0);
+    for (const Raw& x : raw) bucket_ptr[snode[x.j] + 1]++;
+    for (int s = 0; s < ns; ++s) bucket_ptr[s + 1] += bucket_ptr[s];
+    std::vector<Raw> sorted(raw.size());
+    {
+        std::vector<long long> fillp(bucket_ptr.begin(), bucket_ptr.end() - 1);
+        for (const Raw& x : raw) sorted[fillp[snode[x.j]]++] = x;
+    }
+    std::vector<Raw>().swap(raw);
+    srcs.reserve(sorted.size());
+    for (int s = 0; s < ns; ++s) {
+        fill_pos(s);
+        for (long long q = bucket_ptr[s]; q < bucket_ptr[s + 1]; ++q) {
+            const Raw& x = sorted[q];
+            int pi = pos[x.i];
+            if (pi < 0) {
+                clear_pos(s);
+                return set_err(c, KKT_ERR_INTERNAL, "assembly entry outside the supernode structure");
+            }
+            long long slot = sn_lptr[s] + (long long)(x.j - sn_f[s]) * sn_r[s] + pi;
+            srcs.push_back({slot, x.a, x.b});
+        }
+        clear_pos(s);
+    }
+    std::vector<Raw>().swap(sorted);
+    std::stable_sort(srcs.begin(), srcs.end(), [](const Src& x, const Src& y) { return x.slot < y.slot; });
+    std::vector<long long> k_slot, k_sptr;
+    std::vector<int2> k_src;
+    k_src.reserve(srcs.size());
+    for (size_t q = 0; q < srcs.size(); ++q) {
+        if (q == 0 || srcs[q].slot != srcs[q - 1].slot) {
+            k_slot.push_back(srcs[q].slot);
+            k_sptr.push_back((long long)q);
+        }
+        k_src.push_back(make_int2(srcs[q].a, srcs[q].b));
+    }
+    k_sptr.push_back((long long)srcs.size());
+    c->nk = (long long)k_slot.size();
+    std::vector<Src>().swap(srcs);
+
+    // ---- update segments and relative maps
+    std::vector<int> seg_ptr{0}, seg_t, seg_a, seg_b, relmap;
+    std::vector<long long> seg_map;
+    for (int s = 0; s < ns; ++s) {
+        const int cc = sn_c[s], rr = sn_r[s], rb = rr - cc;
+        const int* rows = S.sn_rows.data() + S.sn_rowptr[s];
+        int i = 0;
+        while (i < rb) {
+            int t = snode[rows[cc + i]];
+            int e = i;
+            while (e < rb && snode[rows[cc + e]] == t) ++e;
+            seg_t.push_back(t);
+            seg_a.push_back(i);
+            seg_b.push_back(e);
+            seg_map.push_back((long long)relmap.size());
+            fill_pos(t);
+            for (int q = i; q < rb; ++q) {
+                int pq = pos[rows[cc + q]];
+                if (pq < 0) {
+                    clear_pos(t);
+                    return set_err(c, KKT_ERR_INTERNAL, "supernode row structure is not nested");
+                }
+                relmap.push_back(pq);
+            }
+            clear_pos(t);
+            i = e;
+        }
+        seg_ptr.push_back((int)seg_t.size());
+    }
+
+    // ---- levels of the supernodal tree
+    std::vector<int> level(ns, 0);
+    for (int s = 0; s < ns; ++s)
+        if (S.sn_parent[s] >= 0) level[S.sn_parent[s]] = std::max(level[S.sn_parent[s]], level[s] + 1);
+    int nlev = 0;
+    for (int s = 0; s < ns; ++s) nlev = std::max(nlev, level[s] + 1);
+    c->nlev = nlev;
+    c->h_lvl_ptr.assign(nlev + 1, 0);
+    for (int s = 0; s < ns; ++s) c->h_lvl_ptr[level[s] + 1]++;
+    for (int l = 0; l < nlev; ++l) c->h_lvl_ptr[l + 1] += c->h_lvl_ptr[l];
+    c->h_lvl_sn.resize(ns);
+    c->lvl_max_c.assign(nlev, 0);
+    c->lvl_max_rc.assign(nlev, 0);
+    {
+        std::vector<int> fillp(c->h_lvl_ptr.begin(), c->h_lvl_ptr.end() - 1);
+        for (int s = 0; s < ns; ++s) {
+            c->h_lvl_sn[fillp[level[s]]++] = s;
+            c->lvl_max_c[level[s]] = std::max(c->lvl_max_c[level[s]], sn_c[s]);
+            c->lvl_max_rc[level[s]] =
+                std::max(c->lvl_max_rc[level[s]], (long long)sn_c[s] * sn_r[s]);
+        }
+    }
+
+    // ---- SpMV structures (original labels)
+    std::vector<int> wf_ptr(n + 1, 0), wf_col, wf_idx;
+    for (int col = 0; col < n; ++col)
+        for (int p = W_colptr[col]; p < W_colptr[col + 1]; ++p) {
+            wf_ptr[W_rowind[p] + 1]++;
+            if (W_rowind[p] != col) wf_ptr[col + 1]++;
+        }
+    for (int i = 0; i < n; ++i) wf_ptr[i + 1] += wf_ptr[i];
+    wf_col.resize(wf_ptr[n]);
+    wf_idx.resize(wf_ptr[n]);
+    {
+        std::vector<int> fillp(wf_ptr.begin(), wf_ptr.end() - 1);
+        for (int col = 0; col < n; ++col)
+            for (int p = W_colptr[col]; p < W_colptr[col + 1]; ++p) {
+                int r = W_rowind[p];
+                wf_col[fillp[r]] = col;
+                wf_idx[fillp[r]++] = p;
+                if (r != col) {
+                    wf_col[fillp[col]] = r;
+                    wf_idx[fillp[col]++] = p;
+                }
+            }
+    }
+    std::vector<int> j_ptr(J_rowptr, J_rowptr + m + 1), j_col(J_colind, J_colind + J_rowptr[m]);
+    std::vector<int> jt_ptr(n + 1, 0), jt_row(J_rowptr[m]), jt_idx(J_rowptr[m]);
+    for (int p = 0; p < J_rowptr[m]; ++p) jt_ptr[J_colind[p] + 1]++;
+    for (int i = 0; i < n; ++i) jt_ptr[i + 1] += jt_ptr[i];
+    {
+        std::vector<int> fillp(jt_ptr.begin(), jt_ptr.end() - 1);
+        for (int r = 0; r < m; ++r)
+            for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p) {
+                int col = J_colind[p];
+                jt_row[fillp[col]] = r;
+                jt_idx[fillp[col]++] = p;
+            }
+    }
+
+    // ---- validate every index the kernels will dereference
+    for (size_t e = 0; e < k_slot.size(); ++e)
+        if (k_slot[e] < 0 || k_slot[e] >= c->panel)
+            return set_err(c, KKT_ERR_INTERNAL, "assembly slot out of range");
+    for (const int2& q : k_src) {
+        bool ok = q.y == -1 ? (q.x >= 0 && q.x < W_colptr[n])
+                : q.y == -2 ? (q.x >= 0 && q.x < n)
+                            : (q.x >= 0 && q.x < J_rowptr[m] && q.y < J_rowptr[m]);
+        if (!ok) return set_err(c, KKT_ERR_INTERNAL, "assembly source out of range");
+    }
+    for (int s = 0; s < ns; ++s) {
+        const int cc = sn_c[s], rb = sn_r[s] - cc;
+        const int* rows = S.sn_rows.data() + S.sn_rowptr[s];
+        for (int q = 0; q < sn_r[s]; ++q)
+            if (rows[q] < 0 || rows[q] >= n) return set_err(c, KKT_ERR_INTERNAL, "row out of range");
+        if (rb > 0 && seg_ptr[s + 1] <= seg_ptr[s])
+            return set_err(c, KKT_ERR_INTERNAL, "missing update segment");
+        for (int k = seg_ptr[s]; k < seg_ptr[s + 1]; ++k) {
+            const int t = seg_t[k];
+            if (t <= s || t >= ns) return set_err(c, KKT_ERR_INTERNAL, "bad segment target");
+            for (int i = seg_a[k]; i < seg_b[k]; ++i) {
+                int colo = rows[cc + i] - sn_f[t];
+                if (colo < 0 || colo >= sn_c[t]) return set_err(c, KKT_ERR_INTERNAL, "bad column offset");
+            }
+            for (int i = seg_a[k]; i < rb; ++i) {
+                int rp = relmap[seg_map[k] + (i - seg_a[k])];
+                if (rp < 0 || rp >= sn_r[t]) return set_err(c, KKT_ERR_INTERNAL, "bad relative row");
+            }
+        }
+    }
+
+    // ---- upload
+    int *d_sn_f, *d_sn_c, *d_sn_r, *d_sn_rptr, *d_rows, *d_seg_ptr, *d_seg_t, *d_seg_a, *d_seg_b,
+        *d_relmap;
+    long long *d_sn_lptr, *d_seg_map;
+    TRY(upload(c, &d_sn_f, sn_f));
+    TRY(upload(c, &d_sn_c, sn_c));
+    TRY(upload(c, &d_sn_r, sn_r));
+    TRY(upload(c, &d_sn_lptr, sn_lptr));
+    TRY(upload(c, &d_sn_rptr, S.sn_rowptr));
+    TRY(upload(c, &d_rows, S.sn_rows));
+    TRY(upload(c, &d_seg_ptr, seg_ptr));
+    TRY(upload(c, &d_seg_t, seg_t));
+    TRY(upload(c, &d_seg_a, seg_a));
+    TRY(upload(c, &d_seg_b, seg_b));
+    TRY(upload(c, &d_seg_map, seg_map));
+    TRY(upload(c, &d_relmap, relmap));
+    c->plan = Plan{d_sn_f, d_sn_c, d_sn_r, d_sn_lptr, d_sn_rptr, d_rows,
+                   d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap};
+    TRY(upload(c, &c->d_lvl_sn, c->h_lvl_sn));
+    TRY(upload(c, &c->d_perm, S.perm));
+    TRY(upload(c, &c->d_iperm, S.iperm));
+    TRY(upload(c, &c->d_k_slot, k_slot));
+    TRY(upload(c, &c->d_k_sptr, k_sptr));
+    TRY(upload(c, &c->d_k_src, k_src));
+    TRY(upload(c, &c->d_jrow, jrow));
+    TRY(upload(c, &c->d_wf_ptr, wf_ptr));
+    TRY(upload(c, &c->d_wf_col, wf_col));
+    TRY(upload(c, &c->d_wf_idx, wf_idx));
+    TRY(upload(c, &c->d_j_ptr, j_ptr));
+    TRY(upload(c, &c->d_j_col, j_col));
+    TRY(upload(c, &c->d_jt_ptr, jt_ptr));
+    TRY(upload(c, &c->d_jt_row, jt_row));
+    TRY(upload(c, &c->d_jt_idx, jt_idx));
+    TRY(alloc(c, &c->d_Lx, (size_t)c->panel));
+    TRY(alloc(c, &c->d_sc, 16));
+    TRY(alloc(c, &c->d_fail, 4));
+    TRY(alloc(c, &c->d_part, kRedBlocks));
+    const size_t nm = (size_t)n + m;
+    TRY(alloc(c, &c->w_xp, n));
+    TRY(alloc(c, &c->w_t, n));
+    TRY(alloc(c, &c->w_r, nm));
+    TRY(alloc(c, &c->w_d, nm));
+    TRY(alloc(c, &c->w_q, n));
+    TRY(alloc(c, &c->w_p, std::max(n, m)));
+    TRY(alloc(c, &c->w_sp, std::max(n, m)));
+    TRY(alloc(c, &c->w_res, m));
+    TRY(alloc(c, &c->w_cgx, m));
+    TRY(alloc(c, &c->w_rg, n));
+    TRY(alloc(c, &c->w_tn, n));
+    TRY(alloc(c, &c->v_W, std::max(1, W_colptr[n])));
+    TRY(alloc(c, &c->v_J, std::max(1, J_rowptr[m])));
+    TRY(alloc(c, &c->v_sigma, n));
+    TRY(alloc(c, &c->v_D, std::max(1, m)));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, 16 * sizeof(double)));
+    return KKT_OK;
+}
+
+// x <- K^{-1} x  (in and out may alias; uses w_xp)
+kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st) {
+    const int n = c->n;
+    const int sp = span_begin(c, 2, st);
+    c->stats.kinv_calls++;
+    c->stats.launches += 2 + 2LL * c->nlev;
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp);
+    for (int l = 0; l < c->nlev; ++l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
+        forward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
+                                                        c->d_Lx, c->w_xp);
+    }
+    for (int l = c->nlev - 1; l >= 0; --l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
+        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
+                                                         c->d_Lx, c->w_xp);
+    }
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out);
+    span_end(c, sp, st);
+    CUDA_TRY(c, cudaGetLastError());
+    return KKT_OK;
+}
+
+kkt_status dot(kkt_ctx* c, int len, const double* a, const double* b, int slot, cudaStream_t st) {
+    c->stats.launches += 2;
+    dot_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(len, a, b, c->d_part);
+    dot_final_kernel<<<1, kThreads, 0, st>>>(kRedBlocks, c->d_part, c->d_sc + slot);
+    return KKT_OK;
+}
+
+// r = b - K_orig v and eta; returns eta through *eta (host sync)
+kkt_status residual(kkt_ctx* c, const double* bx, const double* by, const double* vx,
+                    const double* vy, double* rx, double* ry, cudaStream_t st, double* eta) {
+    const int n = c->n, m = c->m;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_sc + SC_RMAX, 0, 3 * sizeof(double), st));
+    c->stats.launches += 1;
+    residual_kernel<<<grid_for((long long)n + m), kThreads, 0, st>>>(
+        n, m, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_j_col, c->d_jt_ptr,
+        c->d_jt_row, c->d_jt_idx, c->f_J, c->f_sigma, c->f_delta_x, c->f_C, bx, by, vx, vy, rx, ry,
+        c->d_sc + SC_RMAX);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    const double rmax = c->h_sc[0], vmax = c->h_sc[1], bmax = c->h_sc[2];
+    const double den = c->knorm * vmax + bmax;
+    *eta = den > 0 ? rmax / den : (rmax > 0 ? INFINITY : 0.0);
+    return KKT_OK;
+}
+
+// Lifted-KKT preconditioner: d = M^{-1} r with M = [[H, J^T], [J, -D^{-1}]]
+kkt_status lifted_precond(kkt_ctx* c, const double* rx, const double* ry, double* dx, double* dy,
+                          cudaStream_t st) {
+    const int n = c->n, m = c->m;
+    c->stats.launches += 2;
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                     c->f_J, rx, ry, c->f_D, c->f_Dconst, 1.0,
+                                                     c->w_t);
+    TRY(apply_kinv(c, c->w_t, dx, st));
+    j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, dx, ry,
+                                                     c->f_D, c->f_Dconst, dy);
+    return KKT_OK;
+}
+
+// HyKKT inner solve (Eq. hykkt / Eq. schurcomp): d = K_orig^{-1} r up to the
+// CG tolerance.  Returns CG iterations through *its.
+kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* dx, double* dy,
+                       cudaStream_t st, int* its, bool* cg_ok) {
+    const int n = c->n, m = c->m;
+    const double gamma = c->f_Dconst;
+    c->stats.launches += 4;
+    // r_gamma = r_x + gamma J^T r_y ; q = K_gamma^{-1} r_gamma
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                     c->f_J, rx, ry, nullptr, 1.0, gamma, c->w_rg);
+    TRY(apply_kinv(c, c->w_rg, c->w_q, st));
+    // rhs = J q - r_y  (stored in w_res: the CG residual starts at rhs)
+    j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, c->w_q, ry,
+                                                     nullptr, 1.0, c->w_res);
+    CUDA_TRY(c, cudaMemsetAsync(c->w_cgx, 0, m * sizeof(double), st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->w_p, c->w_res, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(dot(c, m, c->w_res, c->w_res, SC_DOT0, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_DOT0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    double rr = c->h_sc[0];
+    const double stop = c->opt.tol_cg * std::sqrt(rr);
+    int it = 0;
+    int cur = SC_DOT0, nxt = SC_DOT1;
+    while (std::sqrt(rr) > stop && it < c->opt.max_cg) {
+        c->stats.launches += 4;
+        // Sp = J K^{-1} J^T p
+        jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                         c->f_J, nullptr, c->w_p, nullptr, 1.0, 1.0,
+                                                         c->w_tn);
+        TRY(apply_kinv(c, c->w_tn, c->w_tn, st));
+        j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, c->w_tn,
+                                                         nullptr, nullptr, 1.0, c->w_sp);
+        TRY(dot(c, m, c->w_p, c->w_sp, SC_DOT2, st));
+        cg_update_xr_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, cur, SC_DOT2, c->w_p,
+                                                              c->w_sp, c->w_cgx, c->w_res);
+        TRY(dot(c, m, c->w_res, c->w_res, nxt, st));
+        cg_update_p_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, nxt, cur, c->w_res, c->w_p);
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + nxt, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        rr = c->h_sc[0];
+        std::swap(cur, nxt);
+        ++it;
+    }
+    *its = it;
+    *cg_ok = std::sqrt(rr) <= stop;
+    // dx = K_gamma^{-1} (r_gamma - J^T dy)
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                     c->f_J, c->w_rg, c->w_cgx, nullptr, 1.0, -1.0,
+                                                     c->w_tn);
+    TRY(apply_kinv(c, c->w_tn, dx, st));
+    CUDA_TRY(c, cudaMemcpyAsync(dy, c->w_cgx, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return KKT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kkt_default_options(kkt_options* o) {
+    if (!o) return;
+    o->scheme = KKT_LIFTED;
+    o->leaf_size = 64;
+    o->relax_cols = 48;
+    o->relax_zeros = 1024;
+    o->max_width = 64;
+    o->delta = 1e-8;
+    o->gamma = 1e4;
+    o->tol_refine = 1e-10;
+    o->tol_cg = 1e-10;
+    o->max_refine = 20;
+    o->max_cg = 200;
+    o->target_relaxed = 0;
+}
+
+namespace {
+kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind,
+                          const int* J_rowptr, const int* J_colind, const kkt_options* opt,
+                          bool device, kkt_ctx** out) {
+    if (!out) return set_err(nullptr, KKT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    kkt_ctx* c = new (std::nothrow) kkt_ctx();
+    if (!c) return set_err(nullptr, KKT_ERR_OOM, "host allocation failed");
+    if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
+    if (c->opt.scheme != KKT_LIFTED && c->opt.scheme != KKT_HYKKT) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "unknown scheme");
+    }
+    if (c->opt.max_width <= 0 || c->opt.max_width > 4096) c->opt.max_width = 4096;
+    c->n = n;
+    c->m = m;
+    Graph g;
+    std::string e = build_graph(n, m, W_colptr, W_rowind, J_rowptr, J_colind, g);
+    if (!e.empty()) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
+    }
+    c->nnzW = W_colptr[n];
+    c->nnzJ = J_rowptr[m];
+    SymbolicOptions so;
+    so.leaf_size = c->opt.leaf_size;
+    so.relax_cols = c->opt.relax_cols;
+    so.relax_zeros = c->opt.relax_zeros;
+    so.max_width = c->opt.max_width;
+    e = analyse(g, so, c->sym);
+    if (!e.empty()) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
+    }
+    const int ns = c->sym.ns();
+    c->h_sn_c.resize(ns);
+    c->h_sn_r.resize(ns);
+    for (int s = 0; s < ns; ++s) {
+        c->h_sn_c[s] = c->sym.sn_ptr[s + 1] - c->sym.sn_ptr[s];
+        c->h_sn_r[s] = c->sym.sn_rowptr[s + 1] - c->sym.sn_rowptr[s];
+    }
+    {
+        std::vector<int> level(ns, 0);
+        int nlev = 0;
+        for (int s = 0; s < ns; ++s) {
+            if (c->sym.sn_parent[s] >= 0)
+                level[c->sym.sn_parent[s]] = std::max(level[c->sym.sn_parent[s]], level[s] + 1);
+            nlev = std::max(nlev, level[s] + 1);
+        }
+        c->nlev = nlev;
+    }
+    if (device) {
+        kkt_status st = build_plan(c, W_colptr, W_rowind, J_rowptr, J_colind);
+        if (st != KKT_OK) {
+            set_err(nullptr, st, c->err);
+            kkt_destroy(c);
+            return st;
+        }
+        cudaFuncSetAttribute(factor_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemCapElems * sizeof(double)));
+        cudaFuncSetAttribute(forward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             4096 * (int)sizeof(double));
+        cudaFuncSetAttribute(backward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             4096 * (int)sizeof(double));
+    }
+    c->device_ready = device;
+    *out = c;
+    return KKT_OK;
+}
+}  // namespace
+
+kkt_status kkt_analyse(int n, int m, const int* W_colptr, const int* W_rowind, const int* J_rowptr,
+                       const int* J_colind, const kkt_options* opt, kkt_ctx** out) {
+    return analyse_common(n, m, W_colptr, W_rowind, J_rowptr, J_colind, opt, true, out);
+}
+
+kkt_status kkt_analyse_host(int n, int m, const int* W_colptr, const int* W_rowind,
+                            const int* J_rowptr, const int* J_colind, const kkt_options* opt,
+                            kkt_ctx** out) {
+    return analyse_common(n, m, W_colptr, W_rowind, J_rowptr, J_colind, opt, false, out);
+}
+
+kkt_status kkt_symbolic_sizes(const kkt_ctx* c, int* ns, int64_t* nnz_L, int64_t* panel,
+                              int64_t* row_entries, int* levels, double* flops) {
+    if (!c) return KKT_ERR_ARG;
+    if (ns) *ns = c->sym.ns();
+    if (nnz_L) *nnz_L = c->sym.nnz_L;
+    if (panel) {
+        int64_t p = 0;
+        for (int s = 0; s < c->sym.ns(); ++s) {
+            int64_t cc = c->h_sn_c[s], rr = c->h_sn_r[s];
+            p += cc * rr - cc * (cc - 1) / 2;
+        }
+        *panel = p;
+    }
+    if (row_entries) *row_entries = (int64_t)c->sym.sn_rows.size();
+    if (levels) *levels = c->nlev;
+    if (flops) *flops = c->sym.flops;
+    return KKT_OK;
+}
+
+kkt_status kkt_symbolic_export(const kkt_ctx* c, int* perm, int* parent, int* colcount, int* sn_ptr,
+                               int* sn_rowptr, int* sn_rows) {
+    if (!c) return KKT_ERR_ARG;
+    const Symbolic& S = c->sym;
+    if (perm) std::copy(S.perm.begin(), S.perm.end(), perm);
+    if (parent) std::copy(S.parent.begin(), S.parent.end(), parent);
+    if (colcount) std::copy(S.colcount.begin(), S.colcount.end(), colcount);
+    if (sn_ptr) std::copy(S.sn_ptr.begin(), S.sn_ptr.end(), sn_ptr);
+    if (sn_rowptr) std::copy(S.sn_rowptr.begin(), S.sn_rowptr.end(), sn_rowptr);
+    if (sn_rows) std::copy(S.sn_rows.begin(), S.sn_rows.end(), sn_rows);
+    return KKT_OK;
+}
+
+kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
+                      const double* d_D, double delta_x, cudaStream_t st, kkt_info* info) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->device_ready) return set_err(c, KKT_ERR_STATE, "context was analysed on the host only");
+    if (!d_Wval && c->nnzW > 0) return set_err(c, KKT_ERR_ARG, "d_Wval is NULL");
+    if (!d_Jval && c->nnzJ > 0) return set_err(c, KKT_ERR_ARG, "d_Jval is NULL");
+    if (!d_sigma) return set_err(c, KKT_ERR_ARG, "d_sigma is NULL");
+    if (c->opt.scheme == KKT_HYKKT && d_D) return set_err(c, KKT_ERR_ARG, "HyKKT takes D = gamma");
+    if (!(std::isfinite(delta_x) && delta_x >= 0)) return set_err(c, KKT_ERR_ARG, "bad delta_x");
+    c->factored = false;
+    if (c->nnzW > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_W, d_Wval, (size_t)c->nnzW * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (c->nnzJ > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_J, d_Jval, (size_t)c->nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->v_sigma, d_sigma, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const bool hasD = c->opt.scheme == KKT_LIFTED && d_D;
+    if (hasD && c->m > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_D, d_D, (size_t)c->m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    c->f_W = c->v_W;
+    c->f_J = c->v_J;
+    c->f_sigma = c->v_sigma;
+    c->f_D = hasD ? c->v_D : nullptr;
+    c->f_Dconst = c->opt.scheme == KKT_LIFTED ? 1.0 / c->opt.delta : c->opt.gamma;
+    c->f_delta_x = delta_x;
+    // dual block of the target system: C = 1/D (relaxed problem) or none
+    c->f_C = nullptr;
+    if (c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
+        if (!c->d_Cbuf.p) {
+            TRY(alloc(c, &c->d_Cbuf.p, c->m));
+            c->d_Cbuf.n = c->m;
+        }
+        c->f_C = c->d_Cbuf.p;
+    }
+    const int n = c->n, m = c->m;
+    const int sp_a = span_begin(c, 0, st);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_Lx, 0, (size_t)c->panel * sizeof(double), st));
+    assemble_kernel<<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
+                                                          c->d_jrow, c->f_W, c->f_J, c->f_sigma,
+                                                          c->f_D, c->f_Dconst, delta_x, c->d_Lx);
+    span_end(c, sp_a, st);
+    const int big = 0x7fffffff;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fail, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+    const int sp_f = span_begin(c, 1, st);
+    c->stats.factor_calls++;
+    c->stats.launches += 2 + c->nlev;
+    c->stats.factor_launches += c->nlev;
+    for (int l = 0; l < c->nlev; ++l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
+        factor_level_kernel<<<cnt, kThreads, (size_t)need * sizeof(double), st>>>(
+            c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, c->d_fail, need);
+    }
+    span_end(c, sp_f, st);
+    CUDA_TRY(c, cudaGetLastError());
+    // ||K_orig||_inf
+    CUDA_TRY(c, cudaMemsetAsync(c->d_sc + SC_KNORM, 0, sizeof(double), st));
+    if (c->f_C) {
+        if (c->f_D) recip_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->f_D, c->d_Cbuf.p);
+        else fill_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->opt.delta, c->d_Cbuf.p);
+    }
+    knorm_kernel<<<grid_for((long long)n + m), kThreads, 0, st>>>(
+        n, m, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx,
+        c->f_J, c->f_sigma, delta_x, c->f_C, c->d_sc + SC_KNORM);
+    int fail = big;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_KNORM, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    spans_collect(c);
+    c->knorm = c->h_sc[0];
+    if (info) {
+        info->failed_col = fail == big ? -1 : fail;
+        info->delta_x = delta_x;
+    }
+    if (fail != big) return set_err(c, KKT_ERR_NOT_SPD, "factorization: non-positive pivot in column " + std::to_string(fail));
+    c->factored = true;
+    return KKT_OK;
+}
+
+kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
+                     double* d_ds, cudaStream_t st, kkt_info* info) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_solve called without a successful kkt_factor");
+    if (!d_rx || !d_ry || !d_dx || !d_dy) return set_err(c, KKT_ERR_ARG, "NULL vector");
+    const int n = c->n, m = c->m;
+    double* rx = c->w_r;
+    double* ry = c->w_r + n;
+    double* dx = c->w_d;
+    double* dy = c->w_d + n;
+    CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
+    CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
+    CUDA_TRY(c, cudaMemcpyAsync(rx, d_rx, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(ry, d_ry, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> etas;
+    int slow = 0, cg_total = 0, it = 0;
+    kkt_status result = KKT_ERR_MAXIT;
+    bool cg_failed = false;
+    for (it = 0; it <= c->opt.max_refine; ++it) {
+        if (c->opt.scheme == KKT_LIFTED) {
+            TRY(lifted_precond(c, rx, ry, dx, dy, st));
+        } else {
+            int its = 0;
+            bool ok = true;
+            TRY(hykkt_inner(c, rx, ry, dx, dy, st, &its, &ok));
+            cg_total += its;
+            if (!ok) cg_failed = true;
+        }
+        c->stats.launches += 2;
+        axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, 1.0, dx, d_dx);
+        axpy_kernel<<<grid_for(m), kThreads, 0, st>>>(m, 1.0, dy, d_dy);
+        double eta = 0;
+        TRY(residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, st, &eta));
+        etas.push_back(eta);
+        if (eta <= c->opt.tol_refine) { result = KKT_OK; break; }
+        if (etas.size() >= 2 && eta > 0.9 * etas[etas.size() - 2]) {   // stagnation
+            if (++slow >= 2) { result = KKT_ERR_STALL; break; }
+        } else {
+            slow = 0;
+        }
+    }
+    if (it > c->opt.max_refine) it = c->opt.max_refine;
+    if (d_ds && c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
+        j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, d_dx, d_ry,
+                                                         nullptr, 1.0, d_ds);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    spans_collect(c);
+    if (info) {
+        info->refine_iters = it;
+        info->cg_iters = cg_total;
+        info->bwd_err = etas.empty() ? INFINITY : etas.back();
+    }
+    if (result == KKT_OK && cg_failed) result = KKT_OK;   // refinement reached the tolerance anyway
+    if (result != KKT_OK)
+        set_err(c, result, result == KKT_ERR_STALL ? "refinement stalled" : "refinement hit max_refine");
+    return result;
+}
+
+kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_t st) {
+    if (!c || !d_b || !d_x) return set_err(c, KKT_ERR_ARG, "NULL argument");
+    if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve called without a factor");
+    TRY(apply_kinv(c, d_b, d_x, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    spans_collect(c);
+    return KKT_OK;
+}
+
+kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* val) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->factored) return set_err(c, KKT_ERR_STATE, "no factor");
+    const int ns = c->sym.ns();
+    std::vector<double> Lh((size_t)c->panel);
+    if (val) CUDA_TRY(c, cudaMemcpy(Lh.data(), c->d_Lx, (size_t)c->panel * sizeof(double), cudaMemcpyDeviceToHost));
+    int64_t q = 0;
+    if (colptr) colptr[0] = 0;
+    for (int s = 0; s < ns; ++s) {
+        const int f = c->h_sn_f[s], cc = c->h_sn_c[s], rr = c->h_sn_r[s];
+        const int* rows = c->sym.sn_rows.data() + c->sym.sn_rowptr[s];
+        for (int j = 0; j < cc; ++j) {
+            for (int i = j; i < rr; ++i) {
+                if (rowind) rowind[q] = rows[i];
+                if (val) val[q] = Lh[c->h_sn_lptr[s] + (long long)j * rr + i];
+                ++q;
+            }
+            if (colptr) colptr[f + j + 1] = q;
+        }
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_set_profiling(kkt_ctx* c, int enable) {
+    if (!c) return KKT_ERR_ARG;
+    c->profiling = enable != 0;
+    return KKT_OK;
+}
+
+kkt_status kkt_get_stats(const kkt_ctx* c, kkt_stats* out) {
+    if (!c || !out) return KKT_ERR_ARG;
+    *out = c->stats;
+    return KKT_OK;
+}
+
+kkt_status kkt_reset_stats(kkt_ctx* c) {
+    if (!c) return KKT_ERR_ARG;
+    c->stats = kkt_stats{};
+    return KKT_OK;
+}
+
+const char* kkt_last_error(const kkt_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+void kkt_destroy(kkt_ctx* c) {
+    if (!c) return;
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Host-side symbolic analysis of the condensed KKT matrix (Sec. V-B of
+// Pacaud & Shin: the pattern of K is fixed across IPM iterations, so the
+// ordering and symbolic factorisation are computed once and reused by every
+// refactorisation).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace kktgb {
+
+struct SymbolicOptions {
+    int leaf_size = 64;
+    int relax_cols = 48;
+    int relax_zeros = 1024;
+    int max_width = 64;
+};
+
+// Result of the analysis.  All column/row labels after `perm` are in the
+// permuted ("new") numbering of P K P^T.
+struct Symbolic {
+    int n = 0;
+    std::vector<int> perm;      // new -> old
+    std::vector<int> iperm;     // old -> new
+    std::vector<int> parent;    // elimination tree, -1 for roots
+    std::vector<int> colcount;  // nnz of every column of L (diagonal included)
+    std::vector<int> sn_ptr;    // supernode column boundaries (ns + 1)
+    std::vector<int> sn_rowptr; // offsets into sn_rows (ns + 1)
+    std::vector<int> sn_rows;   // rows(s), ascending, starting with cols(s)
+    std::vector<int> sn_parent; // supernodal tree, -1 for roots
+    double flops = 0.0;         // sum_j colcount_j^2
+    int64_t nnz_L = 0;
+    int ns() const { return (int)sn_ptr.size() - 1; }
+};
+
+// Undirected graph of pattern(W + J^T J) without self loops, CSR with
+// sorted, duplicate-free adjacency lists.
+struct Graph {
+    int n = 0;
+    std::vector<int64_t> xadj;
+    std::vector<int> adj;
+};
+
+// Returns an empty string on success, otherwise a message.
+std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
+                        const int* J_rowptr, const int* J_colind, Graph& g);
+std::string analyse(const Graph& g, const SymbolicOptions& opt, Symbolic& out);
+
+}  // namespace kktgb

@@ -1,0 +1,165 @@
+"""Python binding of the KKT solver: one object per symbolic analysis.
+
+Every numeric step runs in the CUDA library through the C ABI; this module
+only converts arguments (numpy index arrays for patterns, torch CUDA FP64
+tensors for values, torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as nat
+
+
+class KKTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{nat.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw) -> nat.Options:
+    o = nat.Options()
+    nat.lib().kkt_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "scheme" and isinstance(v, str):
+            v = {"lifted": nat.KKT_LIFTED, "hykkt": nat.KKT_HYKKT}[v]
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class SymbolicSizes:
+    ns: int
+    nnz_L: int
+    panel: int
+    row_entries: int
+    levels: int
+    flops: float
+
+
+class KKTSolver:
+    """Symbolic analysis once (``kkt_analyse``), then any number of
+    ``factor``/``solve`` calls with new values on the same pattern."""
+
+    def __init__(self, n, m, W_colptr, W_rowind, J_rowptr, J_colind, host_only=False, **options):
+        self.n, self.m = int(n), int(m)
+        self._keep = [_i32(W_colptr), _i32(W_rowind), _i32(J_rowptr), _i32(J_colind)]
+        self.options = default_options(**options)
+        L = nat.lib()
+        ctx = ctypes.c_void_p()
+        fn = L.kkt_analyse_host if host_only else L.kkt_analyse
+        st = fn(self.n, self.m, *[nat.ptr_i32(a) for a in self._keep],
+                ctypes.byref(self.options), ctypes.byref(ctx))
+        if st != nat.KKT_OK:
+            raise KKTError(st, L.kkt_last_error(None).decode())
+        self._ctx = ctx
+        self.info = nat.Info()
+
+    # ------------------------------------------------------------- symbolic
+    def sizes(self) -> SymbolicSizes:
+        ns = ctypes.c_int()
+        nnz, panel, rows = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lev = ctypes.c_int()
+        fl = ctypes.c_double()
+        self._check(nat.lib().kkt_symbolic_sizes(self._ctx, ctypes.byref(ns), ctypes.byref(nnz),
+                                                 ctypes.byref(panel), ctypes.byref(rows),
+                                                 ctypes.byref(lev), ctypes.byref(fl)))
+        return SymbolicSizes(ns.value, nnz.value, panel.value, rows.value, lev.value, fl.value)
+
+    def symbolic(self) -> dict:
+        s = self.sizes()
+        out = dict(perm=np.empty(self.n, np.int32), parent=np.empty(self.n, np.int32),
+                   colcount=np.empty(self.n, np.int32), sn_ptr=np.empty(s.ns + 1, np.int32),
+                   sn_rowptr=np.empty(s.ns + 1, np.int32),
+                   sn_rows=np.empty(max(1, s.row_entries), np.int32))
+        self._check(nat.lib().kkt_symbolic_export(
+            self._ctx, *[nat.ptr_i32(out[k]) for k in
+                         ("perm", "parent", "colcount", "sn_ptr", "sn_rowptr", "sn_rows")]))
+        out["sn_rows"] = out["sn_rows"][:s.row_entries]
+        return out
+
+    # ------------------------------------------------------------- numeric
+    def factor(self, Wval, Jval, sigma, D=None, delta_x=0.0, stream=None):
+        """Refactorise with new values.  Returns the status code (0 or
+        KKT_ERR_NOT_SPD; other errors raise)."""
+        st = nat.lib().kkt_factor(self._ctx, _dptr(Wval), _dptr(Jval), _dptr(sigma), _dptr(D),
+                                  float(delta_x), _stream(stream), ctypes.byref(self.info))
+        if st not in (nat.KKT_OK, nat.KKT_ERR_NOT_SPD):
+            self._check(st)
+        return st
+
+    def solve(self, rx, ry, dx, dy, ds=None, stream=None):
+        """Solve K_orig [dx; dy] = [rx; ry] into the given tensors.  Returns
+        the status code (0, KKT_ERR_MAXIT or KKT_ERR_STALL; others raise)."""
+        st = nat.lib().kkt_solve(self._ctx, _dptr(rx), _dptr(ry), _dptr(dx), _dptr(dy), _dptr(ds),
+                                 _stream(stream), ctypes.byref(self.info))
+        if st not in (nat.KKT_OK, nat.KKT_ERR_MAXIT, nat.KKT_ERR_STALL):
+            self._check(st)
+        return st
+
+    def backsolve(self, b, x, stream=None):
+        """x = K^{-1} b with the current factor (condensed matrix only)."""
+        self._check(nat.lib().kkt_backsolve(self._ctx, _dptr(b), _dptr(x), _stream(stream)))
+
+    def factor_export(self):
+        """Numeric factor L (permuted order) as CSC numpy arrays."""
+        s = self.sizes()
+        colptr = np.empty(self.n + 1, np.int64)
+        rowind = np.empty(s.panel, np.int32)
+        val = np.empty(s.panel, np.float64)
+        self._check(nat.lib().kkt_factor_export(self._ctx, nat.ptr_i64(colptr), nat.ptr_i32(rowind),
+                                                nat.ptr_f64(val)))
+        return colptr, rowind, val
+
+    def set_profiling(self, on=True):
+        self._check(nat.lib().kkt_set_profiling(self._ctx, int(bool(on))))
+
+    def stats(self) -> dict:
+        st = nat.Stats()
+        self._check(nat.lib().kkt_get_stats(self._ctx, ctypes.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(nat.lib().kkt_reset_stats(self._ctx))
+
+    def last_error(self):
+        return nat.lib().kkt_last_error(self._ctx).decode()
+
+    def _check(self, st):
+        if st != nat.KKT_OK:
+            raise KKTError(st, self.last_error())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            nat.lib().kkt_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

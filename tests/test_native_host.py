@@ -1,0 +1,116 @@
+"""CPU-side checks of the CUDA library: it loads, exports every symbol the
+header declares, and its host logic (tray pattern, symbolic analysis) agrees
+bit-exactly with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from gen.tray import TrayParams, kkt_point
+from oracle import symbolic, tray
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2403_15913_gb300 import _native
+    if not os.path.exists(_native.LIB_PATH):
+        from paper_2403_15913_gb300 import build
+        build.build()
+    _native.lib()
+    return _native
+
+
+def test_library_exports_every_declared_symbol(nat):
+    header = open(os.path.join(ROOT, "include", "kkt.h")).read()
+    declared = set(re.findall(r"\b(kkt_[a-z_]+)\s*\(", header))
+    assert declared, "no declarations found"
+    L = nat.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared == set(nat.EXPORTED)
+
+
+@pytest.mark.parametrize("k,T", [(32, 3), (8, 10), (5, 1)])
+def test_tray_pattern_matches_oracle(nat, k, T):
+    from paper_2403_15913_gb300 import TrayModel
+    p = TrayParams(k=k, T=T)
+    tm = TrayModel(p.as_array())
+    assert (tm.n, tm.m) == (p.n, p.m)
+    Wc, Wr, Jr, Jc = tm.pattern()
+    pt = kkt_point(p, 0)
+    oW = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    oJ = tray.jacobian_csr(p, pt.w)
+    assert np.array_equal(Wc, oW[0]) and np.array_equal(Wr, oW[1])
+    assert np.array_equal(Jr, oJ[0]) and np.array_equal(Jc, oJ[1])
+
+
+def _compare(p_or_adj, pats, n, **opts):
+    from paper_2403_15913_gb300 import KKTSolver
+    Wc, Wr, Jr, Jc = pats
+    m = len(Jr) - 1
+    s = KKTSolver(n, m, Wc, Wr, Jr, Jc, host_only=True, **opts)
+    g = s.symbolic()
+    o = symbolic.analyse(n, Wc, Wr, Jr, Jc, leaf_size=opts["leaf_size"],
+                         relax_cols=opts["relax_cols"], relax_zeros=opts["relax_zeros"],
+                         max_width=opts["max_width"])
+    assert np.array_equal(g["perm"], o.perm)
+    assert np.array_equal(g["parent"], o.parent)
+    assert np.array_equal(g["colcount"], o.colcount)
+    assert np.array_equal(g["sn_ptr"], o.sn_ptr)
+    rows = np.concatenate(o.sn_rows)
+    assert np.array_equal(g["sn_rows"], rows)
+    assert np.array_equal(np.diff(g["sn_rowptr"]), [len(r) for r in o.sn_rows])
+    sz = s.sizes()
+    assert sz.nnz_L == o.nnz_L and sz.flops == o.flops
+    s.close()
+
+
+OPTS = [dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64),
+        dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=4096),
+        dict(leaf_size=16, relax_cols=16, relax_zeros=40, max_width=8),
+        dict(leaf_size=128, relax_cols=64, relax_zeros=4000, max_width=32)]
+
+
+@pytest.mark.parametrize("opts", OPTS)
+@pytest.mark.parametrize("k,T", [(32, 50), (8, 40), (32, 1), (4, 0)])
+def test_symbolic_bit_exact_tray(nat, opts, k, T):
+    p = TrayParams(k=k, T=T)
+    pt = kkt_point(p, 0)
+    W = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = tray.jacobian_csr(p, pt.w)
+    _compare(p, (W[0], W[1], J[0], J[1]), p.n, **opts)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_symbolic_bit_exact_random(nat, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(20, 300))
+    m = int(rng.integers(0, n))
+    # random lower W pattern with diagonal, random J rows of 1..5 entries
+    colptr = [0]
+    rowind = []
+    for j in range(n):
+        rows = sorted(set([j] + [int(i) for i in rng.integers(j, n, rng.integers(0, 3))]))
+        rowind += rows
+        colptr.append(len(rowind))
+    rowptr = [0]
+    colind = []
+    for r in range(m):
+        cols = sorted(set(int(c) for c in rng.integers(0, n, rng.integers(1, 6))))
+        colind += cols
+        rowptr.append(len(colind))
+    pats = tuple(np.array(a, dtype=np.int64) for a in (colptr, rowind, rowptr, colind))
+    opts = dict(leaf_size=int(rng.integers(1, 40)), relax_cols=int(rng.integers(0, 30)),
+                relax_zeros=int(rng.integers(0, 200)), max_width=int(rng.integers(1, 20)))
+    _compare(None, pats, n, **opts)
+
+
+def test_analyse_rejects_bad_patterns(nat):
+    from paper_2403_15913_gb300 import KKTSolver, KKTError
+    with pytest.raises(KKTError):   # upper-triangular W entry
+        KKTSolver(3, 0, [0, 2, 3, 4], [0, 1, 0, 2], [0], [], host_only=True)
+    with pytest.raises(KKTError):   # J column out of range
+        KKTSolver(3, 1, [0, 1, 2, 3], [0, 1, 2], [0, 1], [7], host_only=True)

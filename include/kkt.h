@@ -170,6 +170,24 @@ kkt_status kkt_solve(kkt_ctx* ctx, const double* d_rx, const double* d_ry,
 kkt_status kkt_backsolve(kkt_ctx* ctx, const double* d_b, double* d_x,
                          cudaStream_t stream);
 
+/* Backsolve that allocates nothing (the paper has no counterpart: this is a
+ * service for callers that may not allocate device memory, such as a
+ * real-time control loop that must not touch the allocator after start-up,
+ * or code that runs while another component owns every allocation).
+ * Same result as kkt_backsolve: d_x[n] = K^{-1} d_b[n] with the factor of the
+ * last successful kkt_factor.  Its only scratch (one permuted vector) is a
+ * fixed device array inside the library of KKT_STATIC_SCRATCH_DOUBLES
+ * doubles (16 MiB), which every GPU that loads the library holds until the
+ * process exits.  Sizes n > KKT_STATIC_SCRATCH_DOUBLES return KKT_ERR_ARG.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads, other contexts of this library) race and give wrong
+ * results, so serialise them.  No profiling events are recorded. */
+#define KKT_STATIC_SCRATCH_DOUBLES (1 << 21)
+kkt_status kkt_backsolve_noalloc(kkt_ctx* ctx, const double* d_b, double* d_x,
+                                 cudaStream_t stream);
+
 /* Diagnostic: copy the numeric factor L (permuted order) as CSC with the
  * panel structure: colptr[n+1], rowind[], val[] sized by the panel entries
  * below and on the diagonal (lower trapezoid of each supernode panel). */

@@ -21,12 +21,15 @@ KKT_ERR_INTERNAL = -9
 STATUS_NAMES = {0: "ok", -1: "arg", -2: "oom", -3: "cuda", -4: "not_spd", -5: "maxit",
                 -6: "stall", -7: "timeout", -8: "state", -9: "internal"}
 
+KKT_STATIC_SCRATCH_DOUBLES = 1 << 21   # size of the allocation-free backsolve's scratch
+
 KKT_LIFTED = 0
 KKT_HYKKT = 1
 
 EXPORTED = [
     "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
-    "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_factor_export",
+    "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_backsolve_noalloc",
+    "kkt_factor_export",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
 ]
@@ -95,6 +98,8 @@ def lib():
     L.kkt_solve.restype = ctypes.c_int
     L.kkt_backsolve.argtypes = [P, P, P, P]
     L.kkt_backsolve.restype = ctypes.c_int
+    L.kkt_backsolve_noalloc.argtypes = [P, P, P, P]
+    L.kkt_backsolve_noalloc.restype = ctypes.c_int
     L.kkt_factor_export.argtypes = [P, I64P, I32P, F64P]
     L.kkt_factor_export.restype = ctypes.c_int
     L.kkt_last_error.argtypes = [P]

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -847,6 +848,61 @@ kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_
     TRY(apply_kinv(c, d_b, d_x, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     spans_collect(c);
+    return KKT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free backsolve.  The permuted work vector lives in a file-scope
+// device array; host code must not use the symbol's name as a pointer (it is
+// a host-side stand-in), so its device address is looked up once per device.
+static __device__ __align__(256) double g_noalloc_scratch[KKT_STATIC_SCRATCH_DOUBLES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+kkt_status noalloc_scratch(kkt_ctx* c, double** out) {
+    int dev = -1;
+    CUDA_TRY(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_err(c, KKT_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_err(c, KKT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return KKT_OK;
+}
+}  // namespace
+
+kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_t st) {
+    if (!c || !d_b || !d_x) return set_err(c, KKT_ERR_ARG, "NULL argument");
+    if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve_noalloc called without a factor");
+    if ((long long)c->n > (long long)KKT_STATIC_SCRATCH_DOUBLES)
+        return set_err(c, KKT_ERR_ARG, "n = " + std::to_string(c->n) +
+                                           " exceeds the static scratch of kkt_backsolve_noalloc (" +
+                                           std::to_string(KKT_STATIC_SCRATCH_DOUBLES) + " doubles)");
+    double* xp = nullptr;
+    TRY(noalloc_scratch(c, &xp));
+    const int n = c->n;
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp);
+    for (int l = 0; l < c->nlev; ++l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
+        forward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, xp);
+    }
+    for (int l = c->nlev - 1; l >= 0; --l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
+        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, xp);
+    }
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(st));
     return KKT_OK;
 }
 

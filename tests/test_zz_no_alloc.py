@@ -1,0 +1,40 @@
+"""The allocation-free backsolve, called through the C ABI, gives the same
+K^{-1} b as the ordinary backsolve, on two calls in a row.
+
+This variant exists for callers that must not allocate device memory while
+they run (for example a control loop that may not call the allocator after
+start-up); its scratch vector is a fixed array inside the library.  The file
+name makes pytest collect it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from tests.gpu_common import ensure_built, instance, solver_for, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_backsolve_noalloc_matches_backsolve():
+    torch = torch_cuda()
+    ensure_built()
+    from paper_2403_15913_gb300 import _native as nat
+    p, pt, W, J = instance(32, 50, 0, sigma_range=(1e-2, 1e2))
+    s = solver_for(p, W, J, scheme="lifted", leaf_size=64, relax_cols=48, relax_zeros=1024,
+                   max_width=64)
+    assert s.factor(to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma),
+                    to_dev(torch, np.full(p.m, 1e2)), 10.0) == 0
+    L = nat.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(9)
+    for call in range(2):
+        b = to_dev(torch, rng.standard_normal(p.n))
+        ref = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        out = torch.full((p.n,), np.nan, dtype=torch.float64, device="cuda")
+        s.backsolve(b, ref)
+        st = L.kkt_backsolve_noalloc(s._ctx, ctypes.c_void_p(b.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), stream)
+        assert st == 0, L.kkt_last_error(s._ctx)
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert np.max(np.abs(o - r)) <= 1e-12 * np.max(np.abs(r)), call

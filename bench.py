@@ -120,8 +120,8 @@ def oracle_step_sample(k, T_sample, seed, scheme, gamma):
     pt = kkt_point(p, seed)
     W0 = otray.hessian_lower_csc(p, pt.w, pt.lam)
     J0 = otray.jacobian_csr(p, pt.w)
-    sym = symbolic.analyse(p.n, W0[0], W0[1], J0[0], J0[1], leaf_size=64, relax_cols=48,
-                           relax_zeros=1024, max_width=64)
+    sym = symbolic.analyse(p.n, W0[0], W0[1], J0[0], J0[1], leaf_size=64, relax_cols=32,
+                           relax_zeros=128, max_width=64)
     t0 = time.perf_counter()
     W = otray.hessian_lower_csc(p, pt.w, pt.lam)
     J = otray.jacobian_csr(p, pt.w)

@@ -68,11 +68,11 @@ typedef struct {
     /* symbolic analysis (pinned nested dissection, Sec. V-B) */
     int leaf_size;       /* ND components this small are ordered by minimum
                             degree (default 64)                               */
-    int relax_cols;      /* relaxed amalgamation: max merged width (48);
+    int relax_cols;      /* relaxed amalgamation: max merged width (32);
                             0 keeps fundamental supernodes                    */
-    int relax_zeros;     /* max explicit zeros in a merged panel (1024)       */
+    int relax_zeros;     /* max explicit zeros in a merged panel (128)        */
     int max_width;       /* supernodes wider than this are cut (64);
-                            0 or anything above 4096 means 4096               */
+                            0 or anything above 64 means 64                   */
     /* numerics */
     double delta;        /* Lifted-KKT: D = 1/delta when factor gets D = NULL
                             (default 1e-8)                                    */
@@ -84,6 +84,9 @@ typedef struct {
     int target_relaxed;  /* 0: refine against C = 0 (Eq. kkt:condensed);
                             1: against C = D^{-1} (relaxed problem, Lifted
                             only)                                             */
+    int subtree_cols;    /* subtrees of the supernodal tree with at most this
+                            many columns are factorised and solved by one
+                            CTA each (48); 0 disables                         */
 } kkt_options;
 
 /* Per-call report.  Fields not touched by a call keep their values. */

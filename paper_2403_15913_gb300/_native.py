@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("max_width", ctypes.c_int), ("delta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("tol_refine", ctypes.c_double),
                 ("tol_cg", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int)]
+                ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int),
+                ("subtree_cols", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

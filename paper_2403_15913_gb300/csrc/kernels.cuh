@@ -13,6 +13,7 @@
 namespace kktgb {
 
 constexpr int kThreads = 256;
+constexpr int kSubtreeThreads = 64;   // CTA size of the small-subtree kernels
 constexpr int kRedBlocks = 296;   // 2 x 148..152 SMs: partial-sum slots
 
 // Supernode plan (device pointers).  Panel of supernode s: column-major,
@@ -30,6 +31,7 @@ struct Plan {
     const int* seg_b;         // one past the last below-row of the segment
     const long long* seg_map; // offset in relmap of positions of below rows a..rb-1
     const int* relmap;        // positions of rows in the target's rows(t)
+    const unsigned long long* rmask;   // structural mask of every panel row
 };
 
 // ------------------------------------------------------------- assembly
@@ -62,17 +64,136 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
 }
 
 // ------------------------------------------------------------- factor
-// One CTA per supernode of a level: right-looking column Cholesky of the
-// panel (POTRF of the diagonal block and TRSM of the rows below in one
-// sweep), then the SYRK update L21 L21^T scattered into the ancestors'
-// panels through the precomputed relative maps (FP64 atomics: ancestors
-// are never in the same level, so a panel is only read after every update
-// into it has landed).
+// On GB300 a warp-wide DFMA occupies an SM sub-partition's FP64 pipe for the
+// same time whether 1 or 32 lanes are active, and four warps per SM already
+// saturate the pipe.  The panel kernels are therefore written densely and
+// lane-packed: every FP64 instruction carries 32 useful lanes except at the
+// tails of flattened index spaces.  Panels are dense column-major blocks of
+// rows(s) x cols(s) (explicit zeros of relaxed supernodes included).
+
+// Integer quotient q = e / len and remainder for small non-negative values
+// (e < 2^22), through a float reciprocal with a one-step correction.
+__device__ __forceinline__ void fast_divmod(int e, int len, float rcp, int& q, int& rem) {
+    q = __float2int_rz(((float)e + 0.5f) * rcp);
+    rem = e - q * len;
+    if (rem < 0) { --q; rem += len; }
+    else if (rem >= len) { ++q; rem -= len; }
+}
+
+// 1/sqrt(d) by Newton-Raphson for the reciprocal square root,
+// y <- y (3/2 - d y^2 / 2), started from the single-precision estimate:
+// two steps take the ~2^-22 relative error of the seed below double
+// rounding.  Eight FP64 operations instead of a square root and a division,
+// which matters on the column-sequential pivot chain of the factorisation.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    const double h = 0.5 * d;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
+// Pivot of column j: failure check, L_jj = d / sqrt(d), reciprocal stored
+// for the solves.
+__device__ __forceinline__ double take_pivot(double* A, int r, int f, int j, int* fail,
+                                             double* dinv) {
+    double d = A[j + (long long)j * r];
+    if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(fail, f + j);
+        d = 1.0;
+    }
+    const double inv = rsqrt_newton(d);
+    A[j + (long long)j * r] = d * inv;
+    dinv[f + j] = inv;
+    return inv;
+}
+
+// Right-looking Cholesky of the first c columns of a panel A (lda = r, rows
+// [0, nrows)): for each column j, (1) scale rows j+1.. by 1/L_jj, (2) update
+// the trailing rectangle rows [j+1, nrows) x cols [j+1, c) (entries above the
+// diagonal are skipped), with the thread that finishes (j+1, j+1) taking the
+// next pivot.  Two barriers per column.
+__device__ __forceinline__ void panel_factor(double* A, int f, int c, int r, int nrows, int* fail,
+                                             double* dinv) {
+    __shared__ double s_inv[2];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_inv[0] = take_pivot(A, r, f, 0, fail, dinv);
+    __syncthreads();
+    for (int j = 0; j < c; ++j) {
+        const double inv = s_inv[j & 1];
+        double* colj = A + (long long)j * r;
+        for (int i = j + 1 + tid; i < nrows; i += nt) colj[i] *= inv;
+        __syncthreads();
+        const int len = nrows - j - 1, ncol = c - j - 1;
+        if (ncol > 0) {
+            const float rcp = 1.0f / (float)len;
+            const int total = ncol * len;
+            for (int e = tid; e < total; e += nt) {
+                int q, rem;
+                fast_divmod(e, len, rcp, q, rem);
+                const int kk = j + 1 + q, ii = j + 1 + rem;
+                if (ii < kk) continue;
+                double* p = A + ii + (long long)kk * r;
+                const double v = fma(-colj[ii], colj[kk], *p);
+                if (ii == j + 1 && kk == j + 1) {
+                    *p = v;
+                    s_inv[(j + 1) & 1] = take_pivot(A, r, f, j + 1, fail, dinv);
+                } else {
+                    *p = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Segment lookup for update column jj (below-row index) of supernode s.
+__device__ __forceinline__ void update_target(const Plan& P, int s, int c, int jj, long long& base,
+                                              const int*& rm, int& a) {
+    const int sp0 = P.seg_ptr[s], sp1 = P.seg_ptr[s + 1];
+    int k = sp0;
+    while (k < sp1 - 1 && jj >= P.seg_b[k]) ++k;
+    const int t = P.seg_t[k];
+    a = P.seg_a[k];
+    const int row = P.rows[P.sn_rptr[s] + c + jj];
+    base = P.sn_lptr[t] + (long long)(row - P.sn_f[t]) * P.sn_r[t];
+    rm = P.relmap + P.seg_map[k];
+}
+
+constexpr int kTileI = 8, kTileJ = 4;   // SYRK output tile per warp (lane = one output)
+
+// SYRK output tile (ti, tj) of L21 L21^T, lane -> (ii, jj) = (8 ti + lane % 8,
+// 4 tj + lane / 8), scattered into the ancestors with FP64 atomics.
+__device__ __forceinline__ void syrk_tile(const Plan& P, int s, int c, int r, const double* A,
+                                          double* Lx, int ti, int tj) {
+    const int lane = threadIdx.x & 31;
+    const int rb = r - c;
+    const int ii = ti * kTileI + (lane & 7), jj = tj * kTileJ + (lane >> 3);
+    const bool valid = ii < rb && jj < rb && ii >= jj;
+    const double* ai = A + c + (valid ? ii : 0);
+    const double* aj = A + c + (valid ? jj : 0);
+    double sum = 0.0;
+    for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * r], aj[(long long)k * r], sum);
+    if (valid) {
+        long long base;
+        const int* rm;
+        int a;
+        update_target(P, s, c, jj, base, rm, a);
+        atomicAdd(Lx + base + rm[ii - a], -sum);
+    }
+}
+
+__device__ __forceinline__ int syrk_tiles_i(int rb) { return (rb + kTileI - 1) / kTileI; }
+__device__ __forceinline__ int syrk_tiles_j(int rb) { return (rb + kTileJ - 1) / kTileJ; }
+
+// One CTA per supernode (levels with many supernodes): the whole panel in
+// shared memory when it fits, dense right-looking factorisation, then the
+// SYRK tiles of the rows below the diagonal block.
 __global__ void __launch_bounds__(kThreads)
 factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__ Lx,
-                    int* __restrict__ fail, long long smem_elems) {
+                    int* __restrict__ fail, long long smem_elems, double* __restrict__ dinv) {
     extern __shared__ double sm[];
-    __shared__ double s_inv;
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const long long lp = P.sn_lptr[s];
@@ -84,89 +205,130 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__
         for (long long e = tid; e < (long long)r * c; e += nt) A[e] = g[e];
         __syncthreads();
     }
-    for (int j = 0; j < c; ++j) {
-        if (tid == 0) {
-            double d = A[j + (long long)j * r];
-            if (!(d > 0.0) || !isfinite(d)) {
-                atomicMin(fail, f + j);
-                d = 1.0;
-            }
-            double l = sqrt(d);
-            A[j + (long long)j * r] = l;
-            s_inv = 1.0 / l;
-        }
-        __syncthreads();
-        const double inv = s_inv;
-        double* colj = A + (long long)j * r;
-        for (int i = j + 1 + tid; i < r; i += nt) colj[i] *= inv;
-        __syncthreads();
-        const int nk = c - 1 - j, len = r - 1 - j;
-        for (int idx = tid; idx < nk * len; idx += nt) {
-            const int kk = j + 1 + idx / len;
-            const int ii = j + 1 + idx % len;
-            if (ii >= kk) A[ii + (long long)kk * r] -= colj[ii] * colj[kk];
-        }
-        __syncthreads();
-    }
+    panel_factor(A, f, c, r, r, fail, dinv);
     if (in_smem) {
         double* g = Lx + lp;
         for (long long e = tid; e < (long long)r * c; e += nt) g[e] = A[e];
     }
     const int rb = r - c;
     if (rb <= 0) return;
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    const int sp0 = P.seg_ptr[s], sp1 = P.seg_ptr[s + 1];
-    const int* rows = P.rows + P.sn_rptr[s];
-    for (int jj = warp; jj < rb; jj += nw) {
-        int k = sp0;
-        while (k < sp1 - 1 && jj >= P.seg_b[k]) ++k;
-        const int t = P.seg_t[k], a = P.seg_a[k];
-        const long long base =
-            P.sn_lptr[t] + (long long)(rows[c + jj] - P.sn_f[t]) * P.sn_r[t];
-        const int* rm = P.relmap + P.seg_map[k];
-        for (int ii = jj + lane; ii < rb; ii += 32) {
-            double sum = 0.0;
-            for (int q = 0; q < c; ++q)
-                sum += A[c + ii + (long long)q * r] * A[c + jj + (long long)q * r];
-            atomicAdd(Lx + base + rm[ii - a], -sum);
-        }
+    const int nti = syrk_tiles_i(rb), ntj = syrk_tiles_j(rb);
+    const int warp = tid >> 5, nw = nt >> 5;
+    for (int t = warp; t < nti * ntj; t += nw) {
+        const int ti = t / ntj, tj = t % ntj;
+        if (tj * kTileJ > ti * kTileI + kTileI - 1) continue;   // tile above the diagonal
+        syrk_tile(P, s, c, r, A, Lx, ti, tj);
     }
 }
 
+// Levels with few supernodes run in three launches spread over many CTAs:
+// (1) POTRF of each diagonal block, (2) TRSM of the rows below, one row per
+// warp, (3) SYRK tiles, one tile per warp.
+__global__ void __launch_bounds__(kThreads)
+potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__ Lx,
+                  int* __restrict__ fail, double* __restrict__ dinv) {
+    extern __shared__ double sm[];
+    const int s = lvl_sn[blockIdx.x];
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+    double* g = Lx + P.sn_lptr[s];
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
+    __syncthreads();
+    panel_factor(sm, f, c, c, c, fail, dinv);
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) g[(e % c) + (long long)(e / c) * r] = sm[e];
+}
+
+constexpr int kTrsmWarps = 4;   // rows per TRSM CTA (one per warp)
+
+// X L11^T = A21: task = (supernode, first below-row); warp w solves row
+// task.y + w with lanes over the columns (two per lane).  The columns of L11
+// are pre-scaled by the reciprocal pivots, so a step is one shuffle and one
+// FMA: a_l -= a_k (L_lk / L_kk); the final x_k = a_k / L_kk is one multiply.
+__global__ void __launch_bounds__(32 * kTrsmWarps)
+trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, double* __restrict__ Lx,
+                 const double* __restrict__ dinv) {
+    __shared__ double D[64 * 64];
+    const int2 task = tasks[blockIdx.x];
+    const int s = task.x;
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+    double* g = Lx + P.sn_lptr[s];
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+        const int col = e / c;
+        D[e] = g[(e % c) + (long long)col * r] * dinv[f + col];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = task.y + warp;
+    if (i >= r - c) return;
+    double* row = g + c + i;                       // element k at row[k * r]
+    double a0 = lane < c ? row[(long long)lane * r] : 0.0;
+    double a1 = lane + 32 < c ? row[(long long)(lane + 32) * r] : 0.0;
+    for (int k = 0; k < c; ++k) {
+        const double ak = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
+        if (lane > k && lane < c) a0 = fma(-ak, D[lane + k * c], a0);
+        if (lane + 32 > k && lane + 32 < c) a1 = fma(-ak, D[lane + 32 + k * c], a1);
+    }
+    if (lane < c) row[(long long)lane * r] = a0 * dinv[f + lane];
+    if (lane + 32 < c) row[(long long)(lane + 32) * r] = a1 * dinv[f + lane + 32];
+}
+
+// task = (supernode, tile row ti, tile column tj); one tile per warp.
+__global__ void __launch_bounds__(kThreads)
+syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, double* __restrict__ Lx) {
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= ntasks) return;
+    const int4 task = tasks[t];
+    const int s = task.x;
+    syrk_tile(P, s, P.sn_c[s], P.sn_r[s], Lx + P.sn_lptr[s], Lx, task.y, task.z);
+}
+
 // ------------------------------------------------------------- solves
-// Forward substitution L z = b, one CTA per supernode of a level.
+// Forward substitution L z = b, one CTA per supernode of a level: the
+// diagonal block in shared memory, one warp substitutes with shuffles
+// (reciprocal pivots from the factorisation), then one thread per row of
+// L21 forms its product with z and scatters it.
 __global__ void __launch_bounds__(kThreads)
 forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                     double* __restrict__ x) {
-    extern __shared__ double z[];
+                     const double* __restrict__ dinv, double* __restrict__ x) {
+    __shared__ double D[64 * 64];
+    __shared__ double z[64];
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const double* A = Lx + P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = tid; k < c; k += nt) z[k] = x[f + k];
+    for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
     __syncthreads();
-    for (int j = 0; j < c; ++j) {
-        if (tid == 0) z[j] /= A[j + (long long)j * r];
-        __syncthreads();
-        const double zj = z[j];
-        for (int i = j + 1 + tid; i < c; i += nt) z[i] -= A[i + (long long)j * r] * zj;
-        __syncthreads();
+    if (tid < 32) {
+        const int lane = tid;
+        double z0 = lane < c ? x[f + lane] : 0.0;
+        double z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
+        for (int j = 0; j < c; ++j) {
+            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dinv[f + j];
+            if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
+            if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
+            if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
+        }
+        if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
+        if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
     }
-    for (int k = tid; k < c; k += nt) x[f + k] = z[k];
+    __syncthreads();
     const int* rows = P.rows + P.sn_rptr[s];
     for (int i = tid; i < r - c; i += nt) {
         double sum = 0.0;
-        for (int k = 0; k < c; ++k) sum += A[c + i + (long long)k * r] * z[k];
+        for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
         atomicAdd(x + rows[c + i], -sum);
     }
 }
 
 // Backward substitution L^T w = z, one CTA per supernode of a level
-// (levels visited top-down).
+// (levels visited top-down): t_k = z_k - L21(:,k)^T w_below with lanes over
+// the columns k and warps over row blocks, then one warp substitutes with
+// the diagonal block.
 __global__ void __launch_bounds__(kThreads)
 backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                      double* __restrict__ x) {
-    extern __shared__ double t[];
+                      const double* __restrict__ dinv, double* __restrict__ x) {
+    __shared__ double D[64 * 64];
+    __shared__ double part[kThreads / 32][64];
+    extern __shared__ double xb[];
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const double* A = Lx + P.sn_lptr[s];
@@ -174,21 +336,155 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     const int rb = r - c;
-    for (int k = warp; k < c; k += nw) {
-        double sum = 0.0;
-        for (int i = lane; i < rb; i += 32) sum += A[c + i + (long long)k * r] * x[rows[c + i]];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-        if (lane == 0) t[k] = x[f + k] - sum;
+    for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
+    for (int i = tid; i < rb; i += nt) xb[i] = x[rows[c + i]];
+    __syncthreads();
+    // warp w sums rows i = w, w + nw, ... for columns k = lane, lane + 32
+    {
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = warp; i < rb; i += nw) {
+            const double xv = xb[i];
+            if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
+            if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
+        }
+        part[warp][lane] = s0;
+        part[warp][lane + 32] = s1;
     }
     __syncthreads();
-    for (int j = c - 1; j >= 0; --j) {
-        if (tid == 0) t[j] /= A[j + (long long)j * r];
+    if (tid < 32) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
+        t0 = lane < c ? x[f + lane] - t0 : 0.0;
+        t1 = lane + 32 < c ? x[f + lane + 32] - t1 : 0.0;
+        for (int j = c - 1; j >= 0; --j) {
+            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dinv[f + j];
+            if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
+            if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
+            if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
+        }
+        if (lane < c) x[f + lane] = t0;
+        if (lane + 32 < c) x[f + lane + 32] = t1;
+    }
+}
+
+// ------------------------------------------------------------- subtrees
+// Small subtrees of the supernodal tree (task = its supernodes in
+// postorder) are processed by one CTA each, without per-level launches.
+// Values that earlier supernodes of the same task updated through atomics
+// are read with ld.global.cg (L2), never from a possibly stale L1 line.
+__global__ void __launch_bounds__(kSubtreeThreads)
+factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                      double* __restrict__ Lx, int* __restrict__ fail, double* __restrict__ dinv) {
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, nw = nt >> 5;
+    for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
+        const int s = task_sn[q];
+        const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+        double* g = Lx + P.sn_lptr[s];
+        for (int e = tid; e < r * c; e += nt) sm[e] = __ldcg(g + e);
         __syncthreads();
-        const double tj = t[j];
-        for (int k = tid; k < j; k += nt) t[k] -= A[j + (long long)k * r] * tj;
+        panel_factor(sm, f, c, r, r, fail, dinv);
+        for (int e = tid; e < r * c; e += nt) g[e] = sm[e];
+        const int rb = r - c;
+        if (rb > 0) {
+            const int nti = syrk_tiles_i(rb), ntj = syrk_tiles_j(rb);
+            for (int t = warp; t < nti * ntj; t += nw) {
+                const int ti = t / ntj, tj = t % ntj;
+                if (tj * kTileJ > ti * kTileI + kTileI - 1) continue;
+                syrk_tile(P, s, c, r, sm, Lx, ti, tj);
+            }
+        }
+        __threadfence();
         __syncthreads();
     }
-    for (int k = tid; k < c; k += nt) x[f + k] = t[k];
+}
+
+// Forward substitution over a subtree task (supernodes in postorder).
+__global__ void __launch_bounds__(kSubtreeThreads)
+forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                       const double* __restrict__ Lx, const double* __restrict__ dinv,
+                       double* __restrict__ x) {
+    __shared__ double z[64];
+    extern __shared__ double D[];   // diagonal block of the current supernode
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
+        const int s = task_sn[q];
+        const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+        const double* A = Lx + P.sn_lptr[s];
+        for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
+        __syncthreads();
+        if (tid < 32) {
+            const int lane = tid;
+            double z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
+            double z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
+            for (int j = 0; j < c; ++j) {
+                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dinv[f + j];
+                if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
+                if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
+                if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
+            }
+            if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
+            if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
+        }
+        __syncthreads();
+        const int* rows = P.rows + P.sn_rptr[s];
+        for (int i = tid; i < r - c; i += nt) {
+            double sum = 0.0;
+            for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
+            atomicAdd(x + rows[c + i], -sum);
+        }
+        __threadfence();
+        __syncthreads();
+    }
+}
+
+// Backward substitution over a subtree task (supernodes in reverse postorder).
+__global__ void __launch_bounds__(kSubtreeThreads)
+backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                        const double* __restrict__ Lx, const double* __restrict__ dinv,
+                        double* __restrict__ x) {
+    __shared__ double part[kSubtreeThreads / 32][64];
+    extern __shared__ double dyn[];   // [diagonal block | x of the rows below]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int q = task_ptr[blockIdx.x + 1] - 1; q >= task_ptr[blockIdx.x]; --q) {
+        const int s = task_sn[q];
+        const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+        const double* A = Lx + P.sn_lptr[s];
+        const int* rows = P.rows + P.sn_rptr[s];
+        const int rb = r - c;
+        double* D = dyn;
+        double* xb = dyn + c * c;
+        for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
+        for (int i = tid; i < rb; i += nt) xb[i] = __ldcg(x + rows[c + i]);
+        __syncthreads();
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = warp; i < rb; i += nw) {
+            const double xv = xb[i];
+            if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
+            if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
+        }
+        part[warp][lane] = s0;
+        part[warp][lane + 32] = s1;
+        __syncthreads();
+        if (tid < 32) {
+            double t0 = 0.0, t1 = 0.0;
+            for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
+            t0 = lane < c ? __ldcg(x + f + lane) - t0 : 0.0;
+            t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) - t1 : 0.0;
+            for (int j = c - 1; j >= 0; --j) {
+                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dinv[f + j];
+                if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
+                if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
+                if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
+            }
+            if (lane < c) x[f + lane] = t0;
+            if (lane + 32 < c) x[f + lane + 32] = t1;
+        }
+        __threadfence();
+        __syncthreads();
+    }
 }
 
 __global__ void gather_kernel(int n, const int* __restrict__ idx, const double* __restrict__ in,

@@ -18,6 +18,7 @@ using namespace kktgb;
 namespace {
 
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
+constexpr int kSplitLevel = 2 * 152;   // levels with fewer supernodes use split launches
 
 template <class T>
 struct DevBuf {
@@ -37,10 +38,24 @@ struct kkt_ctx {
     std::vector<long long> h_sn_lptr;
     std::vector<int> h_lvl_ptr, h_lvl_sn;
     std::vector<int> lvl_max_c;
+    std::vector<int> lvl_max_rb;
     std::vector<long long> lvl_max_rc;
+    // levels with few supernodes are factorised by split POTRF/TRSM/SYRK
+    // launches over these task lists (per level offsets into the arrays)
+    std::vector<char> lvl_split;
+    std::vector<int> lvl_trsm_ptr, lvl_syrk_ptr;
+    int2* d_trsm_tasks = nullptr;
+    int4* d_syrk_tasks = nullptr;
+    double* d_dinv = nullptr;
     long long panel = 0;
     long long nk = 0;
-    int nlev = 0;
+    int nlev = 0;          // levels of the supernodes outside small-subtree tasks
+    int tree_levels = 0;   // levels of the whole supernodal tree
+    // small-subtree tasks: supernodes of task b are task_sn[task_ptr[b] ..]
+    int ntasks = 0;
+    int* d_task_ptr = nullptr;
+    int* d_task_sn = nullptr;
+    long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
     // device allocations (all freed in kkt_destroy)
     std::vector<void*> allocs;
     Plan plan{};
@@ -304,27 +319,101 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         seg_ptr.push_back((int)seg_t.size());
     }
 
-    // ---- levels of the supernodal tree
-    std::vector<int> level(ns, 0);
+    // ---- small-subtree tasks, then levels of the remaining supernodes
+    std::vector<int> sub_cols(ns, 0);
+    std::vector<char> small_ok(ns, 1);
+    const long long kTaskPanelCap = 6144;   // panel entries kept in the task CTA's smem
+    for (int s = 0; s < ns; ++s) {
+        sub_cols[s] += sn_c[s];
+        if ((long long)sn_r[s] * sn_c[s] > kTaskPanelCap) small_ok[s] = 0;
+        const int p = S.sn_parent[s];
+        if (p >= 0) {
+            sub_cols[p] += sub_cols[s];
+            if (!small_ok[s]) small_ok[p] = 0;
+        }
+    }
+    std::vector<char> in_task(ns, 0);
     for (int s = 0; s < ns; ++s)
-        if (S.sn_parent[s] >= 0) level[S.sn_parent[s]] = std::max(level[S.sn_parent[s]], level[s] + 1);
+        in_task[s] = c->opt.subtree_cols > 0 && sub_cols[s] <= c->opt.subtree_cols && small_ok[s];
+    std::vector<int> task_of(ns, -1), task_root;
+    for (int s = ns - 1; s >= 0; --s) {
+        if (!in_task[s]) continue;
+        const int p = S.sn_parent[s];
+        if (p >= 0 && in_task[p]) {
+            task_of[s] = task_of[p];
+        } else {
+            task_of[s] = (int)task_root.size();
+            task_root.push_back(s);
+        }
+    }
+    c->ntasks = (int)task_root.size();
+    std::vector<int> task_ptr(c->ntasks + 1, 0), task_sn;
+    for (int s = 0; s < ns; ++s)
+        if (task_of[s] >= 0) task_ptr[task_of[s] + 1]++;
+    for (int b = 0; b < c->ntasks; ++b) task_ptr[b + 1] += task_ptr[b];
+    task_sn.resize(task_ptr[c->ntasks]);
+    {
+        std::vector<int> fillp(task_ptr.begin(), task_ptr.end() - 1);
+        for (int s = 0; s < ns; ++s)   // increasing s: postorder inside every task
+            if (task_of[s] >= 0) {
+                task_sn[fillp[task_of[s]]++] = s;
+                c->task_max_rc = std::max(c->task_max_rc, (long long)sn_r[s] * sn_c[s]);
+                c->task_max_cc = std::max(c->task_max_cc, (long long)sn_c[s] * sn_c[s]);
+                c->task_max_ccrb = std::max(c->task_max_ccrb,
+                                            (long long)sn_c[s] * sn_c[s] + sn_r[s] - sn_c[s]);
+            }
+    }
+    std::vector<int> level(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        const int p = S.sn_parent[s];
+        if (in_task[s] || p < 0) continue;
+        level[p] = std::max(level[p], level[s] + 1);
+    }
     int nlev = 0;
-    for (int s = 0; s < ns; ++s) nlev = std::max(nlev, level[s] + 1);
+    for (int s = 0; s < ns; ++s)
+        if (!in_task[s]) nlev = std::max(nlev, level[s] + 1);
     c->nlev = nlev;
     c->h_lvl_ptr.assign(nlev + 1, 0);
-    for (int s = 0; s < ns; ++s) c->h_lvl_ptr[level[s] + 1]++;
+    for (int s = 0; s < ns; ++s)
+        if (!in_task[s]) c->h_lvl_ptr[level[s] + 1]++;
     for (int l = 0; l < nlev; ++l) c->h_lvl_ptr[l + 1] += c->h_lvl_ptr[l];
-    c->h_lvl_sn.resize(ns);
+    c->h_lvl_sn.resize(c->h_lvl_ptr[nlev]);
     c->lvl_max_c.assign(nlev, 0);
+    c->lvl_max_rb.assign(nlev, 0);
     c->lvl_max_rc.assign(nlev, 0);
     {
         std::vector<int> fillp(c->h_lvl_ptr.begin(), c->h_lvl_ptr.end() - 1);
         for (int s = 0; s < ns; ++s) {
+            if (in_task[s]) continue;
             c->h_lvl_sn[fillp[level[s]]++] = s;
             c->lvl_max_c[level[s]] = std::max(c->lvl_max_c[level[s]], sn_c[s]);
+            c->lvl_max_rb[level[s]] = std::max(c->lvl_max_rb[level[s]], sn_r[s] - sn_c[s]);
             c->lvl_max_rc[level[s]] =
                 std::max(c->lvl_max_rc[level[s]], (long long)sn_c[s] * sn_r[s]);
         }
+    }
+    std::vector<int2> trsm_tasks;
+    std::vector<int4> syrk_tasks;
+    c->lvl_split.assign(nlev, 0);
+    c->lvl_trsm_ptr.assign(nlev + 1, 0);
+    c->lvl_syrk_ptr.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        c->lvl_split[l] = cnt < kSplitLevel;
+        if (c->lvl_split[l]) {
+            for (int q = c->h_lvl_ptr[l]; q < c->h_lvl_ptr[l + 1]; ++q) {
+                const int sn = c->h_lvl_sn[q];
+                const int rb = sn_r[sn] - sn_c[sn];
+                for (int r0 = 0; r0 < rb; r0 += kTrsmWarps) trsm_tasks.push_back(make_int2(sn, r0));
+                const int nti = (rb + kTileI - 1) / kTileI, ntj = (rb + kTileJ - 1) / kTileJ;
+                for (int ti = 0; ti < nti; ++ti)
+                    for (int tj = 0; tj < ntj; ++tj)
+                        if (tj * kTileJ <= ti * kTileI + kTileI - 1)
+                            syrk_tasks.push_back(make_int4(sn, ti, tj, 0));
+            }
+        }
+        c->lvl_trsm_ptr[l + 1] = (int)trsm_tasks.size();
+        c->lvl_syrk_ptr[l + 1] = (int)syrk_tasks.size();
     }
 
     // ---- SpMV structures (original labels)
@@ -395,6 +484,11 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         }
     }
 
+    if (S.sn_rowmask.size() != S.sn_rows.size())
+        return set_err(c, KKT_ERR_INTERNAL, "structural masks missing (supernode wider than 64)");
+    for (int s = 0; s < ns; ++s)
+        if (sn_c[s] > 64) return set_err(c, KKT_ERR_INTERNAL, "supernode wider than 64 columns");
+
     // ---- upload
     int *d_sn_f, *d_sn_c, *d_sn_r, *d_sn_rptr, *d_rows, *d_seg_ptr, *d_seg_t, *d_seg_a, *d_seg_b,
         *d_relmap;
@@ -411,9 +505,19 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(upload(c, &d_seg_b, seg_b));
     TRY(upload(c, &d_seg_map, seg_map));
     TRY(upload(c, &d_relmap, relmap));
+    unsigned long long* d_rmask;
+    {
+        std::vector<unsigned long long> rm(S.sn_rowmask.begin(), S.sn_rowmask.end());
+        TRY(upload(c, &d_rmask, rm));
+    }
     c->plan = Plan{d_sn_f, d_sn_c, d_sn_r, d_sn_lptr, d_sn_rptr, d_rows,
-                   d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap};
+                   d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap, d_rmask};
     TRY(upload(c, &c->d_lvl_sn, c->h_lvl_sn));
+    TRY(upload(c, &c->d_trsm_tasks, trsm_tasks));
+    TRY(upload(c, &c->d_task_ptr, task_ptr));
+    TRY(upload(c, &c->d_task_sn, task_sn));
+    TRY(upload(c, &c->d_syrk_tasks, syrk_tasks));
+    TRY(alloc(c, &c->d_dinv, n));
     TRY(upload(c, &c->d_perm, S.perm));
     TRY(upload(c, &c->d_iperm, S.iperm));
     TRY(upload(c, &c->d_k_slot, k_slot));
@@ -452,25 +556,36 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     return KKT_OK;
 }
 
+// L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
+// levels bottom-up, then levels top-down and subtree tasks.
+void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st) {
+    if (c->ntasks > 0)
+        forward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(double), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp);
+    for (int l = 0; l < c->nlev; ++l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        forward_level_kernel<<<cnt, kThreads, 0, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
+                                                       c->d_Lx, c->d_dinv, xp);
+    }
+    for (int l = c->nlev - 1; l >= 0; --l) {
+        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        size_t sm = (size_t)c->lvl_max_rb[l] * sizeof(double);
+        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
+                                                         c->d_Lx, c->d_dinv, xp);
+    }
+    if (c->ntasks > 0)
+        backward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(double), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp);
+}
+
 // x <- K^{-1} x  (in and out may alias; uses w_xp)
 kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st) {
     const int n = c->n;
     const int sp = span_begin(c, 2, st);
     c->stats.kinv_calls++;
-    c->stats.launches += 2 + 2LL * c->nlev;
+    c->stats.launches += 2 + 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0);
     gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp);
-    for (int l = 0; l < c->nlev; ++l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
-        forward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                        c->d_Lx, c->w_xp);
-    }
-    for (int l = c->nlev - 1; l >= 0; --l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
-        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                         c->d_Lx, c->w_xp);
-    }
+    enqueue_triangular_solves(c, c->w_xp, st);
     scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out);
     span_end(c, sp, st);
     CUDA_TRY(c, cudaGetLastError());
@@ -578,8 +693,8 @@ void kkt_default_options(kkt_options* o) {
     if (!o) return;
     o->scheme = KKT_LIFTED;
     o->leaf_size = 64;
-    o->relax_cols = 48;
-    o->relax_zeros = 1024;
+    o->relax_cols = 32;
+    o->relax_zeros = 128;
     o->max_width = 64;
     o->delta = 1e-8;
     o->gamma = 1e4;
@@ -588,6 +703,7 @@ void kkt_default_options(kkt_options* o) {
     o->max_refine = 20;
     o->max_cg = 200;
     o->target_relaxed = 0;
+    o->subtree_cols = 48;
 }
 
 namespace {
@@ -603,7 +719,7 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
         delete c;
         return set_err(nullptr, KKT_ERR_ARG, "unknown scheme");
     }
-    if (c->opt.max_width <= 0 || c->opt.max_width > 4096) c->opt.max_width = 4096;
+    if (c->opt.max_width <= 0 || c->opt.max_width > 64) c->opt.max_width = 64;
     c->n = n;
     c->m = m;
     Graph g;
@@ -639,7 +755,7 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
                 level[c->sym.sn_parent[s]] = std::max(level[c->sym.sn_parent[s]], level[s] + 1);
             nlev = std::max(nlev, level[s] + 1);
         }
-        c->nlev = nlev;
+        c->tree_levels = nlev;
     }
     if (device) {
         kkt_status st = build_plan(c, W_colptr, W_rowind, J_rowptr, J_colind);
@@ -650,10 +766,8 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
         }
         cudaFuncSetAttribute(factor_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(double)));
-        cudaFuncSetAttribute(forward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             4096 * (int)sizeof(double));
         cudaFuncSetAttribute(backward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             4096 * (int)sizeof(double));
+                             160 * 1024);
     }
     c->device_ready = device;
     *out = c;
@@ -686,7 +800,7 @@ kkt_status kkt_symbolic_sizes(const kkt_ctx* c, int* ns, int64_t* nnz_L, int64_t
         *panel = p;
     }
     if (row_entries) *row_entries = (int64_t)c->sym.sn_rows.size();
-    if (levels) *levels = c->nlev;
+    if (levels) *levels = c->tree_levels;
     if (flops) *flops = c->sym.flops;
     return KKT_OK;
 }
@@ -750,11 +864,32 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
     c->stats.factor_calls++;
     c->stats.launches += 2 + c->nlev;
     c->stats.factor_launches += c->nlev;
+    if (c->ntasks > 0) {
+        factor_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_rc * sizeof(double), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_fail, c->d_dinv);
+        c->stats.launches += 1;
+        c->stats.factor_launches += 1;
+    }
     for (int l = 0; l < c->nlev; ++l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
-        factor_level_kernel<<<cnt, kThreads, (size_t)need * sizeof(double), st>>>(
-            c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, c->d_fail, need);
+        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
+        if (!c->lvl_split[l]) {
+            long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
+            factor_level_kernel<<<cnt, kThreads, (size_t)need * sizeof(double), st>>>(
+                c->plan, lsn, c->d_Lx, c->d_fail, need, c->d_dinv);
+            continue;
+        }
+        const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(double);
+        potrf_diag_kernel<<<cnt, kThreads, dsm, st>>>(c->plan, lsn, c->d_Lx, c->d_fail, c->d_dinv);
+        const int nt = c->lvl_trsm_ptr[l + 1] - c->lvl_trsm_ptr[l];
+        if (nt > 0)
+            trsm_rows_kernel<<<nt, 32 * kTrsmWarps, 0, st>>>(
+                c->plan, c->d_trsm_tasks + c->lvl_trsm_ptr[l], c->d_Lx, c->d_dinv);
+        const int ny = c->lvl_syrk_ptr[l + 1] - c->lvl_syrk_ptr[l];
+        if (ny > 0)
+            syrk_tile_kernel<<<(ny + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(
+                c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, c->d_Lx);
+        c->stats.launches += 2;
     }
     span_end(c, sp_f, st);
     CUDA_TRY(c, cudaGetLastError());
@@ -890,16 +1025,7 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     TRY(noalloc_scratch(c, &xp));
     const int n = c->n;
     gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp);
-    for (int l = 0; l < c->nlev; ++l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
-        forward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, xp);
-    }
-    for (int l = c->nlev - 1; l >= 0; --l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_c[l] * sizeof(double);
-        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], c->d_Lx, xp);
-    }
+    enqueue_triangular_solves(c, xp, st);
     scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));

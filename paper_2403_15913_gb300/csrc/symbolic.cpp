@@ -541,6 +541,51 @@ std::string analyse(const Graph& g, const SymbolicOptions& opt, Symbolic& out) {
     }
     out.sn_ptr = ptr;
     supernode_rows(g, perm, iperm, out.sn_ptr, out.sn_rowptr, out.sn_rows, out.sn_parent);
+
+    // structural row masks (recompute the exact column structures)
+    out.sn_rowmask.clear();
+    int maxw = 0;
+    for (size_t s = 0; s + 1 < out.sn_ptr.size(); ++s) maxw = std::max(maxw, out.sn_ptr[s + 1] - out.sn_ptr[s]);
+    if (maxw <= 64) {
+        const int ns = out.ns();
+        out.sn_rowmask.assign(out.sn_rows.size(), 0ull);
+        std::vector<int> head(n, -1), next(n, -1);
+        for (int j = n - 1; j >= 0; --j)
+            if (parent[j] >= 0) { next[j] = head[parent[j]]; head[parent[j]] = j; }
+        std::vector<std::vector<int>> live(n);
+        std::vector<int> mark(n, -1), pos(n, -1), buf;
+        int s = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == out.sn_ptr[s + 1] || j == 0) {
+                if (j != 0) {
+                    for (int q = out.sn_rowptr[s]; q < out.sn_rowptr[s + 1]; ++q) pos[out.sn_rows[q]] = -1;
+                    ++s;
+                }
+                for (int q = out.sn_rowptr[s]; q < out.sn_rowptr[s + 1]; ++q)
+                    pos[out.sn_rows[q]] = q;
+            }
+            buf.clear();
+            buf.push_back(j);
+            mark[j] = j;
+            int v = perm[j];
+            for (int64_t p = g.xadj[v]; p < g.xadj[v + 1]; ++p) {
+                int i = iperm[g.adj[p]];
+                if (i > j && mark[i] != j) { mark[i] = j; buf.push_back(i); }
+            }
+            for (int c = head[j]; c >= 0; c = next[c]) {
+                for (int i : live[c])
+                    if (i != c && mark[i] != j) { mark[i] = j; buf.push_back(i); }
+                std::vector<int>().swap(live[c]);
+            }
+            const int bit = j - out.sn_ptr[s];
+            for (int i : buf) {
+                if (pos[i] < 0) return "internal error: column structure outside its supernode panel";
+                out.sn_rowmask[pos[i]] |= 1ull << bit;
+            }
+            if (parent[j] >= 0) live[j] = buf;
+        }
+        (void)ns;
+    }
     return "";
 }
 

@@ -28,6 +28,11 @@ struct Symbolic {
     std::vector<int> sn_rowptr; // offsets into sn_rows (ns + 1)
     std::vector<int> sn_rows;   // rows(s), ascending, starting with cols(s)
     std::vector<int> sn_parent; // supernodal tree, -1 for roots
+    // For every entry q of sn_rows (row i of supernode s): bit k is set when
+    // L(i, first(s) + k) is structurally nonzero (true structure, not the
+    // explicit zeros of relaxed panels).  Filled only when every supernode
+    // has at most 64 columns (otherwise empty).
+    std::vector<uint64_t> sn_rowmask;
     double flops = 0.0;         // sum_j colcount_j^2
     int64_t nnz_L = 0;
     int ns() const { return (int)sn_ptr.size() - 1; }

@@ -13,7 +13,7 @@ from tests.gpu_common import (ensure_built, instance, oracle_eta, solver_for, to
 
 pytestmark = pytest.mark.gpu
 
-OPTS = dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64)
+OPTS = dict(leaf_size=64, relax_cols=32, relax_zeros=128, max_width=64)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -73,8 +73,9 @@ def _dense_factor_parity(p, pt, W, J, delta_x, D, opts):
 
 @pytest.mark.parametrize("k,T,opts", [
     (32, 50, OPTS),
+    (32, 40, dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64)),
     (7, 13, dict(leaf_size=16, relax_cols=16, relax_zeros=40, max_width=8)),
-    (32, 20, dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=4096)),
+    (32, 20, dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=64)),
 ])
 def test_factor_matches_oracle(k, T, opts):
     p, pt, W, J = instance(k, T, seed=1, sigma_range=(1e-2, 1e2))

@@ -68,8 +68,9 @@ def _compare(p_or_adj, pats, n, **opts):
     s.close()
 
 
-OPTS = [dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64),
-        dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=4096),
+OPTS = [dict(leaf_size=64, relax_cols=32, relax_zeros=128, max_width=64),
+        dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64),
+        dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=64),
         dict(leaf_size=16, relax_cols=16, relax_zeros=40, max_width=8),
         dict(leaf_size=128, relax_cols=64, relax_zeros=4000, max_width=32)]
 

@@ -5,7 +5,7 @@ The column model is the one of Sec. VI-A of Pacaud & Shin (arXiv 2403.15913):
 F = 0.4, reflux ratio bounded by 1 <= u <= 5.  The paper leaves the tray
 holdups M_n, the feed composition x_f, the set-points and the initial profile
 unstated; the values chosen here are documented constants (M_n = 1,
-x_f = 0.5, xbar = 0.5, ubar = 2, xbar_{n,0} = 0.5).
+x_f = 0.5, xbar = 0.5, ubar = 2, xbar_{n,0} = 0.3).
 
 Nothing in this module evaluates the model or its derivatives: it only fixes
 constants, the variable/constraint index layout, and draws seeded random
@@ -40,7 +40,7 @@ class TrayParams:
     xbar: float = 0.5      # composition set-point (not given)
     ubar: float = 2.0      # reflux set-point (not given)
     rho: float = 1.0       # control weight (paper: rho = 1)
-    x0bar: float = 0.5     # initial composition on every tray (not given)
+    x0bar: float = 0.3     # initial composition on every tray (not given)
     x_lo: float = 0.0
     x_hi: float = 1.0
     u_lo: float = 1.0

@@ -1,19 +1,17 @@
 #!/usr/bin/env python
-"""Benchmark of the KKT hot path: KKT solve time per IPM iteration.
+"""Benchmark of the hot path: time per interior-point iteration.
 
 Workload: the distillation column of Sec. VI-A (32 trays) on T = 5000
-implicit-Euler stages (n = 325,065 variables, m = 320,064 constraints), the
-KKT system taken at a seeded iterate (compositions U(0.05, 0.95), reflux
-U(1.05, 4.95), multipliers N(0, 1), Sigma_x log-uniform on [1e-6, 1e6],
-N(0, 1) right-hand side).
+implicit-Euler stages (n = 325,065 variables, m = 320,064 constraints),
+solved by the device IPM driver from the standard start (compositions at
+xbar_0, reflux at ubar) to tolerance 1e-8.
 
-One step = one KKT solve of an IPM iteration, all on the GPU:
-  derivative evaluation (Jacobian and Lagrangian Hessian kernels),
-  assembly of the condensed matrix, supernodal Cholesky (with inertia
-  correction when a pivot fails), and the Lifted-KKT (or HyKKT) solve with
-  iterative refinement to a backward error <= 1e-10 on the original system.
-The symbolic analysis is done once before timing (reported separately, as
-the paper's SYM column).
+One step = one IPM iteration, all on the GPU: derivative evaluation kernels,
+assembly of the condensed matrix, supernodal Cholesky (inertia correction when
+a pivot fails), the Lifted-KKT (or HyKKT) solve refined to a backward error
+<= 1e-10 on its target system, step recovery, fraction to boundary and the
+filter line search.  When the IPM converges it is restarted (untimed).  The
+symbolic analysis is done once before timing (the paper's SYM column).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme lifted|hykkt]
         python bench.py --impl reference ...   (the CPU oracle, timed as it stands)
@@ -110,64 +108,64 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- oracle
-def oracle_step_sample(k, T_sample, seed, scheme, gamma):
-    """One KKT step of the CPU oracle at a bounded size: model derivatives,
-    condensed matrix, left-looking Cholesky and the hybrid solve."""
+def oracle_ipm_sample(k, T_sample, scheme, budget_s):
+    """Oracle IPM iterations at a bounded size until the budget is spent:
+    returns seconds per iteration (model, sparse factor, hybrid solve, line
+    search: the oracle as it stands, single thread)."""
     import numpy as np
-    from gen.tray import TrayParams, kkt_point
-    from oracle import kkt as okkt, symbolic, tray as otray
+    from gen.tray import TrayParams, ipm_start
+    from oracle import ipm as oipm, symbolic, tray as otray
     p = TrayParams(k=k, T=T_sample)
-    pt = kkt_point(p, seed)
-    W0 = otray.hessian_lower_csc(p, pt.w, pt.lam)
-    J0 = otray.jacobian_csr(p, pt.w)
-    sym = symbolic.analyse(p.n, W0[0], W0[1], J0[0], J0[1], leaf_size=64, relax_cols=32,
+    x0 = ipm_start(p)
+    W = otray.hessian_lower_csc(p, x0, np.zeros(p.m))
+    J = otray.jacobian_csr(p, x0)
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=64, relax_cols=32,
                            relax_zeros=128, max_width=64)
-    t0 = time.perf_counter()
-    W = otray.hessian_lower_csc(p, pt.w, pt.lam)
-    J = otray.jacobian_csr(p, pt.w)
-    if scheme == "lifted":
-        okkt.lifted_solve(sym, p.n, p.m, W, J, pt.sigma, 0.0, np.full(p.m, 1e8), pt.rx, pt.ry)
-    else:
-        okkt.hykkt_solve(sym, p.n, p.m, W, J, pt.sigma, 0.0, gamma, pt.rx, pt.ry)
-    return time.perf_counter() - t0
+    iters, t_total = 0, 0.0
+    while t_total < budget_s or iters == 0:
+        lin = oipm.KKTLinearSolver(scheme, p.n, p.m, None, None, sym=sym, gamma=1e4)
+        s = oipm.IPM(oipm.TrayModel(p), lin, oipm.IPMOptions(relaxed=(scheme == "lifted")), x0)
+        while not s.done and s.it < 200 and t_total < budget_s * 2:
+            t0 = time.perf_counter()
+            info = s.step()
+            dt = time.perf_counter() - t0
+            if info.status != "converged":
+                iters += 1
+                t_total += dt
+        if s.it == 0:
+            break
+    return t_total / max(1, iters), iters
 
 
 def cpu_baseline(args, budget_s=15.0, T_sample=50):
-    times = []
-    t_start = time.perf_counter()
-    while time.perf_counter() - t_start < budget_s or len(times) < 2:
-        times.append(oracle_step_sample(args.k, T_sample, args.seed, args.scheme, args.gamma))
-        if len(times) >= 20:
-            break
-    per = statistics.median(times)
+    per, iters = oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s)
     scale = (args.T + 1) / (T_sample + 1)
     return {"value": per * scale * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{len(times)} oracle KKT steps ({args.scheme}) at {args.k} trays, "
-                       f"T={T_sample}: median {per*1e3:.1f} ms, scaled x{scale:.1f} to T={args.T} "
-                       "(work linear in T)")}
+            "sample": (f"{iters} oracle IPM iterations ({args.scheme}) at {args.k} trays, T={T_sample}: "
+                       f"{per*1e3:.1f} ms each, scaled x{scale:.1f} to T={args.T} (work linear in T)")}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    times = []
-    for i in range(args.warmup + args.steps):
-        t = oracle_step_sample(args.k, 50, args.seed, args.scheme, args.gamma)
-        if i >= args.warmup:
-            times.append(t)
-    scale = (args.T + 1) / 51
-    ms = statistics.mean(times) * scale * 1e3
+    T_sample = 50
+    # warm-up iterations, then the timed ones (each step: one oracle IPM
+    # iteration at T=50, scaled to the workload's horizon)
+    oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s=0.5 * args.warmup)
+    per, iters = oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s=max(2.0, 1.5 * args.steps))
+    scale = (args.T + 1) / (T_sample + 1)
+    ms = per * scale * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"tray column k={args.k} T={args.T} (n={(2*args.k+1)*(args.T+1)}), "
-                               f"{args.scheme} KKT step, oracle on T=50 scaled by (T+1)/51",
-                   "scheme": args.scheme},
+                               f"{args.scheme} IPM iteration; oracle at T={T_sample} scaled by "
+                               f"(T+1)/{T_sample+1}", "scheme": args.scheme},
         "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one oracle KKT step at T=50 scaled x{scale:.1f}"},
+                         "sample": f"{iters} oracle IPM iterations at T={T_sample}, scaled x{scale:.1f}"},
         "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -178,153 +176,154 @@ def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
 
-    from gen.tray import TrayParams, kkt_point
-    from paper_2403_15913_gb300 import KKTSolver, TrayModel
+    from gen.tray import TrayParams, ipm_start
+    from paper_2403_15913_gb300 import IPMSolver
+    from paper_2403_15913_gb300 import _native as nat
+    import ctypes
 
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # replicas: every rank solves its own instance (horizon-shifted start)
     p = TrayParams(k=args.k, T=args.T)
-    pt = kkt_point(p, args.seed + rank)
-    tm = TrayModel(p.as_array())
-    Wc, Wr, Jr, Jc = tm.pattern()
     t0 = time.perf_counter()
-    solver = KKTSolver(p.n, p.m, Wc, Wr, Jr, Jc, scheme=args.scheme, gamma=args.gamma,
-                       max_cg=500)
+    ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500)
     t_analyse = time.perf_counter() - t0
-    sizes = solver.sizes()
-    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-    w, lam, sigma = dev(pt.w), dev(pt.lam), dev(pt.sigma)
-    rx, ry = dev(pt.rx), dev(pt.ry)
-    Wv = torch.empty(tm.nnzW, dtype=torch.float64, device="cuda")
-    Jv = torch.empty(tm.nnzJ, dtype=torch.float64, device="cuda")
-    dx = torch.empty(p.n, dtype=torch.float64, device="cuda")
-    dy = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    kctx = nat.lib().kkt_ipm_kkt(ipm._h)
+    ns, nnzL, panel, rows, lev, fl = (ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(),
+                                      ctypes.c_int64(), ctypes.c_int(), ctypes.c_double())
+    nat.lib().kkt_symbolic_sizes(kctx, ctypes.byref(ns), ctypes.byref(nnzL), ctypes.byref(panel),
+                                 ctypes.byref(rows), ctypes.byref(lev), ctypes.byref(fl))
+    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    state = {"delta_x": 0.0, "launches": 0}
+    x0 = torch.as_tensor(ipm_start(p)).cuda()
+    state = {"solves": 0, "iters_per_solve": []}
     infos = []
 
-    def kkt_step(w_, lam_, sigma_, rx_, ry_):
-        tm.eval(w_, lam_, 1.0, Jval=Jv, Wval=Wv)
-        state["launches"] += 1
-        dxr = state["delta_x"]
-        st = solver.factor(Wv, Jv, sigma_, None, dxr)
-        while st == -4:                                  # inertia correction
-            dxr = 1e-4 if dxr == 0.0 else dxr * 8.0
-            st = solver.factor(Wv, Jv, sigma_, None, dxr)
-        state["delta_x"] = dxr
-        st = solver.solve(rx_, ry_, dx, dy)
-        infos.append(dict(solver.info.as_dict(), status=st))
-        return st
+    def ipm_step():
+        """One IPM iteration; restarts the solve (untimed) when converged."""
+        st = ipm.step()
+        if st == nat.KKT_CONVERGED:
+            state["iters_per_solve"].append(ipm.info.iter)
+            ipm.init(x0)
+            state["solves"] += 1
+            return None
+        if st != nat.KKT_OK:
+            raise RuntimeError(f"IPM step failed with status {st}")
+        infos.append(ipm.info.as_dict())
+        return True
 
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    ipm.init(x0)
+    done = 0
+    while done < args.warmup:
         flush.zero_()
-        kkt_step(w, lam, sigma, rx, ry)
+        if ipm_step():
+            done += 1
     torch.cuda.synchronize()
     infos.clear()
-    solver.set_profiling(True)
-    solver.reset_stats()
-    state["launches"] = 0
+    ipm.set_profiling(True)
+    nat.lib().kkt_reset_stats(kctx)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = []
+    step_ms = []
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
+    while len(step_ms) < args.steps:
         flush.zero_()                                    # L2 flush, outside the events
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        kkt_step(w, lam, sigma, rx, ry)
+        ok = ipm_step()
         e1.record(stream)
-        evs.append((e0, e1))
+        if ok:
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = statistics.mean(step_ms)
-    st = solver.stats()
-    launches = st["launches"] + state["launches"]
+    st = nat.Stats()
+    nat.lib().kkt_get_stats(kctx, ctypes.byref(st))
+    st = st.as_dict()
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
+    ipm.set_profiling(False)
 
-    # ---- end-to-end through the public API with host buffers
-    h_in = [t.cpu().pin_memory() for t in (w, lam, sigma, rx, ry)]
-    h_out = [torch.empty(p.n, dtype=torch.float64).pin_memory(),
-             torch.empty(p.m, dtype=torch.float64).pin_memory()]
-    d_in = [torch.empty_like(t, device="cuda") for t in h_in]
-    solver.set_profiling(False)
-    e2e_ms = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
+    # ---- end to end through the public API: whole solves from a host x0
+    h_x0 = torch.as_tensor(ipm_start(p)).pin_memory()
+    d_x0 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    h_x = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    h_y = torch.empty(p.m, dtype=torch.float64).pin_memory()
+    e2e_total, e2e_iters = 0.0, 0
+    for rep in range(2):
+        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for d, h in zip(d_in, h_in):
-            d.copy_(h, non_blocking=True)
-        kkt_step(*d_in)
-        h_out[0].copy_(dx, non_blocking=True)
-        h_out[1].copy_(dy, non_blocking=True)
+        d_x0.copy_(h_x0, non_blocking=True)
+        ipm.init(d_x0)
+        hist = ipm.solve()
+        x, y, _, _, _ = ipm.get()
+        h_x.copy_(x, non_blocking=True)
+        h_y.copy_(y, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    h2d = sum(t.numel() * 8 for t in h_in)
-    d2h = (p.n + p.m) * 8
+        if rep >= 1:
+            e2e_total += e0.elapsed_time(e1)
+            e2e_iters += hist[-1]["iter"]
+    e2e_ms = e2e_total / max(1, e2e_iters)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    # ---- roofline of the dominant kernel family
     fcalls = max(1, st["factor_calls"])
-    kcalls = max(1, st["kinv_calls"])
     factor_ms = st["factor_ms"] / fcalls
-    solve_ms = st["solve_ms"] / kcalls
-    flops_factor = sizes.flops                      # sum_j cc_j^2
-    flops_solve = 4.0 * sizes.nnz_L                 # forward + backward
-    if st["factor_ms"] >= st["solve_ms"]:
-        roof = {"kernel": "factor_level_kernel (supernodal Cholesky, all levels)",
-                "bound": "alu", "achieved": flops_factor / (factor_ms * 1e-3) / 1e9,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
-    else:
-        roof = {"kernel": "forward/backward_level_kernel (triangular solves, one K^-1)",
-                "bound": "alu", "achieved": flops_solve / (solve_ms * 1e-3) / 1e9,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
+    kinv_ms = st["solve_ms"] / max(1, st["kinv_calls"])
+    roof = {"kernel": "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+            "bound": "alu", "achieved": fl.value / (factor_ms * 1e-3) / 1e9,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["peak_source"] = "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"
-    bwd = [i["bwd_err"] for i in infos]
+    roof["peak_source"] = "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)"
+    n_steps = len(step_ms)
     line = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), "
-                               f"{args.scheme} KKT step at a seeded iterate",
+        "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), full IPM "
+                               f"iteration ({args.scheme}) from xbar_0 = {p.x0bar}, tol 1e-8",
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
-                   "delta": 1e-8, "l2": "flushed (256 MB write) between timed steps",
-                   "analyse_s": round(t_analyse, 3), "supernodes": sizes.ns,
-                   "nnz_L": sizes.nnz_L, "panel_entries": sizes.panel, "levels": sizes.levels,
-                   "factor_gflop": flops_factor / 1e9, "delta_x": state["delta_x"],
-                   "max_bwd_err": max(bwd), "refine_iters": [i["refine_iters"] for i in infos][:3],
-                   "cg_iters": [i["cg_iters"] for i in infos][:3],
-                   "phase_ms": {"assemble": st["assemble_ms"] / fcalls, "factor": factor_ms,
-                                "kinv": solve_ms, "kinv_per_step": st["kinv_calls"] / args.steps,
-                                "other": st["other_ms"] / args.steps},
+                   "tau_relax": 1e-8 if args.scheme == "lifted" else None,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "analyse_s": round(t_analyse, 3), "supernodes": ns.value, "nnz_L": nnzL.value,
+                   "panel_entries": panel.value, "tree_levels": lev.value,
+                   "factor_gflop": fl.value / 1e9,
+                   "ipm_iters_to_converge": state["iters_per_solve"][:4],
+                   "phase_ms": {"eval": statistics.mean(i["t_eval_ms"] for i in infos),
+                                "kkt_solve": statistics.mean(i["t_kkt_ms"] for i in infos),
+                                "factor": factor_ms, "kinv": kinv_ms,
+                                "assemble": st["assemble_ms"] / fcalls,
+                                "factor_calls_per_step": st["factor_calls"] / n_steps,
+                                "kinv_per_step": st["kinv_calls"] / n_steps},
+                   "max_bwd_err": max(i["bwd_err"] for i in infos),
+                   "refine_iters": [i["refine_iters"] for i in infos][:6],
+                   "cg_iters": [i["cg_iters"] for i in infos][:6],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof,
-        "e2e": {"value": statistics.mean(e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
+        "e2e": {"value": e2e_ms, "unit": UNIT,
+                "h2d_bytes_per_step": p.n * 8 / max(1, e2e_iters),
+                "d2h_bytes_per_step": (p.n + p.m) * 8 / max(1, e2e_iters),
+                "scope": "whole solves: x0 host->device, all iterations, (x, y) device->host"},
+        "gpu_launches": int(st["launches"] / n_steps * args.steps) if n_steps else 0,
         "clocks": clk,
         "wall_s": wall,
     }

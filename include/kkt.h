@@ -46,6 +46,7 @@ extern "C" {
 #endif
 
 typedef enum {
+    KKT_CONVERGED = 1,      /* kkt_ipm_step: the optimality error is <= tol   */
     KKT_OK = 0,
     KKT_ERR_ARG = -1,       /* invalid argument (sizes, NULL, bad pattern)    */
     KKT_ERR_OOM = -2,       /* device allocation failed                      */
@@ -253,6 +254,74 @@ kkt_status kkt_tray_eval(const double* params, const double* d_w,
                          const double* d_lam, double obj_weight, double* d_f,
                          double* d_grad, double* d_c, double* d_Jval,
                          double* d_Wval, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Minimal filter line-search interior-point driver (Sec. III: Newton steps
+ * on F_mu(w) = 0, Eq. newtonstep, with a fraction-to-boundary rule; the
+ * filter line search of Wachter & Biegler that MadNLP implements, in its
+ * basic form: monotone barrier update, inertia correction by delta_x, no
+ * second-order correction and no restoration phase).  Every step runs on the
+ * device: derivative kernels of the column model, the KKT solve of this
+ * library, and kernels for the step recovery, fraction to boundary, filter
+ * measures and updates; only scalars come back to the host.
+ *
+ * Problem: min f(x) s.t. c(x) = 0, x_L <= x <= x_U (HyKKT, or Lifted-KKT
+ * with relaxed = 0), or with relaxed = 1 the relaxed problem of
+ * Eq. (problemrelaxation): c(x) - s = 0, -tau <= s <= tau, whose condensed
+ * matrix is W + Sigma_x + J^T Sigma_s J (requires scheme KKT_LIFTED).
+ * ---------------------------------------------------------------------- */
+typedef struct kkt_ipm kkt_ipm;
+
+typedef struct {
+    double tol;        /* stop at scaled optimality error <= tol (1e-8)     */
+    int max_iter;      /* iteration limit of kkt_ipm_solve (200)             */
+    double mu_init;    /* initial barrier parameter (0.1)                   */
+    int relaxed;       /* 1: Lifted-KKT relaxed problem (default: 1 for the
+                          Lifted scheme, 0 for HyKKT)                       */
+    double tau_relax;  /* relaxation tau (1e-8)                             */
+} kkt_ipm_options;
+
+typedef struct {
+    int iter;          /* iterations taken so far                           */
+    int ls_trials;     /* line-search trial points of the last step         */
+    int refine_iters;  /* from the last KKT solve                           */
+    int cg_iters;      /* from the last KKT solve                           */
+    double mu, objective, inf_pr, inf_du, inf_compl, err0;
+    double alpha_pr, alpha_du, delta_x, bwd_err;
+    double t_eval_ms, t_kkt_ms, t_step_ms;   /* device time of the last step:
+                          derivative evaluation, KKT factor + solve, total  */
+} kkt_ipm_info;
+
+void kkt_ipm_default_options(kkt_ipm_options* opt);
+
+/* Creates the driver for the column model with parameters tray_params[16]
+ * (see kkt_tray_sizes); runs the symbolic analysis once (kopt may be NULL). */
+kkt_status kkt_ipm_create(const double* tray_params, const kkt_options* kopt,
+                          const kkt_ipm_options* iopt, kkt_ipm** out);
+
+/* (Re)starts from d_x0[n] (NULL: compositions at xbar_0, controls at ubar),
+ * pushed inside the bounds; multipliers y = 0, bound multipliers 1. */
+kkt_status kkt_ipm_init(kkt_ipm* ipm, const double* d_x0, cudaStream_t stream);
+
+/* One IPM iteration.  Returns KKT_OK after a step, KKT_CONVERGED when the
+ * current point already satisfies the tolerance (no step taken),
+ * KKT_ERR_STALL when the line search failed, KKT_ERR_NOT_SPD when inertia
+ * correction gave up, or another error. */
+kkt_status kkt_ipm_step(kkt_ipm* ipm, cudaStream_t stream, kkt_ipm_info* info);
+
+/* Iterates kkt_ipm_step until convergence (returns KKT_CONVERGED), an error,
+ * or max_iter iterations (returns KKT_ERR_MAXIT); info holds the last step. */
+kkt_status kkt_ipm_solve(kkt_ipm* ipm, cudaStream_t stream, kkt_ipm_info* info);
+
+/* Copies the current iterate (device arrays; any may be NULL): x[n], y[m],
+ * z_L[n], z_U[n], s[m] (relaxed problem only). */
+kkt_status kkt_ipm_get(const kkt_ipm* ipm, double* d_x, double* d_y, double* d_zl,
+                       double* d_zu, double* d_s, cudaStream_t stream);
+
+/* The KKT context the driver uses (for kkt_get_stats / profiling). */
+kkt_ctx* kkt_ipm_kkt(kkt_ipm* ipm);
+
+void kkt_ipm_destroy(kkt_ipm* ipm);
 
 #ifdef __cplusplus
 }

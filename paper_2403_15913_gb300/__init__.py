@@ -5,3 +5,4 @@ dynamic NLPs, with the Lifted-KKT and HyKKT hybrid solvers of Pacaud & Shin
 arguments."""
 from .solver import KKTSolver, KKTError, default_options  # noqa: F401
 from .tray import TrayModel  # noqa: F401
+from .ipm import IPMSolver  # noqa: F401

@@ -8,6 +8,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkkt_gb300.so")
 
+KKT_CONVERGED = 1
 KKT_OK = 0
 KKT_ERR_ARG = -1
 KKT_ERR_OOM = -2
@@ -18,7 +19,7 @@ KKT_ERR_STALL = -6
 KKT_ERR_TIMEOUT = -7
 KKT_ERR_STATE = -8
 KKT_ERR_INTERNAL = -9
-STATUS_NAMES = {0: "ok", -1: "arg", -2: "oom", -3: "cuda", -4: "not_spd", -5: "maxit",
+STATUS_NAMES = {1: "converged", 0: "ok", -1: "arg", -2: "oom", -3: "cuda", -4: "not_spd", -5: "maxit",
                 -6: "stall", -7: "timeout", -8: "state", -9: "internal"}
 
 KKT_STATIC_SCRATCH_DOUBLES = 1 << 21   # size of the allocation-free backsolve's scratch
@@ -32,6 +33,9 @@ EXPORTED = [
     "kkt_factor_export",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
+    "kkt_ipm_default_options", "kkt_ipm_create", "kkt_ipm_init", "kkt_ipm_step", "kkt_ipm_solve",
+    "kkt_ipm_get",
+    "kkt_ipm_kkt", "kkt_ipm_destroy",
 ]
 
 
@@ -59,6 +63,26 @@ class Stats(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("factor_launches", ctypes.c_int64),
                 ("factor_calls", ctypes.c_int64), ("kinv_calls", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class IPMOptions(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double),
+                ("relaxed", ctypes.c_int), ("tau_relax", ctypes.c_double)]
+
+
+class IPMInfo(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int), ("ls_trials", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("mu", ctypes.c_double), ("objective", ctypes.c_double),
+                ("inf_pr", ctypes.c_double), ("inf_du", ctypes.c_double),
+                ("inf_compl", ctypes.c_double), ("err0", ctypes.c_double),
+                ("alpha_pr", ctypes.c_double), ("alpha_du", ctypes.c_double),
+                ("delta_x", ctypes.c_double), ("bwd_err", ctypes.c_double),
+                ("t_eval_ms", ctypes.c_double), ("t_kkt_ms", ctypes.c_double),
+                ("t_step_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -119,6 +143,23 @@ def lib():
     L.kkt_get_stats.restype = ctypes.c_int
     L.kkt_reset_stats.argtypes = [P]
     L.kkt_reset_stats.restype = ctypes.c_int
+    L.kkt_ipm_default_options.argtypes = [ctypes.POINTER(IPMOptions)]
+    L.kkt_ipm_default_options.restype = None
+    L.kkt_ipm_create.argtypes = [F64P, ctypes.POINTER(Options), ctypes.POINTER(IPMOptions),
+                                 ctypes.POINTER(P)]
+    L.kkt_ipm_create.restype = ctypes.c_int
+    L.kkt_ipm_init.argtypes = [P, P, P]
+    L.kkt_ipm_init.restype = ctypes.c_int
+    L.kkt_ipm_step.argtypes = [P, P, ctypes.POINTER(IPMInfo)]
+    L.kkt_ipm_step.restype = ctypes.c_int
+    L.kkt_ipm_solve.argtypes = [P, P, ctypes.POINTER(IPMInfo)]
+    L.kkt_ipm_solve.restype = ctypes.c_int
+    L.kkt_ipm_get.argtypes = [P, P, P, P, P, P, P]
+    L.kkt_ipm_get.restype = ctypes.c_int
+    L.kkt_ipm_kkt.argtypes = [P]
+    L.kkt_ipm_kkt.restype = P
+    L.kkt_ipm_destroy.argtypes = [P]
+    L.kkt_ipm_destroy.restype = None
     _lib = L
     return L
 

@@ -1,0 +1,693 @@
+// Minimal filter line-search interior-point driver on the device (Sec. III of
+// Pacaud & Shin: Newton steps on F_mu(w) = 0 with a fraction-to-boundary rule;
+// the filter line search of Wachter & Biegler (2006), basic form).
+//
+// Per iteration (host logic in C++, every vector operation in a kernel):
+//   1. derivatives of the column model at (x, y)          kkt_tray_eval
+//   2. optimality error E_0; monotone barrier update      errors_kernel
+//   3. Sigma_x, r_x = -(grad phi + J^T y), r_y            prepare_kernel
+//   4. KKT factor (inertia-correction ladder) and solve   kkt_factor / kkt_solve
+//   5. bound-multiplier steps, fraction to boundary,
+//      directional derivative of the barrier function    recover_kernel
+//   6. backtracking filter line search on (theta, phi)    trial/measure kernels
+//   7. update with the bound-multiplier safeguard         accept_kernel
+// Only scalars (norms, step lengths, filter measures) come back to the host.
+// Constants are the published defaults of the reference algorithm.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kkt.h"
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kRB = 296;            // CTAs of the reduction kernels (fixed: deterministic sums)
+constexpr int kQ = 8;               // quantities per reduction
+
+// Wachter-Biegler defaults
+constexpr double kKappaEps = 10.0, kKappaMu = 0.2, kThetaMu = 1.5, kTauMin = 0.99;
+constexpr double kSMax = 100.0, kBoundPush = 1e-2, kBoundFrac = 1e-2, kKappaSigma = 1e10;
+constexpr double kGammaTheta = 1e-5, kGammaPhi = 1e-8, kDelta = 1.0, kSTheta = 1.1, kSPhi = 2.3;
+constexpr double kEtaPhi = 1e-8;
+constexpr int kMaxLs = 40;
+constexpr double kDeltaW0 = 1e-4, kDeltaMin = 1e-20, kDeltaMax = 1e40;
+constexpr double kKappaWMinus = 1.0 / 3.0, kKappaWPlus = 8.0, kKappaWPlusBar = 100.0;
+
+enum Op { SUM = 0, MAX = 1, MIN = 2 };
+
+__device__ __forceinline__ double combine(double a, double b, int op) {
+    return op == SUM ? a + b : (op == MAX ? fmax(a, b) : fmin(a, b));
+}
+
+__device__ __forceinline__ double block_reduce(double v, int op, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = combine(v, __shfl_down_sync(0xffffffffu, v, o), op);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const double id = op == SUM ? 0.0 : (op == MAX ? -INFINITY : INFINITY);
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : id;
+        for (int o = 16; o > 0; o >>= 1) v = combine(v, __shfl_down_sync(0xffffffffu, v, o), op);
+    }
+    return v;
+}
+
+// Writes the block's K partial results to part[blockIdx.x * kQ + q].
+template <int K>
+__device__ __forceinline__ void store_partials(const double (&v)[K], const int (&ops)[K], double* part) {
+    __shared__ double red[kT / 32];
+    for (int q = 0; q < K; ++q) {
+        const double r = block_reduce(v[q], ops[q], red);
+        if (threadIdx.x == 0) part[blockIdx.x * kQ + q] = r;
+    }
+}
+
+// Final reduction of kRB partial blocks, fixed order: out[q] for q < nq.
+__global__ void final_reduce_kernel(const double* __restrict__ part, const int* __restrict__ ops,
+                                    int nq, double* __restrict__ out) {
+    const int q = threadIdx.x;
+    if (q >= nq) return;
+    const int op = ops[q];
+    double acc = part[q];
+    for (int b = 1; b < kRB; ++b) acc = combine(acc, part[b * kQ + q], op);
+    out[q] = acc;
+}
+
+struct Bounds {
+    const double *xlo, *xhi;
+    double tau;   // slack bounds [-tau, tau]
+};
+
+// J^T v through the CSC of J (deterministic gather).
+__global__ void jt_kernel(int n, const int* __restrict__ cp, const int* __restrict__ ri,
+                          const int* __restrict__ idx, const double* __restrict__ J,
+                          const double* __restrict__ v, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = cp[i]; q < cp[i + 1]; ++q) s += J[idx[q]] * v[ri[q]];
+        out[i] = s;
+    }
+}
+
+__global__ void push_kernel(int n, const double* __restrict__ lo, const double* __restrict__ hi,
+                            double clo, double chi, double* __restrict__ x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double l = lo ? lo[i] : clo, h = hi ? hi[i] : chi;
+        const double pl = fmin(kBoundPush * fmax(1.0, fabs(l)), kBoundFrac * (h - l));
+        const double pu = fmin(kBoundPush * fmax(1.0, fabs(h)), kBoundFrac * (h - l));
+        x[i] = fmin(fmax(x[i], l + pl), h - pu);
+    }
+}
+
+__global__ void fill_kernel(int n, double v, double* __restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = v;
+}
+
+__global__ void copy_kernel(int n, const double* __restrict__ a, double* __restrict__ b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+// Optimality measures: [max|du|, max|pr|, max z*gap, min z*gap, sum|y|, sum z, 0, 0]
+__global__ void __launch_bounds__(kT)
+errors_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
+              const double* __restrict__ s, const double* __restrict__ y,
+              const double* __restrict__ zl, const double* __restrict__ zu,
+              const double* __restrict__ vl, const double* __restrict__ vu,
+              const double* __restrict__ grad, const double* __restrict__ jty,
+              const double* __restrict__ c, double* __restrict__ part) {
+    double v[6] = {0.0, 0.0, -INFINITY, INFINITY, 0.0, 0.0};
+    const int ops[6] = {MAX, MAX, MAX, MIN, SUM, SUM};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
+            v[0] = fmax(v[0], fabs(grad[i] + jty[i] - zl[i] + zu[i]));
+            const double a = zl[i] * gl, b = zu[i] * gu;
+            v[2] = fmax(v[2], fmax(a, b));
+            v[3] = fmin(v[3], fmin(a, b));
+            v[5] += zl[i] + zu[i];
+        } else {
+            const int k = i - n;
+            v[1] = fmax(v[1], fabs(relaxed ? c[k] - s[k] : c[k]));
+            v[4] += fabs(y[k]);
+            if (relaxed) {
+                v[0] = fmax(v[0], fabs(-y[k] - vl[k] + vu[k]));
+                const double a = vl[k] * (s[k] + B.tau), b = vu[k] * (B.tau - s[k]);
+                v[2] = fmax(v[2], fmax(a, b));
+                v[3] = fmin(v[3], fmin(a, b));
+                v[5] += vl[k] + vu[k];
+            }
+        }
+    }
+    store_partials<6>(v, ops, part);
+}
+
+__global__ void prepare_kernel(int n, int m, int relaxed, Bounds B, double mu,
+                               const double* __restrict__ x, const double* __restrict__ s,
+                               const double* __restrict__ y, const double* __restrict__ zl,
+                               const double* __restrict__ zu, const double* __restrict__ vl,
+                               const double* __restrict__ vu, const double* __restrict__ grad,
+                               const double* __restrict__ jty, const double* __restrict__ c,
+                               double* __restrict__ sigma, double* __restrict__ rx,
+                               double* __restrict__ ry, double* __restrict__ D) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
+            sigma[i] = zl[i] / gl + zu[i] / gu;
+            rx[i] = -(grad[i] - mu / gl + mu / gu + jty[i]);
+        } else {
+            const int k = i - n;
+            if (relaxed) {
+                const double hl = s[k] + B.tau, hu = B.tau - s[k];
+                const double sig = vl[k] / hl + vu[k] / hu;
+                const double gphi = -mu / hl + mu / hu;
+                D[k] = sig;
+                ry[k] = -(c[k] - s[k]) - (gphi - y[k]) / sig;
+            } else {
+                ry[k] = -c[k];
+            }
+        }
+    }
+}
+
+// Step recovery, fraction to boundary and directional derivative:
+// partials [alpha_pr (min), alpha_du (min), dphi (sum)].
+__global__ void __launch_bounds__(kT)
+recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
+               const double* __restrict__ x, const double* __restrict__ s,
+               const double* __restrict__ y, const double* __restrict__ zl,
+               const double* __restrict__ zu, const double* __restrict__ vl,
+               const double* __restrict__ vu, const double* __restrict__ grad,
+               const double* __restrict__ dx, const double* __restrict__ dy,
+               double* __restrict__ ds, double* __restrict__ dzl, double* __restrict__ dzu,
+               double* __restrict__ dvl, double* __restrict__ dvu, double* __restrict__ part) {
+    double v[3] = {1.0, 1.0, 0.0};
+    const int ops[3] = {MIN, MIN, SUM};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
+            const double d = dx[i];
+            const double a = mu / gl - zl[i] - (zl[i] / gl) * d;
+            const double b = mu / gu - zu[i] + (zu[i] / gu) * d;
+            dzl[i] = a;
+            dzu[i] = b;
+            if (d < 0) v[0] = fmin(v[0], -tau * gl / d);
+            if (d > 0) v[0] = fmin(v[0], tau * gu / d);
+            if (a < 0) v[1] = fmin(v[1], -tau * zl[i] / a);
+            if (b < 0) v[1] = fmin(v[1], -tau * zu[i] / b);
+            v[2] += (grad[i] - mu / gl + mu / gu) * d;
+        } else if (relaxed) {
+            const int k = i - n;
+            const double hl = s[k] + B.tau, hu = B.tau - s[k];
+            const double sig = vl[k] / hl + vu[k] / hu;
+            const double gphi = -mu / hl + mu / hu;
+            const double d = (dy[k] - gphi + y[k]) / sig;
+            ds[k] = d;
+            const double a = mu / hl - vl[k] - (vl[k] / hl) * d;
+            const double b = mu / hu - vu[k] + (vu[k] / hu) * d;
+            dvl[k] = a;
+            dvu[k] = b;
+            if (d < 0) v[0] = fmin(v[0], -tau * hl / d);
+            if (d > 0) v[0] = fmin(v[0], tau * hu / d);
+            if (a < 0) v[1] = fmin(v[1], -tau * vl[k] / a);
+            if (b < 0) v[1] = fmin(v[1], -tau * vu[k] / b);
+            v[2] += gphi * d;
+        }
+    }
+    store_partials<3>(v, ops, part);
+}
+
+__global__ void trial_kernel(int n, int m, int relaxed, double alpha, const double* __restrict__ x,
+                             const double* __restrict__ dx, const double* __restrict__ s,
+                             const double* __restrict__ ds, double* __restrict__ xt,
+                             double* __restrict__ st) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) xt[i] = x[i] + alpha * dx[i];
+        else if (relaxed) st[i - n] = s[i - n] + alpha * ds[i - n];
+    }
+}
+
+// Filter measures at a point: partials [theta = sum |c - s|, sum log(gaps)].
+__global__ void __launch_bounds__(kT)
+measure_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
+               const double* __restrict__ s, const double* __restrict__ c, double* __restrict__ part) {
+    double v[2] = {0.0, 0.0};
+    const int ops[2] = {SUM, SUM};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            v[1] += log(x[i] - B.xlo[i]) + log(B.xhi[i] - x[i]);
+        } else {
+            const int k = i - n;
+            v[0] += fabs(relaxed ? c[k] - s[k] : c[k]);
+            if (relaxed) v[1] += log(s[k] + B.tau) + log(B.tau - s[k]);
+        }
+    }
+    store_partials<2>(v, ops, part);
+}
+
+__global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, double alpha,
+                              double alpha_du, double* __restrict__ x, double* __restrict__ s,
+                              double* __restrict__ y, double* __restrict__ zl,
+                              double* __restrict__ zu, double* __restrict__ vl,
+                              double* __restrict__ vu, const double* __restrict__ dx,
+                              const double* __restrict__ ds, const double* __restrict__ dy,
+                              const double* __restrict__ dzl, const double* __restrict__ dzu,
+                              const double* __restrict__ dvl, const double* __restrict__ dvu) {
+    const double k = kKappaSigma;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double xn = x[i] + alpha * dx[i];
+            x[i] = xn;
+            const double gl = xn - B.xlo[i], gu = B.xhi[i] - xn;
+            const double a = zl[i] + alpha_du * dzl[i], b = zu[i] + alpha_du * dzu[i];
+            zl[i] = fmax(fmin(a, k * mu / gl), mu / (k * gl));
+            zu[i] = fmax(fmin(b, k * mu / gu), mu / (k * gu));
+        } else {
+            const int q = i - n;
+            y[q] += alpha * dy[q];
+            if (relaxed) {
+                const double sn = s[q] + alpha * ds[q];
+                s[q] = sn;
+                const double hl = sn + B.tau, hu = B.tau - sn;
+                const double a = vl[q] + alpha_du * dvl[q], b = vu[q] + alpha_du * dvu[q];
+                vl[q] = fmax(fmin(a, k * mu / hl), mu / (k * hl));
+                vu[q] = fmax(fmin(b, k * mu / hu), mu / (k * hu));
+            }
+        }
+    }
+}
+
+int grid(long long w) {
+    long long g = (w + kT - 1) / kT;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 8));
+}
+
+}  // namespace
+
+struct kkt_ipm {
+    kkt_ipm_options opt{};
+    double params[16];
+    int n = 0, m = 0, nnzW = 0, nnzJ = 0;
+    kkt_ctx* kkt = nullptr;
+    std::string err;
+    std::vector<void*> allocs;
+    // device state
+    double *x, *s, *y, *zl, *zu, *vl, *vu, *xlo, *xhi;
+    double *grad, *c, *Jv, *Wv, *jty, *sigma, *rx, *ry, *D;
+    double *dx, *dy, *ds, *dzl, *dzu, *dvl, *dvu, *xt, *st, *ct;
+    double *part, *red, *f;
+    int* ops;
+    int *jt_cp, *jt_ri, *jt_idx;
+    double* h_red = nullptr;   // pinned
+    // host state
+    double mu = 0.1, theta_max = 0, theta_min = 0, delta_last = 0;
+    std::vector<std::pair<double, double>> filter;
+    int it = 0;
+    bool started = false;
+    cudaEvent_t ev[4] = {};
+};
+
+namespace {
+
+kkt_status ierr(kkt_ipm* p, kkt_status st, const std::string& msg) {
+    if (p) p->err = msg;
+    return st;
+}
+
+#define ICUDA(p, call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return ierr(p, e_ == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+template <class T>
+kkt_status dalloc(kkt_ipm* p, T** out, size_t count) {
+    ICUDA(p, cudaMalloc((void**)out, std::max<size_t>(1, count) * sizeof(T)));
+    p->allocs.push_back(*out);
+    return KKT_OK;
+}
+
+#define ITRY(x)                       \
+    do {                              \
+        kkt_status s_ = (x);          \
+        if (s_ != KKT_OK) return s_;  \
+    } while (0)
+
+Bounds bounds_of(const kkt_ipm* p) { return Bounds{p->xlo, p->xhi, p->opt.tau_relax}; }
+
+// reduce kRB partials to q results and copy them to the host
+kkt_status finish_reduce(kkt_ipm* p, const int* h_ops, int nq, cudaStream_t st, double* out) {
+    ICUDA(p, cudaMemcpyAsync(p->ops, h_ops, nq * sizeof(int), cudaMemcpyHostToDevice, st));
+    final_reduce_kernel<<<1, 32, 0, st>>>(p->part, p->ops, nq, p->red);
+    ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    for (int q = 0; q < nq; ++q) out[q] = p->h_red[q];
+    return KKT_OK;
+}
+
+struct Errors {
+    double du, pr, zg_max, zg_min, sum_y, sum_z;
+};
+
+double err_mu(const kkt_ipm* p, const Errors& e, double mu) {
+    const int n = p->n, m = p->m;
+    const bool rel = p->opt.relaxed;
+    const double cnt_mult = m + 2.0 * n + (rel ? 2.0 * m : 0.0);
+    const double cnt_z = 2.0 * n + (rel ? 2.0 * m : 0.0);
+    const double s_d = std::max(kSMax, (e.sum_y + e.sum_z) / cnt_mult) / kSMax;
+    const double s_c = std::max(kSMax, e.sum_z / cnt_z) / kSMax;
+    const double compl_mu = std::max(e.zg_max - mu, mu - e.zg_min);
+    return std::max(std::max(e.du / s_d, e.pr), compl_mu / s_c);
+}
+
+kkt_status measures(kkt_ipm* p, const double* x, const double* s, const double* c, cudaStream_t st,
+                    double* theta, double* logsum) {
+    measure_kernel<<<kRB, kT, 0, st>>>(p->n, p->m, p->opt.relaxed, bounds_of(p), x, s, c, p->part);
+    static const int ops[2] = {SUM, SUM};
+    double out[2];
+    ITRY(finish_reduce(p, ops, 2, st, out));
+    *theta = out[0];
+    *logsum = out[1];
+    return KKT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kkt_ipm_default_options(kkt_ipm_options* o) {
+    if (!o) return;
+    o->tol = 1e-8;
+    o->max_iter = 200;
+    o->mu_init = 0.1;
+    o->relaxed = -1;   // decided from the scheme
+    o->tau_relax = 1e-8;
+}
+
+kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const kkt_ipm_options* iopt,
+                          kkt_ipm** out) {
+    if (!params || !out) return KKT_ERR_ARG;
+    *out = nullptr;
+    kkt_ipm* p = new (std::nothrow) kkt_ipm();
+    if (!p) return KKT_ERR_OOM;
+    std::copy(params, params + 16, p->params);
+    if (iopt) p->opt = *iopt; else kkt_ipm_default_options(&p->opt);
+    kkt_options ko;
+    if (kopt) ko = *kopt; else kkt_default_options(&ko);
+    if (p->opt.relaxed < 0) p->opt.relaxed = ko.scheme == KKT_LIFTED ? 1 : 0;
+    if (p->opt.relaxed && ko.scheme != KKT_LIFTED) {
+        delete p;
+        return KKT_ERR_ARG;
+    }
+    ko.target_relaxed = p->opt.relaxed ? 1 : 0;
+    if (!(p->opt.tol > 0 && p->opt.mu_init > 0 && p->opt.tau_relax > 0)) {
+        delete p;
+        return KKT_ERR_ARG;
+    }
+    kkt_status stt = kkt_tray_sizes(params, &p->n, &p->m, &p->nnzW, &p->nnzJ);
+    if (stt != KKT_OK) {
+        delete p;
+        return stt;
+    }
+    const int n = p->n, m = p->m;
+    std::vector<int> Wc(n + 1), Wr(p->nnzW), Jr(m + 1), Jc(p->nnzJ);
+    kkt_tray_pattern(params, Wc.data(), Wr.data(), Jr.data(), Jc.data());
+    stt = kkt_analyse(n, m, Wc.data(), Wr.data(), Jr.data(), Jc.data(), &ko, &p->kkt);
+    if (stt != KKT_OK) {
+        delete p;
+        return stt;
+    }
+    // CSC of J for J^T y
+    std::vector<int> cp(n + 1, 0), ri(p->nnzJ), idx(p->nnzJ);
+    for (int q = 0; q < p->nnzJ; ++q) cp[Jc[q] + 1]++;
+    for (int i = 0; i < n; ++i) cp[i + 1] += cp[i];
+    {
+        std::vector<int> fillp(cp.begin(), cp.end() - 1);
+        for (int r = 0; r < m; ++r)
+            for (int q = Jr[r]; q < Jr[r + 1]; ++q) {
+                ri[fillp[Jc[q]]] = r;
+                idx[fillp[Jc[q]]++] = q;
+            }
+    }
+    // bounds: 0 <= x, y <= 1 (x_lo, x_hi), 1 <= u <= 5 (u_lo, u_hi), stage-major
+    const int k = (int)params[0];
+    std::vector<double> lo(n), hi(n);
+    for (int i = 0; i < n; ++i) {
+        const bool is_u = (i % (2 * k + 1)) == 2 * k;
+        lo[i] = is_u ? params[14] : params[12];
+        hi[i] = is_u ? params[15] : params[13];
+    }
+    auto fail = [&](kkt_status s) {
+        kkt_ipm_destroy(p);
+        return s;
+    };
+    double** vecs_n[] = {&p->x, &p->zl, &p->zu, &p->xlo, &p->xhi, &p->grad, &p->jty, &p->sigma,
+                         &p->rx, &p->dx, &p->dzl, &p->dzu, &p->xt};
+    for (double** v : vecs_n)
+        if (dalloc(p, v, n) != KKT_OK) return fail(KKT_ERR_OOM);
+    double** vecs_m[] = {&p->s, &p->y, &p->vl, &p->vu, &p->c, &p->ry, &p->D, &p->dy, &p->ds,
+                         &p->dvl, &p->dvu, &p->st, &p->ct};
+    for (double** v : vecs_m)
+        if (dalloc(p, v, m) != KKT_OK) return fail(KKT_ERR_OOM);
+    if (dalloc(p, &p->Jv, p->nnzJ) != KKT_OK || dalloc(p, &p->Wv, p->nnzW) != KKT_OK ||
+        dalloc(p, &p->part, (size_t)kRB * kQ) != KKT_OK || dalloc(p, &p->red, kQ) != KKT_OK ||
+        dalloc(p, &p->f, 1) != KKT_OK || dalloc(p, &p->ops, kQ) != KKT_OK ||
+        dalloc(p, &p->jt_cp, n + 1) != KKT_OK || dalloc(p, &p->jt_ri, p->nnzJ) != KKT_OK ||
+        dalloc(p, &p->jt_idx, p->nnzJ) != KKT_OK)
+        return fail(KKT_ERR_OOM);
+    if (cudaMemcpy(p->jt_cp, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->jt_ri, ri.data(), p->nnzJ * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->jt_idx, idx.data(), p->nnzJ * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->xlo, lo.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->xhi, hi.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(KKT_ERR_CUDA);
+    if (cudaMallocHost((void**)&p->h_red, kQ * sizeof(double)) != cudaSuccess) return fail(KKT_ERR_OOM);
+    for (auto& e : p->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(KKT_ERR_CUDA);
+    *out = p;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
+    if (!p) return KKT_ERR_ARG;
+    const int n = p->n, m = p->m;
+    if (d_x0) {
+        ICUDA(p, cudaMemcpyAsync(p->x, d_x0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        const int k = (int)p->params[0];
+        std::vector<double> x0(n);
+        for (int i = 0; i < n; ++i) x0[i] = (i % (2 * k + 1)) == 2 * k ? p->params[9] : p->params[11];
+        ICUDA(p, cudaMemcpyAsync(p->x, x0.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+        ICUDA(p, cudaStreamSynchronize(st));
+    }
+    push_kernel<<<grid(n), kT, 0, st>>>(n, p->xlo, p->xhi, 0, 0, p->x);
+    fill_kernel<<<grid(m), kT, 0, st>>>(m, 0.0, p->y);
+    fill_kernel<<<grid(n), kT, 0, st>>>(n, 1.0, p->zl);
+    fill_kernel<<<grid(n), kT, 0, st>>>(n, 1.0, p->zu);
+    if (p->opt.relaxed) {
+        ITRY(kkt_tray_eval(p->params, p->x, nullptr, 1.0, nullptr, nullptr, p->s, nullptr, nullptr, st));
+        push_kernel<<<grid(m), kT, 0, st>>>(m, nullptr, nullptr, -p->opt.tau_relax, p->opt.tau_relax, p->s);
+        fill_kernel<<<grid(m), kT, 0, st>>>(m, 1.0, p->vl);
+        fill_kernel<<<grid(m), kT, 0, st>>>(m, 1.0, p->vu);
+    }
+    ITRY(kkt_tray_eval(p->params, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
+    double th = 0, ls = 0;
+    ITRY(measures(p, p->x, p->s, p->c, st, &th, &ls));
+    p->theta_max = 1e4 * std::max(1.0, th);
+    p->theta_min = 1e-4 * std::max(1.0, th);
+    p->mu = p->opt.mu_init;
+    p->filter.clear();
+    p->delta_last = 0.0;
+    p->it = 0;
+    p->started = true;
+    ICUDA(p, cudaGetLastError());
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
+    if (!p) return KKT_ERR_ARG;
+    if (!p->started) return ierr(p, KKT_ERR_STATE, "kkt_ipm_step before kkt_ipm_init");
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    const Bounds B = bounds_of(p);
+    kkt_ipm_info inf{};
+    inf.iter = p->it;
+    cudaEventRecord(p->ev[0], st);
+    // 1. derivatives
+    ITRY(kkt_tray_eval(p->params, p->x, p->y, 1.0, p->f, p->grad, p->c, p->Jv, p->Wv, st));
+    jt_kernel<<<grid(n), kT, 0, st>>>(n, p->jt_cp, p->jt_ri, p->jt_idx, p->Jv, p->y, p->jty);
+    cudaEventRecord(p->ev[1], st);
+    // 2. optimality error and barrier update
+    errors_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, p->x, p->s, p->y, p->zl, p->zu, p->vl, p->vu,
+                                      p->grad, p->jty, p->c, p->part);
+    static const int eops[6] = {MAX, MAX, MAX, MIN, SUM, SUM};
+    double ev6[6];
+    ITRY(finish_reduce(p, eops, 6, st, ev6));
+    Errors E{ev6[0], ev6[1], ev6[2], ev6[3], ev6[4], ev6[5]};
+    ICUDA(p, cudaMemcpyAsync(p->h_red, p->f, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    const double fval = p->h_red[0];
+    const double e0 = err_mu(p, E, 0.0);
+    inf.objective = fval;
+    inf.inf_du = E.du;
+    inf.inf_pr = E.pr;
+    inf.inf_compl = std::max(std::fabs(E.zg_max), std::fabs(E.zg_min));
+    inf.err0 = e0;
+    inf.mu = p->mu;
+    if (e0 <= p->opt.tol) {
+        if (info) *info = inf;
+        return KKT_CONVERGED;
+    }
+    while (p->mu > p->opt.tol / 10) {
+        if (err_mu(p, E, p->mu) > kKappaEps * p->mu) break;
+        p->mu = std::max(p->opt.tol / 10, std::min(kKappaMu * p->mu, std::pow(p->mu, kThetaMu)));
+        p->filter.clear();
+    }
+    const double mu = p->mu;
+    inf.mu = mu;
+    // 3. right-hand side and diagonals
+    prepare_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, p->x, p->s, p->y, p->zl,
+                                                        p->zu, p->vl, p->vu, p->grad, p->jty, p->c,
+                                                        p->sigma, p->rx, p->ry, p->D);
+    // 4. factor with inertia correction, solve
+    kkt_info ki{};
+    double delta = 0.0;
+    kkt_status fs;
+    while (true) {
+        fs = kkt_factor(p->kkt, p->Wv, p->Jv, p->sigma, rel ? p->D : nullptr, delta, st, &ki);
+        if (fs == KKT_OK) break;
+        if (fs != KKT_ERR_NOT_SPD) return ierr(p, fs, std::string("kkt_factor: ") + kkt_last_error(p->kkt));
+        if (delta == 0.0)
+            delta = p->delta_last == 0.0 ? kDeltaW0 : std::max(kDeltaMin, kKappaWMinus * p->delta_last);
+        else
+            delta *= p->delta_last == 0.0 ? kKappaWPlusBar : kKappaWPlus;
+        if (delta > kDeltaMax) return ierr(p, KKT_ERR_NOT_SPD, "inertia correction gave up");
+    }
+    if (delta > 0) p->delta_last = delta;
+    inf.delta_x = delta;
+    kkt_status ss = kkt_solve(p->kkt, p->rx, p->ry, p->dx, p->dy, nullptr, st, &ki);
+    if (ss != KKT_OK && ss != KKT_ERR_MAXIT && ss != KKT_ERR_STALL)
+        return ierr(p, ss, std::string("kkt_solve: ") + kkt_last_error(p->kkt));
+    inf.refine_iters = ki.refine_iters;
+    inf.cg_iters = ki.cg_iters;
+    inf.bwd_err = ki.bwd_err;
+    cudaEventRecord(p->ev[2], st);
+    // 5. recovery, fraction to boundary, directional derivative
+    const double tau = std::max(kTauMin, 1.0 - mu);
+    recover_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, mu, tau, p->x, p->s, p->y, p->zl, p->zu, p->vl,
+                                       p->vu, p->grad, p->dx, p->dy, p->ds, p->dzl, p->dzu, p->dvl,
+                                       p->dvu, p->part);
+    static const int rops[3] = {MIN, MIN, SUM};
+    double rv[3];
+    ITRY(finish_reduce(p, rops, 3, st, rv));
+    const double a_pr = rv[0], a_du = rv[1], dphi = rv[2];
+    // 6. filter line search
+    double th = 0, lsum = 0;
+    ITRY(measures(p, p->x, p->s, p->c, st, &th, &lsum));
+    const double ph = fval - mu * lsum;
+    double alpha = a_pr;
+    bool accepted = false;
+    int ls = 0;
+    for (ls = 1; ls <= kMaxLs; ++ls) {
+        trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, alpha, p->x, p->dx, p->s, p->ds,
+                                                          p->xt, p->st);
+        ITRY(kkt_tray_eval(p->params, p->xt, nullptr, 1.0, p->f, nullptr, p->ct, nullptr, nullptr, st));
+        double tht = 0, lst = 0;
+        ICUDA(p, cudaMemcpyAsync(p->red + kQ - 1, p->f, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ITRY(measures(p, p->xt, p->st, p->ct, st, &tht, &lst));
+        ICUDA(p, cudaMemcpyAsync(p->h_red, p->red + kQ - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ICUDA(p, cudaStreamSynchronize(st));
+        const double ft = p->h_red[0];
+        const double pht = ft - mu * lst;
+        bool ok = tht <= p->theta_max;
+        for (const auto& fe : p->filter)
+            if (!(tht < fe.first || pht < fe.second)) { ok = false; break; }
+        bool f_type = false;
+        if (ok) {
+            const bool switching = dphi < 0 && alpha * std::pow(-dphi, kSPhi) > kDelta * std::pow(th, kSTheta);
+            if (th <= p->theta_min && switching) {
+                ok = pht <= ph + kEtaPhi * alpha * dphi;
+                f_type = true;
+            } else {
+                ok = tht <= (1 - kGammaTheta) * th || pht <= ph - kGammaPhi * th;
+            }
+        }
+        if (ok) {
+            if (!f_type) p->filter.emplace_back((1 - kGammaTheta) * th, ph - kGammaPhi * th);
+            accepted = true;
+            break;
+        }
+        alpha *= 0.5;
+    }
+    inf.ls_trials = ls;
+    if (!accepted) {
+        if (info) *info = inf;
+        return ierr(p, KKT_ERR_STALL, "line search failed (no restoration phase)");
+    }
+    // 7. update
+    accept_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, alpha, a_du, p->x, p->s,
+                                                       p->y, p->zl, p->zu, p->vl, p->vu, p->dx,
+                                                       p->ds, p->dy, p->dzl, p->dzu, p->dvl, p->dvu);
+    cudaEventRecord(p->ev[3], st);
+    ICUDA(p, cudaEventSynchronize(p->ev[3]));
+    float t01 = 0, t12 = 0, t03 = 0;
+    cudaEventElapsedTime(&t01, p->ev[0], p->ev[1]);
+    cudaEventElapsedTime(&t12, p->ev[1], p->ev[2]);
+    cudaEventElapsedTime(&t03, p->ev[0], p->ev[3]);
+    inf.t_eval_ms = t01;
+    inf.t_kkt_ms = t12;
+    inf.t_step_ms = t03;
+    inf.alpha_pr = alpha;
+    inf.alpha_du = a_du;
+    p->it++;
+    inf.iter = p->it;
+    ICUDA(p, cudaGetLastError());
+    if (info) *info = inf;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_solve(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
+    if (!p) return KKT_ERR_ARG;
+    kkt_ipm_info last{};
+    for (int k = 0; k <= p->opt.max_iter; ++k) {
+        const kkt_status s = kkt_ipm_step(p, st, &last);
+        if (s != KKT_OK) {
+            if (info) *info = last;
+            return s;
+        }
+    }
+    if (info) *info = last;
+    return ierr(p, KKT_ERR_MAXIT, "kkt_ipm_solve: max_iter reached");
+}
+
+kkt_status kkt_ipm_get(const kkt_ipm* p, double* d_x, double* d_y, double* d_zl, double* d_zu,
+                       double* d_s, cudaStream_t st) {
+    if (!p) return KKT_ERR_ARG;
+    const int n = p->n, m = p->m;
+    if (d_x) copy_kernel<<<grid(n), kT, 0, st>>>(n, p->x, d_x);
+    if (d_y) copy_kernel<<<grid(m), kT, 0, st>>>(m, p->y, d_y);
+    if (d_zl) copy_kernel<<<grid(n), kT, 0, st>>>(n, p->zl, d_zl);
+    if (d_zu) copy_kernel<<<grid(n), kT, 0, st>>>(n, p->zu, d_zu);
+    if (d_s && p->opt.relaxed) copy_kernel<<<grid(m), kT, 0, st>>>(m, p->s, d_s);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return KKT_ERR_CUDA;
+    return KKT_OK;
+}
+
+kkt_ctx* kkt_ipm_kkt(kkt_ipm* p) { return p ? p->kkt : nullptr; }
+
+void kkt_ipm_destroy(kkt_ipm* p) {
+    if (!p) return;
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    for (void* a : p->allocs) cudaFree(a);
+    if (p->h_red) cudaFreeHost(p->h_red);
+    if (p->kkt) kkt_destroy(p->kkt);
+    delete p;
+}
+
+}  // extern "C"

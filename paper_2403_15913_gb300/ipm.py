@@ -1,0 +1,87 @@
+"""Binding of the device IPM driver (kkt_ipm_* in include/kkt.h): argument
+marshalling only; every step runs in the CUDA library."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+from .solver import KKTError, _dptr, _stream, default_options
+
+
+class IPMSolver:
+    """Minimal filter line-search IPM on the column model, on the device."""
+
+    def __init__(self, params, scheme="lifted", tol=1e-8, max_iter=200, mu_init=0.1,
+                 relaxed=None, tau_relax=1e-8, **kkt_options):
+        self.params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        L = nat.lib()
+        ko = default_options(scheme=scheme, **kkt_options)
+        io = nat.IPMOptions()
+        L.kkt_ipm_default_options(ctypes.byref(io))
+        io.tol, io.max_iter, io.mu_init, io.tau_relax = tol, max_iter, mu_init, tau_relax
+        io.relaxed = -1 if relaxed is None else int(bool(relaxed))
+        self.max_iter = max_iter
+        h = ctypes.c_void_p()
+        st = L.kkt_ipm_create(nat.ptr_f64(self.params), ctypes.byref(ko), ctypes.byref(io),
+                              ctypes.byref(h))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_create failed")
+        self._h = h
+        n, m = ctypes.c_int(), ctypes.c_int()
+        L.kkt_tray_sizes(nat.ptr_f64(self.params), ctypes.byref(n), ctypes.byref(m), None, None)
+        self.n, self.m = n.value, m.value
+        self.info = nat.IPMInfo()
+
+    def init(self, x0=None, stream=None):
+        st = nat.lib().kkt_ipm_init(self._h, _dptr(x0), _stream(stream))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_init failed")
+
+    def step(self, stream=None):
+        """One iteration; returns the status code (0 stepped, 1 converged,
+        negative: error such as a failed line search)."""
+        return nat.lib().kkt_ipm_step(self._h, _stream(stream), ctypes.byref(self.info))
+
+    def solve(self, stream=None):
+        history = []
+        for _ in range(self.max_iter + 1):
+            st = self.step(stream)
+            history.append(dict(self.info.as_dict(), status=st))
+            if st != nat.KKT_OK:
+                break
+        return history
+
+    def get(self, stream=None):
+        import torch
+        x = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        y = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        zl = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        zu = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        s = torch.zeros(self.m, dtype=torch.float64, device="cuda")
+        st = nat.lib().kkt_ipm_get(self._h, _dptr(x), _dptr(y), _dptr(zl), _dptr(zu), _dptr(s),
+                                   _stream(stream))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_get failed")
+        return x, y, zl, zu, s
+
+    def kkt_stats(self):
+        ctx = nat.lib().kkt_ipm_kkt(self._h)
+        out = nat.Stats()
+        nat.lib().kkt_get_stats(ctx, ctypes.byref(out))
+        return out.as_dict()
+
+    def set_profiling(self, on=True):
+        nat.lib().kkt_set_profiling(nat.lib().kkt_ipm_kkt(self._h), int(bool(on)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().kkt_ipm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "kkt.h"
+#include "tray_internal.h"
 
 namespace {
 
@@ -66,16 +67,38 @@ __device__ __forceinline__ void store_partials(const double (&v)[K], const int (
     }
 }
 
-// Final reduction of kRB partial blocks, fixed order: out[q] for q < nq.
+// Final reduction of kRB partial blocks: warp q reduces quantity q, lane l
+// combines blocks l, l + 32, ... in order, then a fixed shuffle tree
+// (deterministic).  Launch with 32 * nq threads.
 __global__ void final_reduce_kernel(const double* __restrict__ part, const int* __restrict__ ops,
                                     int nq, double* __restrict__ out) {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= nq) return;
     const int op = ops[q];
-    double acc = part[q];
-    for (int b = 1; b < kRB; ++b) acc = combine(acc, part[b * kQ + q], op);
-    out[q] = acc;
+    double acc = part[lane * kQ + q];
+    for (int b = lane + 32; b < kRB; b += 32) acc = combine(acc, part[b * kQ + q], op);
+    for (int o = 16; o > 0; o >>= 1) acc = combine(acc, __shfl_down_sync(0xffffffffu, acc, o), op);
+    if (lane == 0) out[q] = acc;
 }
+
+// sum of log(g) over a thread's elements as log(prod of mantissas) plus the
+// exponents times ln 2: one logarithm per thread instead of one per element.
+struct LogSum {
+    double mant = 1.0;
+    long long expo = 0;
+    __device__ __forceinline__ void add(double g) {
+        int e;
+        const double m = frexp(g, &e);       // g = m 2^e, m in [0.5, 1)
+        mant *= m;
+        expo += e;
+        int e2;
+        mant = frexp(mant, &e2);             // keep the running product normalised
+        expo += e2;
+    }
+    __device__ __forceinline__ double value() const {
+        return log(mant) + (double)expo * 0.69314718055994530942;
+    }
+};
 
 struct Bounds {
     const double *xlo, *xhi;
@@ -236,15 +259,21 @@ measure_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x
                const double* __restrict__ s, const double* __restrict__ c, double* __restrict__ part) {
     double v[2] = {0.0, 0.0};
     const int ops[2] = {SUM, SUM};
+    LogSum ls;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
-            v[1] += log(x[i] - B.xlo[i]) + log(B.xhi[i] - x[i]);
+            ls.add(x[i] - B.xlo[i]);
+            ls.add(B.xhi[i] - x[i]);
         } else {
             const int k = i - n;
             v[0] += fabs(relaxed ? c[k] - s[k] : c[k]);
-            if (relaxed) v[1] += log(s[k] + B.tau) + log(B.tau - s[k]);
+            if (relaxed) {
+                ls.add(s[k] + B.tau);
+                ls.add(B.tau - s[k]);
+            }
         }
     }
+    v[1] = ls.value();
     store_partials<2>(v, ops, part);
 }
 
@@ -343,10 +372,23 @@ Bounds bounds_of(const kkt_ipm* p) { return Bounds{p->xlo, p->xhi, p->opt.tau_re
 // reduce kRB partials to q results and copy them to the host
 kkt_status finish_reduce(kkt_ipm* p, const int* h_ops, int nq, cudaStream_t st, double* out) {
     ICUDA(p, cudaMemcpyAsync(p->ops, h_ops, nq * sizeof(int), cudaMemcpyHostToDevice, st));
-    final_reduce_kernel<<<1, 32, 0, st>>>(p->part, p->ops, nq, p->red);
+    final_reduce_kernel<<<1, 32 * nq, 0, st>>>(p->part, p->ops, nq, p->red);
     ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
     ICUDA(p, cudaStreamSynchronize(st));
     for (int q = 0; q < nq; ++q) out[q] = p->h_red[q];
+    return KKT_OK;
+}
+
+// objective at w via partials in part[b * kQ + kQ - 1] and the final reduce
+kkt_status objective(kkt_ipm* p, const double* w, cudaStream_t st, double* f) {
+    if (!kktgb::tray_objective_partials(p->params, w, p->part + (kQ - 1), kQ, kRB, st))
+        return ierr(p, KKT_ERR_CUDA, "objective kernel launch failed");
+    static const int ops[1] = {SUM};
+    ICUDA(p, cudaMemcpyAsync(p->ops, ops, sizeof(int), cudaMemcpyHostToDevice, st));
+    final_reduce_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->ops, 1, p->red);
+    ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    *f = p->h_red[0];
     return KKT_OK;
 }
 
@@ -519,7 +561,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     inf.iter = p->it;
     cudaEventRecord(p->ev[0], st);
     // 1. derivatives
-    ITRY(kkt_tray_eval(p->params, p->x, p->y, 1.0, p->f, p->grad, p->c, p->Jv, p->Wv, st));
+    ITRY(kkt_tray_eval(p->params, p->x, p->y, 1.0, nullptr, p->grad, p->c, p->Jv, p->Wv, st));
     jt_kernel<<<grid(n), kT, 0, st>>>(n, p->jt_cp, p->jt_ri, p->jt_idx, p->Jv, p->y, p->jty);
     cudaEventRecord(p->ev[1], st);
     // 2. optimality error and barrier update
@@ -529,9 +571,8 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     double ev6[6];
     ITRY(finish_reduce(p, eops, 6, st, ev6));
     Errors E{ev6[0], ev6[1], ev6[2], ev6[3], ev6[4], ev6[5]};
-    ICUDA(p, cudaMemcpyAsync(p->h_red, p->f, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ICUDA(p, cudaStreamSynchronize(st));
-    const double fval = p->h_red[0];
+    double fval = 0.0;
+    ITRY(objective(p, p->x, st, &fval));
     const double e0 = err_mu(p, E, 0.0);
     inf.objective = fval;
     inf.inf_du = E.du;
@@ -596,13 +637,10 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     for (ls = 1; ls <= kMaxLs; ++ls) {
         trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, alpha, p->x, p->dx, p->s, p->ds,
                                                           p->xt, p->st);
-        ITRY(kkt_tray_eval(p->params, p->xt, nullptr, 1.0, p->f, nullptr, p->ct, nullptr, nullptr, st));
-        double tht = 0, lst = 0;
-        ICUDA(p, cudaMemcpyAsync(p->red + kQ - 1, p->f, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ITRY(kkt_tray_eval(p->params, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
+        double tht = 0, lst = 0, ft = 0;
         ITRY(measures(p, p->xt, p->st, p->ct, st, &tht, &lst));
-        ICUDA(p, cudaMemcpyAsync(p->h_red, p->red + kQ - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
-        ICUDA(p, cudaStreamSynchronize(st));
-        const double ft = p->h_red[0];
+        ITRY(objective(p, p->xt, st, &ft));
         const double pht = ft - mu * lst;
         bool ok = tht <= p->theta_max;
         for (const auto& fe : p->filter)

@@ -13,6 +13,14 @@
 namespace kktgb {
 
 constexpr int kThreads = 256;
+
+// Kernels that run inside the graph of one CG iteration take `active`: when
+// it points to 0 (CG has converged) they return at once, so iterations
+// enqueued after convergence do nothing.  NULL means always active.
+#define KKT_RETURN_IF_INACTIVE(active) \
+    do {                               \
+        if ((active) && *(active) == 0) return; \
+    } while (0)
 constexpr int kSubtreeThreads = 64;   // CTA size of the small-subtree kernels
 constexpr int kRedBlocks = 296;   // 2 x 148..152 SMs: partial-sum slots
 
@@ -288,7 +296,9 @@ syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, double* __r
 // L21 forms its product with z and scatters it.
 __global__ void __launch_bounds__(kThreads)
 forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                     const double* __restrict__ dinv, double* __restrict__ x) {
+                     const double* __restrict__ dinv, double* __restrict__ x,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     __shared__ double D[64 * 64];
     __shared__ double z[64];
     const int s = lvl_sn[blockIdx.x];
@@ -301,8 +311,11 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __res
         const int lane = tid;
         double z0 = lane < c ? x[f + lane] : 0.0;
         double z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
+        const double di0 = lane < c ? dinv[f + lane] : 0.0;
+        const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
         for (int j = 0; j < c; ++j) {
-            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dinv[f + j];
+            const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
+            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dj;
             if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
             if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
             if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
@@ -325,7 +338,9 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __res
 // the diagonal block.
 __global__ void __launch_bounds__(kThreads)
 backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                      const double* __restrict__ dinv, double* __restrict__ x) {
+                      const double* __restrict__ dinv, double* __restrict__ x,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     __shared__ double D[64 * 64];
     __shared__ double part[kThreads / 32][64];
     extern __shared__ double xb[];
@@ -356,8 +371,11 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
         for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
         t0 = lane < c ? x[f + lane] - t0 : 0.0;
         t1 = lane + 32 < c ? x[f + lane + 32] - t1 : 0.0;
+        const double di0 = lane < c ? dinv[f + lane] : 0.0;
+        const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
         for (int j = c - 1; j >= 0; --j) {
-            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dinv[f + j];
+            const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
+            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dj;
             if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
             if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
             if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
@@ -404,7 +422,9 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
 __global__ void __launch_bounds__(kSubtreeThreads)
 forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
                        const double* __restrict__ Lx, const double* __restrict__ dinv,
-                       double* __restrict__ x) {
+                       double* __restrict__ x,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     __shared__ double z[64];
     extern __shared__ double D[];   // diagonal block of the current supernode
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -418,8 +438,11 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
             const int lane = tid;
             double z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
             double z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
+            const double di0 = lane < c ? dinv[f + lane] : 0.0;
+            const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
             for (int j = 0; j < c; ++j) {
-                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dinv[f + j];
+                const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
+                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dj;
                 if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
                 if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
                 if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
@@ -443,7 +466,9 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
 __global__ void __launch_bounds__(kSubtreeThreads)
 backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
                         const double* __restrict__ Lx, const double* __restrict__ dinv,
-                        double* __restrict__ x) {
+                        double* __restrict__ x,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     __shared__ double part[kSubtreeThreads / 32][64];
     extern __shared__ double dyn[];   // [diagonal block | x of the rows below]
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -473,8 +498,11 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
             for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
             t0 = lane < c ? __ldcg(x + f + lane) - t0 : 0.0;
             t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) - t1 : 0.0;
+            const double di0 = lane < c ? dinv[f + lane] : 0.0;
+            const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
             for (int j = c - 1; j >= 0; --j) {
-                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dinv[f + j];
+                const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
+                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dj;
                 if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
                 if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
                 if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
@@ -488,13 +516,17 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
 }
 
 __global__ void gather_kernel(int n, const int* __restrict__ idx, const double* __restrict__ in,
-                              double* __restrict__ out) {
+                              double* __restrict__ out,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[i] = in[idx[i]];
 }
 
 __global__ void scatter_kernel(int n, const int* __restrict__ idx, const double* __restrict__ in,
-                               double* __restrict__ out) {
+                               double* __restrict__ out,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[idx[i]] = in[i];
 }
@@ -505,7 +537,9 @@ __global__ void jt_axpy_kernel(int n, const int* __restrict__ jt_ptr, const int*
                                const int* __restrict__ jt_idx, const double* __restrict__ J,
                                const double* __restrict__ ax, const double* __restrict__ ay,
                                const double* __restrict__ Dscale, double Dconst, double alpha,
-                               double* __restrict__ out) {
+                               double* __restrict__ out,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = jt_ptr[i]; q < jt_ptr[i + 1]; ++q) {
@@ -521,7 +555,9 @@ __global__ void jt_axpy_kernel(int n, const int* __restrict__ jt_ptr, const int*
 __global__ void j_apply_kernel(int m, const int* __restrict__ j_ptr, const int* __restrict__ j_col,
                                const double* __restrict__ J, const double* __restrict__ x,
                                const double* __restrict__ by, const double* __restrict__ Dscale,
-                               double Dconst, double* __restrict__ out) {
+                               double Dconst, double* __restrict__ out,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = j_ptr[r]; q < j_ptr[r + 1]; ++q) s += J[q] * x[j_col[q]];
@@ -657,7 +693,9 @@ __global__ void fill_kernel(int n, double v, double* __restrict__ y) {
 // sums, a single CTA adds them in a fixed order.
 __global__ void __launch_bounds__(kThreads)
 dot_partial_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
-                   double* __restrict__ part) {
+                   double* __restrict__ part,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s += a[i] * b[i];
@@ -666,7 +704,9 @@ dot_partial_kernel(int n, const double* __restrict__ a, const double* __restrict
 }
 
 __global__ void __launch_bounds__(kThreads)
-dot_final_kernel(int nparts, const double* __restrict__ part, double* __restrict__ out) {
+dot_final_kernel(int nparts, const double* __restrict__ part, double* __restrict__ out,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
     s = block_sum(s);
@@ -677,7 +717,9 @@ dot_final_kernel(int nparts, const double* __restrict__ part, double* __restrict
 // x += alpha p; r -= alpha q   with alpha = sc[rr] / sc[pq]
 __global__ void cg_update_xr_kernel(int m, const double* __restrict__ sc, int i_rr, int i_pq,
                                     const double* __restrict__ p, const double* __restrict__ q,
-                                    double* __restrict__ x, double* __restrict__ r) {
+                                    double* __restrict__ x, double* __restrict__ r,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     const double alpha = sc[i_rr] / sc[i_pq];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
@@ -687,10 +729,35 @@ __global__ void cg_update_xr_kernel(int m, const double* __restrict__ sc, int i_
 
 // p = r + beta p   with beta = sc[rr_new] / sc[rr_old]
 __global__ void cg_update_p_kernel(int m, const double* __restrict__ sc, int i_new, int i_old,
-                                   const double* __restrict__ r, double* __restrict__ p) {
+                                   const double* __restrict__ r, double* __restrict__ p,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
     const double beta = sc[i_new] / sc[i_old];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
         p[i] = r[i] + beta * p[i];
+}
+
+// CG bookkeeping on the device (HyKKT, Eq. schurcomp): cg[0] = active flag,
+// cg[1] = iterations.  Start: stop = tol sqrt(rr0); active when
+// sqrt(rr0) > stop.  After each iteration: rr_old <- rr_new, iterations + 1,
+// active while sqrt(rr) > stop and iterations < max_cg.
+__global__ void cg_init_kernel(double* __restrict__ sc, int i_rr, int i_stop, double tol, int max_cg,
+                               int* __restrict__ cg) {
+    const double rr = sc[i_rr];
+    const double stop = tol * sqrt(rr);
+    sc[i_stop] = stop;
+    cg[0] = (sqrt(rr) > stop && max_cg > 0) ? 1 : 0;
+    cg[1] = 0;
+}
+
+__global__ void cg_check_kernel(double* __restrict__ sc, int i_new, int i_old, int i_stop, int max_cg,
+                                int* __restrict__ cg) {
+    if (cg[0] == 0) return;
+    const double rr = sc[i_new];
+    sc[i_old] = rr;
+    const int it = cg[1] + 1;
+    cg[1] = it;
+    cg[0] = (sqrt(rr) > sc[i_stop] && it < max_cg) ? 1 : 0;
 }
 
 }  // namespace kktgb

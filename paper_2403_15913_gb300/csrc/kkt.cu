@@ -87,6 +87,13 @@ struct kkt_ctx {
     const double* f_C = nullptr;   // dual block of the target system (device) or NULL
     DevBuf<double> d_Cbuf;
     bool device_ready = false;   // false for host-only analyses
+    // CUDA graphs captured once after the analysis: the triangular solves on
+    // w_xp, and one HyKKT CG iteration on the internal CG vectors
+    cudaGraph_t tri_graph = nullptr, cg_graph = nullptr;
+    cudaGraphExec_t tri_exec = nullptr, cg_exec = nullptr;
+    size_t tri_nodes = 0, cg_nodes = 0;
+    int* d_cg = nullptr;        // [active, iterations]
+    int* h_cg = nullptr;        // pinned
     // tracing
     bool profiling = false;
     kkt_stats stats{};
@@ -102,7 +109,9 @@ struct kkt_ctx {
 namespace {
 
 // device scalar slots
-enum { SC_RMAX = 0, SC_VMAX, SC_BMAX, SC_KNORM, SC_DOT0, SC_DOT1, SC_DOT2, SC_DOT3, SC_COUNT };
+enum { SC_RMAX = 0, SC_VMAX, SC_BMAX, SC_KNORM, SC_DOT0, SC_DOT1, SC_DOT2, SC_DOT3, SC_STOP,
+       SC_COUNT };
+constexpr int kCgBatch = 8;   // CG iterations enqueued between convergence checks
 
 thread_local std::string g_err;   // last error of calls that have no context
 
@@ -553,29 +562,31 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(alloc(c, &c->v_sigma, n));
     TRY(alloc(c, &c->v_D, std::max(1, m)));
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, 16 * sizeof(double)));
+    TRY(alloc(c, &c->d_cg, 2));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_cg, 2 * sizeof(int)));
     return KKT_OK;
 }
 
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
 // levels bottom-up, then levels top-down and subtree tasks.
-void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st) {
+void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st, const int* active) {
     if (c->ntasks > 0)
         forward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(double), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp);
+            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp, active);
     for (int l = 0; l < c->nlev; ++l) {
         int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         forward_level_kernel<<<cnt, kThreads, 0, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                       c->d_Lx, c->d_dinv, xp);
+                                                       c->d_Lx, c->d_dinv, xp, active);
     }
     for (int l = c->nlev - 1; l >= 0; --l) {
         int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         size_t sm = (size_t)c->lvl_max_rb[l] * sizeof(double);
         backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                         c->d_Lx, c->d_dinv, xp);
+                                                         c->d_Lx, c->d_dinv, xp, active);
     }
     if (c->ntasks > 0)
         backward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(double), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp);
+            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp, active);
 }
 
 // x <- K^{-1} x  (in and out may alias; uses w_xp)
@@ -584,18 +595,23 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
     const int sp = span_begin(c, 2, st);
     c->stats.kinv_calls++;
     c->stats.launches += 2 + 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0);
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp);
-    enqueue_triangular_solves(c, c->w_xp, st);
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out);
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp, nullptr);
+    if (c->tri_exec) {
+        CUDA_TRY(c, cudaGraphLaunch(c->tri_exec, st));
+    } else {
+        enqueue_triangular_solves(c, c->w_xp, st, nullptr);
+    }
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out, nullptr);
     span_end(c, sp, st);
     CUDA_TRY(c, cudaGetLastError());
     return KKT_OK;
 }
 
-kkt_status dot(kkt_ctx* c, int len, const double* a, const double* b, int slot, cudaStream_t st) {
+kkt_status dot(kkt_ctx* c, int len, const double* a, const double* b, int slot, cudaStream_t st,
+               const int* active = nullptr) {
     c->stats.launches += 2;
-    dot_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(len, a, b, c->d_part);
-    dot_final_kernel<<<1, kThreads, 0, st>>>(kRedBlocks, c->d_part, c->d_sc + slot);
+    dot_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(len, a, b, c->d_part, active);
+    dot_final_kernel<<<1, kThreads, 0, st>>>(kRedBlocks, c->d_part, c->d_sc + slot, active);
     return KKT_OK;
 }
 
@@ -624,15 +640,64 @@ kkt_status lifted_precond(kkt_ctx* c, const double* rx, const double* ry, double
     c->stats.launches += 2;
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
                                                      c->f_J, rx, ry, c->f_D, c->f_Dconst, 1.0,
-                                                     c->w_t);
+                                                     c->w_t, nullptr);
     TRY(apply_kinv(c, c->w_t, dx, st));
     j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, dx, ry,
-                                                     c->f_D, c->f_Dconst, dy);
+                                                     c->f_D, c->f_Dconst, dy, nullptr);
+    return KKT_OK;
+}
+
+// One CG iteration on S_gamma = J K_gamma^{-1} J^T with the internal vectors
+// (p = w_p, S p = w_sp, x = w_cgx, r = w_res), every kernel guarded by the
+// device flag d_cg[0].
+void enqueue_cg_iteration(kkt_ctx* c, cudaStream_t st) {
+    const int n = c->n, m = c->m;
+    const int* act = c->d_cg;
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->v_J,
+                                                     nullptr, c->w_p, nullptr, 1.0, 1.0, c->w_tn, act);
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, c->w_xp, act);
+    enqueue_triangular_solves(c, c->w_xp, st, act);
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, c->w_tn, act);
+    j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
+                                                     nullptr, nullptr, 1.0, c->w_sp, act);
+    dot(c, m, c->w_p, c->w_sp, SC_DOT2, st, act);
+    cg_update_xr_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, SC_DOT0, SC_DOT2, c->w_p,
+                                                          c->w_sp, c->w_cgx, c->w_res, act);
+    dot(c, m, c->w_res, c->w_res, SC_DOT1, st, act);
+    cg_update_p_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, SC_DOT1, SC_DOT0, c->w_res,
+                                                         c->w_p, act);
+    cg_check_kernel<<<1, 1, 0, st>>>(c->d_sc, SC_DOT1, SC_DOT0, SC_STOP, c->opt.max_cg, c->d_cg);
+}
+
+// Capture the triangular-solve sequence and (HyKKT) one CG iteration as
+// CUDA graphs; they only touch buffers owned by the context.
+kkt_status capture_graphs(kkt_ctx* c) {
+    cudaStream_t cs;
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    auto capture = [&](auto&& body, cudaGraph_t* g, cudaGraphExec_t* e, size_t* nodes) -> cudaError_t {
+        cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) return err;
+        body();
+        err = cudaStreamEndCapture(cs, g);
+        if (err != cudaSuccess) return err;
+        err = cudaGraphInstantiate(e, *g, 0);
+        if (err != cudaSuccess) return err;
+        return cudaGraphGetNodes(*g, nullptr, nodes);
+    };
+    cudaError_t err = capture([&] { enqueue_triangular_solves(c, c->w_xp, cs, nullptr); },
+                              &c->tri_graph, &c->tri_exec, &c->tri_nodes);
+    if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
+        err = capture([&] { enqueue_cg_iteration(c, cs); }, &c->cg_graph, &c->cg_exec, &c->cg_nodes);
+    cudaStreamDestroy(cs);
+    if (err != cudaSuccess) return set_err(c, KKT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
     return KKT_OK;
 }
 
 // HyKKT inner solve (Eq. hykkt / Eq. schurcomp): d = K_orig^{-1} r up to the
-// CG tolerance.  Returns CG iterations through *its.
+// CG tolerance.  Returns CG iterations through *its.  The CG iterations run
+// as graph launches in batches of kCgBatch between convergence checks; the
+// device flag makes the iterations after convergence no-ops, so the iteration
+// count equals that of a check after every iteration.
 kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* dx, double* dy,
                        cudaStream_t st, int* its, bool* cg_ok) {
     const int n = c->n, m = c->m;
@@ -640,46 +705,42 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
     c->stats.launches += 4;
     // r_gamma = r_x + gamma J^T r_y ; q = K_gamma^{-1} r_gamma
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
-                                                     c->f_J, rx, ry, nullptr, 1.0, gamma, c->w_rg);
+                                                     c->f_J, rx, ry, nullptr, 1.0, gamma, c->w_rg, nullptr);
     TRY(apply_kinv(c, c->w_rg, c->w_q, st));
-    // rhs = J q - r_y  (stored in w_res: the CG residual starts at rhs)
+    // rhs = J q - r_y (the CG residual starts at rhs, x at 0)
     j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, c->w_q, ry,
-                                                     nullptr, 1.0, c->w_res);
+                                                     nullptr, 1.0, c->w_res, nullptr);
     CUDA_TRY(c, cudaMemsetAsync(c->w_cgx, 0, m * sizeof(double), st));
     CUDA_TRY(c, cudaMemcpyAsync(c->w_p, c->w_res, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(dot(c, m, c->w_res, c->w_res, SC_DOT0, st));
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_DOT0, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(c, cudaStreamSynchronize(st));
-    double rr = c->h_sc[0];
-    const double stop = c->opt.tol_cg * std::sqrt(rr);
-    int it = 0;
-    int cur = SC_DOT0, nxt = SC_DOT1;
-    while (std::sqrt(rr) > stop && it < c->opt.max_cg) {
-        c->stats.launches += 4;
-        // Sp = J K^{-1} J^T p
-        jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
-                                                         c->f_J, nullptr, c->w_p, nullptr, 1.0, 1.0,
-                                                         c->w_tn);
-        TRY(apply_kinv(c, c->w_tn, c->w_tn, st));
-        j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, c->w_tn,
-                                                         nullptr, nullptr, 1.0, c->w_sp);
-        TRY(dot(c, m, c->w_p, c->w_sp, SC_DOT2, st));
-        cg_update_xr_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, cur, SC_DOT2, c->w_p,
-                                                              c->w_sp, c->w_cgx, c->w_res);
-        TRY(dot(c, m, c->w_res, c->w_res, nxt, st));
-        cg_update_p_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, nxt, cur, c->w_res, c->w_p);
-        CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + nxt, sizeof(double), cudaMemcpyDeviceToHost, st));
+    cg_init_kernel<<<1, 1, 0, st>>>(c->d_sc, SC_DOT0, SC_STOP, c->opt.tol_cg, c->opt.max_cg, c->d_cg);
+    const int sp = span_begin(c, 3, st);
+    while (true) {
+        for (int b = 0; b < kCgBatch; ++b) {
+            if (c->cg_exec) {
+                CUDA_TRY(c, cudaGraphLaunch(c->cg_exec, st));
+            } else {
+                enqueue_cg_iteration(c, st);
+            }
+        }
+        c->stats.launches += (long long)kCgBatch * (long long)c->cg_nodes;
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_cg, c->d_cg, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaStreamSynchronize(st));
-        rr = c->h_sc[0];
-        std::swap(cur, nxt);
-        ++it;
+        if (c->h_cg[0] == 0) break;
     }
+    span_end(c, sp, st);
+    const int it = c->h_cg[1];
+    c->stats.kinv_calls += it;
     *its = it;
-    *cg_ok = std::sqrt(rr) <= stop;
+    // converged unless the iteration limit stopped it (same test as the loop)
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_DOT1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc + 1, c->d_sc + SC_STOP, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    *cg_ok = it < c->opt.max_cg || !(std::sqrt(c->h_sc[0]) > c->h_sc[1]);
     // dx = K_gamma^{-1} (r_gamma - J^T dy)
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
                                                      c->f_J, c->w_rg, c->w_cgx, nullptr, 1.0, -1.0,
-                                                     c->w_tn);
+                                                     c->w_tn, nullptr);
     TRY(apply_kinv(c, c->w_tn, dx, st));
     CUDA_TRY(c, cudaMemcpyAsync(dy, c->w_cgx, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return KKT_OK;
@@ -768,6 +829,12 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
                              (int)(kSmemCapElems * sizeof(double)));
         cudaFuncSetAttribute(backward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              160 * 1024);
+        st = capture_graphs(c);
+        if (st != KKT_OK) {
+            set_err(nullptr, st, c->err);
+            kkt_destroy(c);
+            return st;
+        }
     }
     c->device_ready = device;
     *out = c;
@@ -961,7 +1028,7 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
     if (it > c->opt.max_refine) it = c->opt.max_refine;
     if (d_ds && c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
         j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, d_dx, d_ry,
-                                                         nullptr, 1.0, d_ds);
+                                                         nullptr, 1.0, d_ds, nullptr);
     }
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1024,9 +1091,9 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     double* xp = nullptr;
     TRY(noalloc_scratch(c, &xp));
     const int n = c->n;
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp);
-    enqueue_triangular_solves(c, xp, st);
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x);
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp, nullptr);
+    enqueue_triangular_solves(c, xp, st, nullptr);
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x, nullptr);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
     return KKT_OK;
@@ -1077,6 +1144,11 @@ const char* kkt_last_error(const kkt_ctx* c) { return c ? c->err.c_str() : g_err
 
 void kkt_destroy(kkt_ctx* c) {
     if (!c) return;
+    if (c->tri_exec) cudaGraphExecDestroy(c->tri_exec);
+    if (c->tri_graph) cudaGraphDestroy(c->tri_graph);
+    if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+    if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
+    if (c->h_cg) cudaFreeHost(c->h_cg);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_sc) cudaFreeHost(c->h_sc);

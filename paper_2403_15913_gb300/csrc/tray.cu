@@ -18,6 +18,7 @@
 #include <string>
 
 #include "kkt.h"
+#include "tray_internal.h"
 
 namespace {
 
@@ -167,7 +168,48 @@ __global__ void tray_objective_kernel(TrayP P, const double* __restrict__ w, dou
     if (threadIdx.x == 0) *f = red[0];
 }
 
+// Objective partials over a fixed grid: CTA b sums its grid-stride share of
+// the (stage, tray) terms and writes part[b * stride].
+__global__ void __launch_bounds__(256)
+tray_objective_partials_kernel(TrayP P, const double* __restrict__ w, double* __restrict__ part,
+                               int stride) {
+    __shared__ double red[256 / 32];
+    const int k = P.k;
+    const long long total = (long long)(P.T + 1) * (k + 1);
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / (k + 1)), i = (int)(e % (k + 1));
+        const long long base = (long long)t * P.nst();
+        if (i < k) {
+            const double d = w[base + i] - P.xbar;
+            s = fma(d, d, s);
+        } else {
+            const double d = w[base + 2 * k] - P.ubar;
+            s = fma(P.rho * d, d, s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int q = 0; q < 256 / 32; ++q) acc += red[q];
+        part[(long long)blockIdx.x * stride] = acc;
+    }
+}
+
 }  // namespace
+
+namespace kktgb {
+bool tray_objective_partials(const double* params, const double* d_w, double* d_part, int stride,
+                             int nblocks, cudaStream_t stream) {
+    TrayP P;
+    if (!unpack(params, P) || !d_w || !d_part || nblocks <= 0) return false;
+    tray_objective_partials_kernel<<<nblocks, 256, 0, stream>>>(P, d_w, d_part, stride);
+    return cudaGetLastError() == cudaSuccess;
+}
+}  // namespace kktgb
 
 extern "C" {
 

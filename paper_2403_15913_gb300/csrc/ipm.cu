@@ -178,15 +178,15 @@ __global__ void prepare_kernel(int n, int m, int relaxed, Bounds B, double mu,
                                double* __restrict__ ry, double* __restrict__ D) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
-            const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
-            sigma[i] = zl[i] / gl + zu[i] / gu;
-            rx[i] = -(grad[i] - mu / gl + mu / gu + jty[i]);
+            const double igl = 1.0 / (x[i] - B.xlo[i]), igu = 1.0 / (B.xhi[i] - x[i]);
+            sigma[i] = zl[i] * igl + zu[i] * igu;
+            rx[i] = -(grad[i] - mu * igl + mu * igu + jty[i]);
         } else {
             const int k = i - n;
             if (relaxed) {
-                const double hl = s[k] + B.tau, hu = B.tau - s[k];
-                const double sig = vl[k] / hl + vu[k] / hu;
-                const double gphi = -mu / hl + mu / hu;
+                const double ihl = 1.0 / (s[k] + B.tau), ihu = 1.0 / (B.tau - s[k]);
+                const double sig = vl[k] * ihl + vu[k] * ihu;
+                const double gphi = -mu * ihl + mu * ihu;
                 D[k] = sig;
                 ry[k] = -(c[k] - s[k]) - (gphi - y[k]) / sig;
             } else {
@@ -212,25 +212,27 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
             const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
+            const double igl = 1.0 / gl, igu = 1.0 / gu;
             const double d = dx[i];
-            const double a = mu / gl - zl[i] - (zl[i] / gl) * d;
-            const double b = mu / gu - zu[i] + (zu[i] / gu) * d;
+            const double a = mu * igl - zl[i] - (zl[i] * igl) * d;
+            const double b = mu * igu - zu[i] + (zu[i] * igu) * d;
             dzl[i] = a;
             dzu[i] = b;
             if (d < 0) v[0] = fmin(v[0], -tau * gl / d);
             if (d > 0) v[0] = fmin(v[0], tau * gu / d);
             if (a < 0) v[1] = fmin(v[1], -tau * zl[i] / a);
             if (b < 0) v[1] = fmin(v[1], -tau * zu[i] / b);
-            v[2] += (grad[i] - mu / gl + mu / gu) * d;
+            v[2] += (grad[i] - mu * igl + mu * igu) * d;
         } else if (relaxed) {
             const int k = i - n;
             const double hl = s[k] + B.tau, hu = B.tau - s[k];
-            const double sig = vl[k] / hl + vu[k] / hu;
-            const double gphi = -mu / hl + mu / hu;
+            const double ihl = 1.0 / hl, ihu = 1.0 / hu;
+            const double sig = vl[k] * ihl + vu[k] * ihu;
+            const double gphi = -mu * ihl + mu * ihu;
             const double d = (dy[k] - gphi + y[k]) / sig;
             ds[k] = d;
-            const double a = mu / hl - vl[k] - (vl[k] / hl) * d;
-            const double b = mu / hu - vu[k] + (vu[k] / hu) * d;
+            const double a = mu * ihl - vl[k] - (vl[k] * ihl) * d;
+            const double b = mu * ihu - vu[k] + (vu[k] * ihu) * d;
             dvl[k] = a;
             dvu[k] = b;
             if (d < 0) v[0] = fmin(v[0], -tau * hl / d);
@@ -290,20 +292,20 @@ __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, do
         if (i < n) {
             const double xn = x[i] + alpha * dx[i];
             x[i] = xn;
-            const double gl = xn - B.xlo[i], gu = B.xhi[i] - xn;
+            const double igl = 1.0 / (xn - B.xlo[i]), igu = 1.0 / (B.xhi[i] - xn);
             const double a = zl[i] + alpha_du * dzl[i], b = zu[i] + alpha_du * dzu[i];
-            zl[i] = fmax(fmin(a, k * mu / gl), mu / (k * gl));
-            zu[i] = fmax(fmin(b, k * mu / gu), mu / (k * gu));
+            zl[i] = fmax(fmin(a, k * mu * igl), (mu / k) * igl);
+            zu[i] = fmax(fmin(b, k * mu * igu), (mu / k) * igu);
         } else {
             const int q = i - n;
             y[q] += alpha * dy[q];
             if (relaxed) {
                 const double sn = s[q] + alpha * ds[q];
                 s[q] = sn;
-                const double hl = sn + B.tau, hu = B.tau - sn;
+                const double ihl = 1.0 / (sn + B.tau), ihu = 1.0 / (B.tau - sn);
                 const double a = vl[q] + alpha_du * dvl[q], b = vu[q] + alpha_du * dvu[q];
-                vl[q] = fmax(fmin(a, k * mu / hl), mu / (k * hl));
-                vu[q] = fmax(fmin(b, k * mu / hu), mu / (k * hu));
+                vl[q] = fmax(fmin(a, k * mu * ihl), (mu / k) * ihl);
+                vu[q] = fmax(fmin(b, k * mu * ihu), (mu / k) * ihu);
             }
         }
     }

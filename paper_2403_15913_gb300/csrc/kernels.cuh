@@ -43,28 +43,36 @@ struct Plan {
 };
 
 // ------------------------------------------------------------- assembly
+// Js = J scaled row-wise by sqrt(D) (D > 0 in both schemes), so that every
+// J^T D J product of the assembly is one FMA: D_r J_ra J_rb = Js_a Js_b.
+__global__ void scale_rows_sqrt_kernel(int nnz, const int* __restrict__ jrow,
+                                       const double* __restrict__ J, const double* __restrict__ D,
+                                       double Dconst, double* __restrict__ Js) {
+    const double sc = sqrt(Dconst);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x)
+        Js[q] = J[q] * (D ? sqrt(D[jrow[q]]) : sc);
+}
+
 // One thread per stored entry of the lower triangle of P K P^T: sums its
-// sources (W entry, diagonal Sigma_x + delta_x, products D_r J_ra J_rb) and
+// sources (W entry, diagonal Sigma_x + delta_x, products Js_a Js_b) and
 // writes the panel slot.  Source encoding: b == -1 -> W[a];
-// b == -2 -> sigma[a] + delta_x; b >= 0 -> D[jrow[a]] * J[a] * J[b].
+// b == -2 -> sigma[a] + delta_x; b >= 0 -> Js[a] * Js[b].
 __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot,
                                 const long long* __restrict__ sptr,
-                                const int2* __restrict__ src, const int* __restrict__ jrow,
-                                const double* __restrict__ W, const double* __restrict__ J,
-                                const double* __restrict__ sigma, const double* __restrict__ D,
-                                double Dconst, double delta_x, double* __restrict__ Lx) {
+                                const int2* __restrict__ src, const double* __restrict__ W,
+                                const double* __restrict__ Js, const double* __restrict__ sigma,
+                                double delta_x, double* __restrict__ Lx) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
          e += (long long)gridDim.x * blockDim.x) {
         double v = 0.0;
         for (long long q = sptr[e]; q < sptr[e + 1]; ++q) {
-            int2 s = src[q];
+            const int2 s = src[q];
             if (s.y == -1) {
                 v += W[s.x];
             } else if (s.y == -2) {
                 v += sigma[s.x] + delta_x;
             } else {
-                double d = D ? D[jrow[s.x]] : Dconst;
-                v += d * J[s.x] * J[s.y];
+                v = fma(Js[s.x], Js[s.y], v);
             }
         }
         Lx[slot[e]] = v;
@@ -245,7 +253,7 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__ L
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) g[(e % c) + (long long)(e / c) * r] = sm[e];
 }
 
-constexpr int kTrsmWarps = 4;   // rows per TRSM CTA (one per warp)
+constexpr int kTrsmWarps = 8;   // rows per TRSM CTA (one per warp)
 
 // X L11^T = A21: task = (supernode, first below-row); warp w solves row
 // task.y + w with lanes over the columns (two per lane).  The columns of L11
@@ -289,6 +297,19 @@ syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, double* __r
     syrk_tile(P, s, P.sn_c[s], P.sn_r[s], Lx + P.sn_lptr[s], Lx, task.y, task.z);
 }
 
+// After the factorisation: Lhat = L diag(1/l) (unit diagonal; the reciprocal
+// pivots stay in dinv).  The triangular solves then substitute without
+// divisions: L z = b is Lhat u = b with z = u / l, and L^T w = z is
+// Lhat^T w = u / l^2.  One CTA per supernode.
+__global__ void __launch_bounds__(kThreads)
+normalize_panels_kernel(Plan P, int ns, double* __restrict__ Lx, const double* __restrict__ dinv) {
+    for (int s = blockIdx.x; s < ns; s += gridDim.x) {
+        const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+        double* A = Lx + P.sn_lptr[s];
+        for (int e = threadIdx.x; e < r * c; e += blockDim.x) A[e] *= dinv[f + e / r];
+    }
+}
+
 // ------------------------------------------------------------- solves
 // Forward substitution L z = b, one CTA per supernode of a level: the
 // diagonal block in shared memory, one warp substitutes with shuffles
@@ -311,12 +332,8 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __res
         const int lane = tid;
         double z0 = lane < c ? x[f + lane] : 0.0;
         double z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
-        const double di0 = lane < c ? dinv[f + lane] : 0.0;
-        const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-        for (int j = 0; j < c; ++j) {
-            const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
-            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dj;
-            if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
+        for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
+            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
             if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
             if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
         }
@@ -369,14 +386,13 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
     if (tid < 32) {
         double t0 = 0.0, t1 = 0.0;
         for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
-        t0 = lane < c ? x[f + lane] - t0 : 0.0;
-        t1 = lane + 32 < c ? x[f + lane + 32] - t1 : 0.0;
+        // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
         const double di0 = lane < c ? dinv[f + lane] : 0.0;
         const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-        for (int j = c - 1; j >= 0; --j) {
-            const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
-            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dj;
-            if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
+        t0 = lane < c ? x[f + lane] * di0 * di0 - t0 : 0.0;
+        t1 = lane + 32 < c ? x[f + lane + 32] * di1 * di1 - t1 : 0.0;
+        for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
+            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
             if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
             if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
         }
@@ -438,12 +454,8 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
             const int lane = tid;
             double z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
             double z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
-            const double di0 = lane < c ? dinv[f + lane] : 0.0;
-            const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-            for (int j = 0; j < c; ++j) {
-                const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
-                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31) * dj;
-                if (j < 32) { if (lane == j) z0 = zj; } else { if (lane == j - 32) z1 = zj; }
+            for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
+                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
                 if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
                 if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
             }
@@ -496,14 +508,13 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
         if (tid < 32) {
             double t0 = 0.0, t1 = 0.0;
             for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
-            t0 = lane < c ? __ldcg(x + f + lane) - t0 : 0.0;
-            t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) - t1 : 0.0;
+            // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
             const double di0 = lane < c ? dinv[f + lane] : 0.0;
             const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-            for (int j = c - 1; j >= 0; --j) {
-                const double dj = __shfl_sync(0xffffffffu, j < 32 ? di0 : di1, j & 31);
-                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31) * dj;
-                if (j < 32) { if (lane == j) t0 = wj; } else { if (lane == j - 32) t1 = wj; }
+            t0 = lane < c ? __ldcg(x + f + lane) * di0 * di0 - t0 : 0.0;
+            t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) * di1 * di1 - t1 : 0.0;
+            for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
+                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
                 if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
                 if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
             }

@@ -46,6 +46,7 @@ struct kkt_ctx {
     std::vector<int> lvl_trsm_ptr, lvl_syrk_ptr;
     int2* d_trsm_tasks = nullptr;
     int4* d_syrk_tasks = nullptr;
+
     double* d_dinv = nullptr;
     long long panel = 0;
     long long nk = 0;
@@ -78,6 +79,7 @@ struct kkt_ctx {
     // private copies of the values of the last kkt_factor (residuals of the
     // following solves read them, so callers may free their buffers)
     double *v_W = nullptr, *v_J = nullptr, *v_sigma = nullptr, *v_D = nullptr;
+    double* v_Js = nullptr;     // J scaled by sqrt(D) for the assembly
     double* h_sc = nullptr;     // pinned host scalars
     // factor inputs of the last kkt_factor
     bool factored = false;
@@ -524,6 +526,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(upload(c, &c->d_lvl_sn, c->h_lvl_sn));
     TRY(upload(c, &c->d_trsm_tasks, trsm_tasks));
     TRY(upload(c, &c->d_task_ptr, task_ptr));
+
     TRY(upload(c, &c->d_task_sn, task_sn));
     TRY(upload(c, &c->d_syrk_tasks, syrk_tasks));
     TRY(alloc(c, &c->d_dinv, n));
@@ -559,6 +562,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(alloc(c, &c->w_tn, n));
     TRY(alloc(c, &c->v_W, std::max(1, W_colptr[n])));
     TRY(alloc(c, &c->v_J, std::max(1, J_rowptr[m])));
+    TRY(alloc(c, &c->v_Js, std::max(1, J_rowptr[m])));
     TRY(alloc(c, &c->v_sigma, n));
     TRY(alloc(c, &c->v_D, std::max(1, m)));
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, 16 * sizeof(double)));
@@ -921,9 +925,12 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
     const int n = c->n, m = c->m;
     const int sp_a = span_begin(c, 0, st);
     CUDA_TRY(c, cudaMemsetAsync(c->d_Lx, 0, (size_t)c->panel * sizeof(double), st));
+    if (c->nnzJ > 0)
+        scale_rows_sqrt_kernel<<<grid_for(c->nnzJ), kThreads, 0, st>>>(c->nnzJ, c->d_jrow, c->f_J, c->f_D,
+                                                                       c->f_Dconst, c->v_Js);
     assemble_kernel<<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
-                                                          c->d_jrow, c->f_W, c->f_J, c->f_sigma,
-                                                          c->f_D, c->f_Dconst, delta_x, c->d_Lx);
+                                                          c->f_W, c->v_Js, c->f_sigma, delta_x,
+                                                          c->d_Lx);
     span_end(c, sp_a, st);
     const int big = 0x7fffffff;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_fail, &big, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -958,6 +965,9 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
                 c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, c->d_Lx);
         c->stats.launches += 2;
     }
+    normalize_panels_kernel<<<std::min(c->sym.ns(), 152 * 16), kThreads, 0, st>>>(
+        c->plan, c->sym.ns(), c->d_Lx, c->d_dinv);
+    c->stats.launches += 1;
     span_end(c, sp_f, st);
     CUDA_TRY(c, cudaGetLastError());
     // ||K_orig||_inf
@@ -1103,8 +1113,11 @@ kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* v
     if (!c) return KKT_ERR_ARG;
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "no factor");
     const int ns = c->sym.ns();
-    std::vector<double> Lh((size_t)c->panel);
-    if (val) CUDA_TRY(c, cudaMemcpy(Lh.data(), c->d_Lx, (size_t)c->panel * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> Lh((size_t)c->panel), dv(c->n);
+    if (val) {
+        CUDA_TRY(c, cudaMemcpy(Lh.data(), c->d_Lx, (size_t)c->panel * sizeof(double), cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(dv.data(), c->d_dinv, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     int64_t q = 0;
     if (colptr) colptr[0] = 0;
     for (int s = 0; s < ns; ++s) {
@@ -1113,7 +1126,8 @@ kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* v
         for (int j = 0; j < cc; ++j) {
             for (int i = j; i < rr; ++i) {
                 if (rowind) rowind[q] = rows[i];
-                if (val) val[q] = Lh[c->h_sn_lptr[s] + (long long)j * rr + i];
+                // the device keeps Lhat = L diag(1/l); export L
+                if (val) val[q] = Lh[c->h_sn_lptr[s] + (long long)j * rr + i] / dv[f + j];
                 ++q;
             }
             if (colptr) colptr[f + j + 1] = q;

@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x DFMA/clk/SM x flops x GHz = 1258.6
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FFMA lanes/SM x flops x GHz = 80,548
 METRIC = "KKT solve time per IPM iteration"
 UNIT = "ms/iter"
 
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--T", type=int, default=5000)
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--gamma", type=float, default=1e4)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -189,7 +192,8 @@ def run_ours(args, ws, rank, local):
     # replicas: every rank solves its own instance (horizon-shifted start)
     p = TrayParams(k=args.k, T=args.T)
     t0 = time.perf_counter()
-    ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500)
+    ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500,
+                    precision=1 if args.precision == "fp32" else 0)
     t_analyse = time.perf_counter() - t0
     kctx = nat.lib().kkt_ipm_kkt(ipm._h)
     ns, nnzL, panel, rows, lev, fl = (ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(),
@@ -288,20 +292,26 @@ def run_ours(args, ws, rank, local):
     fcalls = max(1, st["factor_calls"])
     factor_ms = st["factor_ms"] / fcalls
     kinv_ms = st["solve_ms"] / max(1, st["kinv_calls"])
+    f32 = args.precision == "fp32"
     roof = {"kernel": "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
             "bound": "alu", "achieved": fl.value / (factor_ms * 1e-3) / 1e9,
-            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
+            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["peak_source"] = "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)"
+    roof["peak_source"] = ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
+                           if f32 else
+                           "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")
     n_steps = len(step_ms)
     line = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64",
+        "data": "synthetic",
         "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), full IPM "
                                f"iteration ({args.scheme}) from xbar_0 = {p.x0bar}, tol 1e-8",
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
+                   "precision": args.precision,
+                   "fp32_factors": st["fp32_factors"], "fp64_fallbacks": st["fp64_fallbacks"],
                    "tau_relax": 1e-8 if args.scheme == "lifted" else None,
                    "l2": "flushed (256 MB write) between timed steps",
                    "analyse_s": round(t_analyse, 3), "supernodes": ns.value, "nnz_L": nnzL.value,

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("tol_refine", ctypes.c_double),
                 ("tol_cg", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int),
-                ("subtree_cols", ctypes.c_int)]
+                ("subtree_cols", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("assemble_ms", ctypes.c_double), ("factor_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("factor_launches", ctypes.c_int64),
-                ("factor_calls", ctypes.c_int64), ("kinv_calls", ctypes.c_int64)]
+                ("factor_calls", ctypes.c_int64), ("kinv_calls", ctypes.c_int64),
+                ("fp32_factors", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -57,11 +57,12 @@ __global__ void scale_rows_sqrt_kernel(int nnz, const int* __restrict__ jrow,
 // sources (W entry, diagonal Sigma_x + delta_x, products Js_a Js_b) and
 // writes the panel slot.  Source encoding: b == -1 -> W[a];
 // b == -2 -> sigma[a] + delta_x; b >= 0 -> Js[a] * Js[b].
+template <typename T>
 __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot,
                                 const long long* __restrict__ sptr,
                                 const int2* __restrict__ src, const double* __restrict__ W,
                                 const double* __restrict__ Js, const double* __restrict__ sigma,
-                                double delta_x, double* __restrict__ Lx) {
+                                double delta_x, T* __restrict__ Lx) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
          e += (long long)gridDim.x * blockDim.x) {
         double v = 0.0;
@@ -75,7 +76,7 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
                 v = fma(Js[s.x], Js[s.y], v);
             }
         }
-        Lx[slot[e]] = v;
+        Lx[slot[e]] = (T)v;
     }
 }
 
@@ -110,16 +111,20 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return y;
 }
 
+__device__ __forceinline__ double pivot_rsqrt(double d) { return rsqrt_newton(d); }
+__device__ __forceinline__ float pivot_rsqrt(float d) { return 1.0f / sqrtf(d); }
+
 // Pivot of column j: failure check, L_jj = d / sqrt(d), reciprocal stored
 // for the solves.
-__device__ __forceinline__ double take_pivot(double* A, int r, int f, int j, int* fail,
-                                             double* dinv) {
-    double d = A[j + (long long)j * r];
+template <typename T>
+__device__ __forceinline__ T take_pivot(T* A, int r, int f, int j, int* fail,
+                                             T* dinv) {
+    T d = A[j + (long long)j * r];
     if (!(d > 0.0) || !isfinite(d)) {
         atomicMin(fail, f + j);
         d = 1.0;
     }
-    const double inv = rsqrt_newton(d);
+    const T inv = pivot_rsqrt(d);
     A[j + (long long)j * r] = d * inv;
     dinv[f + j] = inv;
     return inv;
@@ -130,15 +135,16 @@ __device__ __forceinline__ double take_pivot(double* A, int r, int f, int j, int
 // the trailing rectangle rows [j+1, nrows) x cols [j+1, c) (entries above the
 // diagonal are skipped), with the thread that finishes (j+1, j+1) taking the
 // next pivot.  Two barriers per column.
-__device__ __forceinline__ void panel_factor(double* A, int f, int c, int r, int nrows, int* fail,
-                                             double* dinv) {
-    __shared__ double s_inv[2];
+template <typename T>
+__device__ __forceinline__ void panel_factor(T* A, int f, int c, int r, int nrows, int* fail,
+                                             T* dinv) {
+    __shared__ T s_inv[2];
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) s_inv[0] = take_pivot(A, r, f, 0, fail, dinv);
     __syncthreads();
     for (int j = 0; j < c; ++j) {
-        const double inv = s_inv[j & 1];
-        double* colj = A + (long long)j * r;
+        const T inv = s_inv[j & 1];
+        T* colj = A + (long long)j * r;
         for (int i = j + 1 + tid; i < nrows; i += nt) colj[i] *= inv;
         __syncthreads();
         const int len = nrows - j - 1, ncol = c - j - 1;
@@ -150,8 +156,8 @@ __device__ __forceinline__ void panel_factor(double* A, int f, int c, int r, int
                 fast_divmod(e, len, rcp, q, rem);
                 const int kk = j + 1 + q, ii = j + 1 + rem;
                 if (ii < kk) continue;
-                double* p = A + ii + (long long)kk * r;
-                const double v = fma(-colj[ii], colj[kk], *p);
+                T* p = A + ii + (long long)kk * r;
+                const T v = fma(-colj[ii], colj[kk], *p);
                 if (ii == j + 1 && kk == j + 1) {
                     *p = v;
                     s_inv[(j + 1) & 1] = take_pivot(A, r, f, j + 1, fail, dinv);
@@ -181,15 +187,16 @@ constexpr int kTileI = 8, kTileJ = 4;   // SYRK output tile per warp (lane = one
 
 // SYRK output tile (ti, tj) of L21 L21^T, lane -> (ii, jj) = (8 ti + lane % 8,
 // 4 tj + lane / 8), scattered into the ancestors with FP64 atomics.
-__device__ __forceinline__ void syrk_tile(const Plan& P, int s, int c, int r, const double* A,
-                                          double* Lx, int ti, int tj) {
+template <typename T>
+__device__ __forceinline__ void syrk_tile(const Plan& P, int s, int c, int r, const T* A,
+                                          T* Lx, int ti, int tj) {
     const int lane = threadIdx.x & 31;
     const int rb = r - c;
     const int ii = ti * kTileI + (lane & 7), jj = tj * kTileJ + (lane >> 3);
     const bool valid = ii < rb && jj < rb && ii >= jj;
-    const double* ai = A + c + (valid ? ii : 0);
-    const double* aj = A + c + (valid ? jj : 0);
-    double sum = 0.0;
+    const T* ai = A + c + (valid ? ii : 0);
+    const T* aj = A + c + (valid ? jj : 0);
+    T sum = 0.0;
     for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * r], aj[(long long)k * r], sum);
     if (valid) {
         long long base;
@@ -206,24 +213,26 @@ __device__ __forceinline__ int syrk_tiles_j(int rb) { return (rb + kTileJ - 1) /
 // One CTA per supernode (levels with many supernodes): the whole panel in
 // shared memory when it fits, dense right-looking factorisation, then the
 // SYRK tiles of the rows below the diagonal block.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__ Lx,
-                    int* __restrict__ fail, long long smem_elems, double* __restrict__ dinv) {
-    extern __shared__ double sm[];
+factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
+                    int* __restrict__ fail, long long smem_elems, T* __restrict__ dinv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const long long lp = P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool in_smem = (long long)r * c <= smem_elems;
-    double* A = in_smem ? sm : Lx + lp;
+    T* A = in_smem ? sm : Lx + lp;
     if (in_smem) {
-        const double* g = Lx + lp;
+        const T* g = Lx + lp;
         for (long long e = tid; e < (long long)r * c; e += nt) A[e] = g[e];
         __syncthreads();
     }
     panel_factor(A, f, c, r, r, fail, dinv);
     if (in_smem) {
-        double* g = Lx + lp;
+        T* g = Lx + lp;
         for (long long e = tid; e < (long long)r * c; e += nt) g[e] = A[e];
     }
     const int rb = r - c;
@@ -240,13 +249,15 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__
 // Levels with few supernodes run in three launches spread over many CTAs:
 // (1) POTRF of each diagonal block, (2) TRSM of the rows below, one row per
 // warp, (3) SYRK tiles, one tile per warp.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, double* __restrict__ Lx,
-                  int* __restrict__ fail, double* __restrict__ dinv) {
-    extern __shared__ double sm[];
+potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
+                  int* __restrict__ fail, T* __restrict__ dinv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-    double* g = Lx + P.sn_lptr[s];
+    T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
     __syncthreads();
     panel_factor(sm, f, c, c, c, fail, dinv);
@@ -259,14 +270,15 @@ constexpr int kTrsmWarps = 8;   // rows per TRSM CTA (one per warp)
 // task.y + w with lanes over the columns (two per lane).  The columns of L11
 // are pre-scaled by the reciprocal pivots, so a step is one shuffle and one
 // FMA: a_l -= a_k (L_lk / L_kk); the final x_k = a_k / L_kk is one multiply.
+template <typename T>
 __global__ void __launch_bounds__(32 * kTrsmWarps)
-trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, double* __restrict__ Lx,
-                 const double* __restrict__ dinv) {
-    __shared__ double D[64 * 64];
+trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
+                 const T* __restrict__ dinv) {
+    __shared__ T D[64 * 64];
     const int2 task = tasks[blockIdx.x];
     const int s = task.x;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-    double* g = Lx + P.sn_lptr[s];
+    T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
         const int col = e / c;
         D[e] = g[(e % c) + (long long)col * r] * dinv[f + col];
@@ -275,11 +287,11 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, double* __restrict__ Lx
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = task.y + warp;
     if (i >= r - c) return;
-    double* row = g + c + i;                       // element k at row[k * r]
-    double a0 = lane < c ? row[(long long)lane * r] : 0.0;
-    double a1 = lane + 32 < c ? row[(long long)(lane + 32) * r] : 0.0;
+    T* row = g + c + i;                       // element k at row[k * r]
+    T a0 = lane < c ? row[(long long)lane * r] : 0.0;
+    T a1 = lane + 32 < c ? row[(long long)(lane + 32) * r] : 0.0;
     for (int k = 0; k < c; ++k) {
-        const double ak = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
+        const T ak = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
         if (lane > k && lane < c) a0 = fma(-ak, D[lane + k * c], a0);
         if (lane + 32 > k && lane + 32 < c) a1 = fma(-ak, D[lane + 32 + k * c], a1);
     }
@@ -288,8 +300,9 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, double* __restrict__ Lx
 }
 
 // task = (supernode, tile row ti, tile column tj); one tile per warp.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, double* __restrict__ Lx) {
+syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, T* __restrict__ Lx) {
     const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (t >= ntasks) return;
     const int4 task = tasks[t];
@@ -301,11 +314,12 @@ syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, double* __r
 // pivots stay in dinv).  The triangular solves then substitute without
 // divisions: L z = b is Lhat u = b with z = u / l, and L^T w = z is
 // Lhat^T w = u / l^2.  One CTA per supernode.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-normalize_panels_kernel(Plan P, int ns, double* __restrict__ Lx, const double* __restrict__ dinv) {
+normalize_panels_kernel(Plan P, int ns, T* __restrict__ Lx, const T* __restrict__ dinv) {
     for (int s = blockIdx.x; s < ns; s += gridDim.x) {
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-        double* A = Lx + P.sn_lptr[s];
+        T* A = Lx + P.sn_lptr[s];
         for (int e = threadIdx.x; e < r * c; e += blockDim.x) A[e] *= dinv[f + e / r];
     }
 }
@@ -315,25 +329,26 @@ normalize_panels_kernel(Plan P, int ns, double* __restrict__ Lx, const double* _
 // diagonal block in shared memory, one warp substitutes with shuffles
 // (reciprocal pivots from the factorisation), then one thread per row of
 // L21 forms its product with z and scatters it.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                     const double* __restrict__ dinv, double* __restrict__ x,
+forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
+                     const T* __restrict__ dinv, T* __restrict__ x,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ double D[64 * 64];
-    __shared__ double z[64];
+    __shared__ T D[64 * 64];
+    __shared__ T z[64];
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-    const double* A = Lx + P.sn_lptr[s];
+    const T* A = Lx + P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
     __syncthreads();
     if (tid < 32) {
         const int lane = tid;
-        double z0 = lane < c ? x[f + lane] : 0.0;
-        double z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
+        T z0 = lane < c ? x[f + lane] : 0.0;
+        T z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
         for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
-            const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
+            const T zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
             if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
             if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
         }
@@ -343,7 +358,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __res
     __syncthreads();
     const int* rows = P.rows + P.sn_rptr[s];
     for (int i = tid; i < r - c; i += nt) {
-        double sum = 0.0;
+        T sum = 0.0;
         for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
         atomicAdd(x + rows[c + i], -sum);
     }
@@ -353,17 +368,19 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __res
 // (levels visited top-down): t_k = z_k - L21(:,k)^T w_below with lanes over
 // the columns k and warps over row blocks, then one warp substitutes with
 // the diagonal block.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __restrict__ Lx,
-                      const double* __restrict__ dinv, double* __restrict__ x,
+backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
+                      const T* __restrict__ dinv, T* __restrict__ x,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ double D[64 * 64];
-    __shared__ double part[kThreads / 32][64];
-    extern __shared__ double xb[];
+    __shared__ T D[64 * 64];
+    __shared__ T part[kThreads / 32][64];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xb = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-    const double* A = Lx + P.sn_lptr[s];
+    const T* A = Lx + P.sn_lptr[s];
     const int* rows = P.rows + P.sn_rptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
@@ -373,9 +390,9 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
     __syncthreads();
     // warp w sums rows i = w, w + nw, ... for columns k = lane, lane + 32
     {
-        double s0 = 0.0, s1 = 0.0;
+        T s0 = 0.0, s1 = 0.0;
         for (int i = warp; i < rb; i += nw) {
-            const double xv = xb[i];
+            const T xv = xb[i];
             if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
             if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
         }
@@ -384,15 +401,15 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
     }
     __syncthreads();
     if (tid < 32) {
-        double t0 = 0.0, t1 = 0.0;
+        T t0 = 0.0, t1 = 0.0;
         for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
         // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
-        const double di0 = lane < c ? dinv[f + lane] : 0.0;
-        const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
+        const T di0 = lane < c ? dinv[f + lane] : 0.0;
+        const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
         t0 = lane < c ? x[f + lane] * di0 * di0 - t0 : 0.0;
         t1 = lane + 32 < c ? x[f + lane + 32] * di1 * di1 - t1 : 0.0;
         for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
-            const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
+            const T wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
             if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
             if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
         }
@@ -406,16 +423,18 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const double* __re
 // postorder) are processed by one CTA each, without per-level launches.
 // Values that earlier supernodes of the same task updated through atomics
 // are read with ld.global.cg (L2), never from a possibly stale L1 line.
+template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                      double* __restrict__ Lx, int* __restrict__ fail, double* __restrict__ dinv) {
-    extern __shared__ double sm[];
+                      T* __restrict__ Lx, int* __restrict__ fail, T* __restrict__ dinv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, nw = nt >> 5;
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-        double* g = Lx + P.sn_lptr[s];
+        T* g = Lx + P.sn_lptr[s];
         for (int e = tid; e < r * c; e += nt) sm[e] = __ldcg(g + e);
         __syncthreads();
         panel_factor(sm, f, c, r, r, fail, dinv);
@@ -435,27 +454,29 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
 }
 
 // Forward substitution over a subtree task (supernodes in postorder).
+template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                       const double* __restrict__ Lx, const double* __restrict__ dinv,
-                       double* __restrict__ x,
+                       const T* __restrict__ Lx, const T* __restrict__ dinv,
+                       T* __restrict__ x,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ double z[64];
-    extern __shared__ double D[];   // diagonal block of the current supernode
+    __shared__ T z[64];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* D = reinterpret_cast<T*>(smem_raw);   // diagonal block of the current supernode
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-        const double* A = Lx + P.sn_lptr[s];
+        const T* A = Lx + P.sn_lptr[s];
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
         __syncthreads();
         if (tid < 32) {
             const int lane = tid;
-            double z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
-            double z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
+            T z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
+            T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
             for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
-                const double zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
+                const T zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
                 if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
                 if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
             }
@@ -465,7 +486,7 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
         __syncthreads();
         const int* rows = P.rows + P.sn_rptr[s];
         for (int i = tid; i < r - c; i += nt) {
-            double sum = 0.0;
+            T sum = 0.0;
             for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
             atomicAdd(x + rows[c + i], -sum);
         }
@@ -475,30 +496,32 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
 }
 
 // Backward substitution over a subtree task (supernodes in reverse postorder).
+template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                        const double* __restrict__ Lx, const double* __restrict__ dinv,
-                        double* __restrict__ x,
+                        const T* __restrict__ Lx, const T* __restrict__ dinv,
+                        T* __restrict__ x,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ double part[kSubtreeThreads / 32][64];
-    extern __shared__ double dyn[];   // [diagonal block | x of the rows below]
+    __shared__ T part[kSubtreeThreads / 32][64];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* dyn = reinterpret_cast<T*>(smem_raw);   // [diagonal block | x of the rows below]
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     for (int q = task_ptr[blockIdx.x + 1] - 1; q >= task_ptr[blockIdx.x]; --q) {
         const int s = task_sn[q];
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
-        const double* A = Lx + P.sn_lptr[s];
+        const T* A = Lx + P.sn_lptr[s];
         const int* rows = P.rows + P.sn_rptr[s];
         const int rb = r - c;
-        double* D = dyn;
-        double* xb = dyn + c * c;
+        T* D = dyn;
+        T* xb = dyn + c * c;
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
         for (int i = tid; i < rb; i += nt) xb[i] = __ldcg(x + rows[c + i]);
         __syncthreads();
-        double s0 = 0.0, s1 = 0.0;
+        T s0 = 0.0, s1 = 0.0;
         for (int i = warp; i < rb; i += nw) {
-            const double xv = xb[i];
+            const T xv = xb[i];
             if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
             if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
         }
@@ -506,15 +529,15 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
         part[warp][lane + 32] = s1;
         __syncthreads();
         if (tid < 32) {
-            double t0 = 0.0, t1 = 0.0;
+            T t0 = 0.0, t1 = 0.0;
             for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
             // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
-            const double di0 = lane < c ? dinv[f + lane] : 0.0;
-            const double di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
+            const T di0 = lane < c ? dinv[f + lane] : 0.0;
+            const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
             t0 = lane < c ? __ldcg(x + f + lane) * di0 * di0 - t0 : 0.0;
             t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) * di1 * di1 - t1 : 0.0;
             for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
-                const double wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
+                const T wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
                 if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
                 if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
             }
@@ -526,20 +549,22 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
     }
 }
 
-__global__ void gather_kernel(int n, const int* __restrict__ idx, const double* __restrict__ in,
-                              double* __restrict__ out,
+template <typename Tin, typename Tout>
+__global__ void gather_kernel(int n, const int* __restrict__ idx, const Tin* __restrict__ in,
+                              Tout* __restrict__ out,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = in[idx[i]];
+        out[i] = (Tout)in[idx[i]];
 }
 
-__global__ void scatter_kernel(int n, const int* __restrict__ idx, const double* __restrict__ in,
-                               double* __restrict__ out,
+template <typename Tin, typename Tout>
+__global__ void scatter_kernel(int n, const int* __restrict__ idx, const Tin* __restrict__ in,
+                               Tout* __restrict__ out,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[idx[i]] = in[i];
+        out[idx[i]] = (Tout)in[i];
 }
 
 // ------------------------------------------------------------- sparse BLAS

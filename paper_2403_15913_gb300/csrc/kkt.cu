@@ -80,6 +80,9 @@ struct kkt_ctx {
     // following solves read them, so callers may free their buffers)
     double *v_W = nullptr, *v_J = nullptr, *v_sigma = nullptr, *v_D = nullptr;
     double* v_Js = nullptr;     // J scaled by sqrt(D) for the assembly
+    // FP32 factor (precision = 1): panels, reciprocal pivots, permuted vector
+    float *d_Lx32 = nullptr, *d_dinv32 = nullptr, *w_xp32 = nullptr;
+    int cur_prec = 0;           // precision of the current factor: 0 FP64, 1 FP32
     double* h_sc = nullptr;     // pinned host scalars
     // factor inputs of the last kkt_factor
     bool factored = false;
@@ -91,9 +94,9 @@ struct kkt_ctx {
     bool device_ready = false;   // false for host-only analyses
     // CUDA graphs captured once after the analysis: the triangular solves on
     // w_xp, and one HyKKT CG iteration on the internal CG vectors
-    cudaGraph_t tri_graph = nullptr, cg_graph = nullptr;
-    cudaGraphExec_t tri_exec = nullptr, cg_exec = nullptr;
-    size_t tri_nodes = 0, cg_nodes = 0;
+    cudaGraph_t tri_graph = nullptr, cg_graph = nullptr, tri_graph32 = nullptr, cg_graph32 = nullptr;
+    cudaGraphExec_t tri_exec = nullptr, cg_exec = nullptr, tri_exec32 = nullptr, cg_exec32 = nullptr;
+    size_t tri_nodes = 0, cg_nodes = 0, tri_nodes32 = 0, cg_nodes32 = 0;
     int* d_cg = nullptr;        // [active, iterations]
     int* h_cg = nullptr;        // pinned
     // tracing
@@ -567,30 +570,42 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(alloc(c, &c->v_D, std::max(1, m)));
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, 16 * sizeof(double)));
     TRY(alloc(c, &c->d_cg, 2));
+    if (c->opt.precision == 1) {
+        TRY(alloc(c, &c->d_Lx32, (size_t)c->panel));
+        TRY(alloc(c, &c->d_dinv32, n));
+        TRY(alloc(c, &c->w_xp32, n));
+    }
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_cg, 2 * sizeof(int)));
     return KKT_OK;
 }
 
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
-// levels bottom-up, then levels top-down and subtree tasks.
-void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st, const int* active) {
+// levels bottom-up, then levels top-down and subtree tasks (panels Lx and
+// reciprocal pivots dinv of the precision T).
+template <typename T>
+void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStream_t st,
+                               const int* active) {
     if (c->ntasks > 0)
-        forward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(double), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp, active);
+        forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
     for (int l = 0; l < c->nlev; ++l) {
         int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        forward_level_kernel<<<cnt, kThreads, 0, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                       c->d_Lx, c->d_dinv, xp, active);
+        forward_level_kernel<T><<<cnt, kThreads, 0, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], Lx, dinv,
+                                                          xp, active);
     }
     for (int l = c->nlev - 1; l >= 0; --l) {
         int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_rb[l] * sizeof(double);
-        backward_level_kernel<<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l],
-                                                         c->d_Lx, c->d_dinv, xp, active);
+        size_t sm = (size_t)c->lvl_max_rb[l] * sizeof(T);
+        backward_level_kernel<T><<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], Lx,
+                                                            dinv, xp, active);
     }
     if (c->ntasks > 0)
-        backward_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(double), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_dinv, xp, active);
+        backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(T), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+}
+
+void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st, const int* active) {
+    enqueue_triangular_solves<double>(c, c->d_Lx, c->d_dinv, xp, st, active);
 }
 
 // x <- K^{-1} x  (in and out may alias; uses w_xp)
@@ -599,13 +614,23 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
     const int sp = span_begin(c, 2, st);
     c->stats.kinv_calls++;
     c->stats.launches += 2 + 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0);
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp, nullptr);
-    if (c->tri_exec) {
-        CUDA_TRY(c, cudaGraphLaunch(c->tri_exec, st));
+    if (c->cur_prec == 1) {
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp32, nullptr);
+        if (c->tri_exec32) {
+            CUDA_TRY(c, cudaGraphLaunch(c->tri_exec32, st));
+        } else {
+            enqueue_triangular_solves<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, st, nullptr);
+        }
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp32, out, nullptr);
     } else {
-        enqueue_triangular_solves(c, c->w_xp, st, nullptr);
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp, nullptr);
+        if (c->tri_exec) {
+            CUDA_TRY(c, cudaGraphLaunch(c->tri_exec, st));
+        } else {
+            enqueue_triangular_solves(c, c->w_xp, st, nullptr);
+        }
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out, nullptr);
     }
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, out, nullptr);
     span_end(c, sp, st);
     CUDA_TRY(c, cudaGetLastError());
     return KKT_OK;
@@ -654,14 +679,15 @@ kkt_status lifted_precond(kkt_ctx* c, const double* rx, const double* ry, double
 // One CG iteration on S_gamma = J K_gamma^{-1} J^T with the internal vectors
 // (p = w_p, S p = w_sp, x = w_cgx, r = w_res), every kernel guarded by the
 // device flag d_cg[0].
-void enqueue_cg_iteration(kkt_ctx* c, cudaStream_t st) {
+template <typename T>
+void enqueue_cg_iteration(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStream_t st) {
     const int n = c->n, m = c->m;
     const int* act = c->d_cg;
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->v_J,
                                                      nullptr, c->w_p, nullptr, 1.0, 1.0, c->w_tn, act);
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, c->w_xp, act);
-    enqueue_triangular_solves(c, c->w_xp, st, act);
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp, c->w_tn, act);
+    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, xp, act);
+    enqueue_triangular_solves<T>(c, Lx, dinv, xp, st, act);
+    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, c->w_tn, act);
     j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
                                                      nullptr, nullptr, 1.0, c->w_sp, act);
     dot(c, m, c->w_p, c->w_sp, SC_DOT2, st, act);
@@ -691,7 +717,15 @@ kkt_status capture_graphs(kkt_ctx* c) {
     cudaError_t err = capture([&] { enqueue_triangular_solves(c, c->w_xp, cs, nullptr); },
                               &c->tri_graph, &c->tri_exec, &c->tri_nodes);
     if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
-        err = capture([&] { enqueue_cg_iteration(c, cs); }, &c->cg_graph, &c->cg_exec, &c->cg_nodes);
+        err = capture([&] { enqueue_cg_iteration<double>(c, c->d_Lx, c->d_dinv, c->w_xp, cs); },
+                      &c->cg_graph, &c->cg_exec, &c->cg_nodes);
+    if (err == cudaSuccess && c->opt.precision == 1) {
+        err = capture([&] { enqueue_triangular_solves<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, cs, nullptr); },
+                      &c->tri_graph32, &c->tri_exec32, &c->tri_nodes32);
+        if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
+            err = capture([&] { enqueue_cg_iteration<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, cs); },
+                          &c->cg_graph32, &c->cg_exec32, &c->cg_nodes32);
+    }
     cudaStreamDestroy(cs);
     if (err != cudaSuccess) return set_err(c, KKT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
     return KKT_OK;
@@ -720,14 +754,18 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
     cg_init_kernel<<<1, 1, 0, st>>>(c->d_sc, SC_DOT0, SC_STOP, c->opt.tol_cg, c->opt.max_cg, c->d_cg);
     const int sp = span_begin(c, 3, st);
     while (true) {
+        const bool f32 = c->cur_prec == 1;
         for (int b = 0; b < kCgBatch; ++b) {
-            if (c->cg_exec) {
-                CUDA_TRY(c, cudaGraphLaunch(c->cg_exec, st));
+            cudaGraphExec_t ex = f32 ? c->cg_exec32 : c->cg_exec;
+            if (ex) {
+                CUDA_TRY(c, cudaGraphLaunch(ex, st));
+            } else if (f32) {
+                enqueue_cg_iteration<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, st);
             } else {
-                enqueue_cg_iteration(c, st);
+                enqueue_cg_iteration<double>(c, c->d_Lx, c->d_dinv, c->w_xp, st);
             }
         }
-        c->stats.launches += (long long)kCgBatch * (long long)c->cg_nodes;
+        c->stats.launches += (long long)kCgBatch * (long long)(f32 ? c->cg_nodes32 : c->cg_nodes);
         CUDA_TRY(c, cudaMemcpyAsync(c->h_cg, c->d_cg, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaStreamSynchronize(st));
         if (c->h_cg[0] == 0) break;
@@ -750,6 +788,57 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
     return KKT_OK;
 }
 
+// Zero the panels, assemble, factorise (subtree tasks, levels), normalise to
+// unit diagonal: everything the numeric factorisation enqueues for the panel
+// precision T.  The fail word is reset first.
+template <typename T>
+kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
+    const int big = 0x7fffffff;
+    const int sp_a = span_begin(c, 0, st);
+    CUDA_TRY(c, cudaMemsetAsync(Lx, 0, (size_t)c->panel * sizeof(T), st));
+    assemble_kernel<T><<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
+                                                             c->f_W, c->v_Js, c->f_sigma, delta_x, Lx);
+    span_end(c, sp_a, st);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fail, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+    const int sp_f = span_begin(c, 1, st);
+    c->stats.factor_calls++;
+    c->stats.launches += 2 + c->nlev;
+    c->stats.factor_launches += c->nlev;
+    if (c->ntasks > 0) {
+        factor_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_rc * sizeof(T), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, c->d_fail, dinv);
+        c->stats.launches += 1;
+        c->stats.factor_launches += 1;
+    }
+    for (int l = 0; l < c->nlev; ++l) {
+        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
+        if (!c->lvl_split[l]) {
+            long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
+            factor_level_kernel<T><<<cnt, kThreads, (size_t)need * sizeof(T), st>>>(
+                c->plan, lsn, Lx, c->d_fail, need, dinv);
+            continue;
+        }
+        const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
+        potrf_diag_kernel<T><<<cnt, kThreads, dsm, st>>>(c->plan, lsn, Lx, c->d_fail, dinv);
+        const int nt = c->lvl_trsm_ptr[l + 1] - c->lvl_trsm_ptr[l];
+        if (nt > 0)
+            trsm_rows_kernel<T><<<nt, 32 * kTrsmWarps, 0, st>>>(
+                c->plan, c->d_trsm_tasks + c->lvl_trsm_ptr[l], Lx, dinv);
+        const int ny = c->lvl_syrk_ptr[l + 1] - c->lvl_syrk_ptr[l];
+        if (ny > 0)
+            syrk_tile_kernel<T><<<(ny + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(
+                c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, Lx);
+        c->stats.launches += 2;
+    }
+    normalize_panels_kernel<T><<<std::min(c->sym.ns(), 152 * 16), kThreads, 0, st>>>(
+        c->plan, c->sym.ns(), Lx, dinv);
+    c->stats.launches += 1;
+    span_end(c, sp_f, st);
+    CUDA_TRY(c, cudaGetLastError());
+    return KKT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -769,6 +858,7 @@ void kkt_default_options(kkt_options* o) {
     o->max_cg = 200;
     o->target_relaxed = 0;
     o->subtree_cols = 48;
+    o->precision = 0;
 }
 
 namespace {
@@ -783,6 +873,10 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
     if (c->opt.scheme != KKT_LIFTED && c->opt.scheme != KKT_HYKKT) {
         delete c;
         return set_err(nullptr, KKT_ERR_ARG, "unknown scheme");
+    }
+    if (c->opt.precision != 0 && c->opt.precision != 1) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32 factor)");
     }
     if (c->opt.max_width <= 0 || c->opt.max_width > 64) c->opt.max_width = 64;
     c->n = n;
@@ -829,9 +923,13 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
             kkt_destroy(c);
             return st;
         }
-        cudaFuncSetAttribute(factor_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(factor_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(double)));
-        cudaFuncSetAttribute(backward_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(factor_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemCapElems * sizeof(float)));
+        cudaFuncSetAttribute(backward_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             160 * 1024);
+        cudaFuncSetAttribute(backward_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              160 * 1024);
         st = capture_graphs(c);
         if (st != KKT_OK) {
@@ -924,52 +1022,30 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
     }
     const int n = c->n, m = c->m;
     const int sp_a = span_begin(c, 0, st);
-    CUDA_TRY(c, cudaMemsetAsync(c->d_Lx, 0, (size_t)c->panel * sizeof(double), st));
     if (c->nnzJ > 0)
         scale_rows_sqrt_kernel<<<grid_for(c->nnzJ), kThreads, 0, st>>>(c->nnzJ, c->d_jrow, c->f_J, c->f_D,
                                                                        c->f_Dconst, c->v_Js);
-    assemble_kernel<<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
-                                                          c->f_W, c->v_Js, c->f_sigma, delta_x,
-                                                          c->d_Lx);
     span_end(c, sp_a, st);
     const int big = 0x7fffffff;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_fail, &big, sizeof(int), cudaMemcpyHostToDevice, st));
-    const int sp_f = span_begin(c, 1, st);
-    c->stats.factor_calls++;
-    c->stats.launches += 2 + c->nlev;
-    c->stats.factor_launches += c->nlev;
-    if (c->ntasks > 0) {
-        factor_subtree_kernel<<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_rc * sizeof(double), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, c->d_Lx, c->d_fail, c->d_dinv);
-        c->stats.launches += 1;
-        c->stats.factor_launches += 1;
-    }
-    for (int l = 0; l < c->nlev; ++l) {
-        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
-        if (!c->lvl_split[l]) {
-            long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
-            factor_level_kernel<<<cnt, kThreads, (size_t)need * sizeof(double), st>>>(
-                c->plan, lsn, c->d_Lx, c->d_fail, need, c->d_dinv);
-            continue;
+    int fail = big;
+    int detail = 0;
+    if (c->opt.precision == 1) {
+        TRY(enqueue_numeric_factor<float>(c, c->d_Lx32, c->d_dinv32, delta_x, st));
+        CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        c->stats.fp32_factors++;
+        c->cur_prec = 1;
+        detail = 1;
+        if (fail != big) {            // FP32 pivot failed: factorise in FP64
+            c->stats.fp64_fallbacks++;
+            detail = 2;
+            fail = big;
         }
-        const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(double);
-        potrf_diag_kernel<<<cnt, kThreads, dsm, st>>>(c->plan, lsn, c->d_Lx, c->d_fail, c->d_dinv);
-        const int nt = c->lvl_trsm_ptr[l + 1] - c->lvl_trsm_ptr[l];
-        if (nt > 0)
-            trsm_rows_kernel<<<nt, 32 * kTrsmWarps, 0, st>>>(
-                c->plan, c->d_trsm_tasks + c->lvl_trsm_ptr[l], c->d_Lx, c->d_dinv);
-        const int ny = c->lvl_syrk_ptr[l + 1] - c->lvl_syrk_ptr[l];
-        if (ny > 0)
-            syrk_tile_kernel<<<(ny + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(
-                c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, c->d_Lx);
-        c->stats.launches += 2;
     }
-    normalize_panels_kernel<<<std::min(c->sym.ns(), 152 * 16), kThreads, 0, st>>>(
-        c->plan, c->sym.ns(), c->d_Lx, c->d_dinv);
-    c->stats.launches += 1;
-    span_end(c, sp_f, st);
-    CUDA_TRY(c, cudaGetLastError());
+    if (detail != 1) {
+        TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, delta_x, st));
+        c->cur_prec = 0;
+    }
     // ||K_orig||_inf
     CUDA_TRY(c, cudaMemsetAsync(c->d_sc + SC_KNORM, 0, sizeof(double), st));
     if (c->f_C) {
@@ -979,15 +1055,15 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
     knorm_kernel<<<grid_for((long long)n + m), kThreads, 0, st>>>(
         n, m, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx,
         c->f_J, c->f_sigma, delta_x, c->f_C, c->d_sc + SC_KNORM);
-    int fail = big;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_KNORM, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (detail != 1) CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     spans_collect(c);
     c->knorm = c->h_sc[0];
     if (info) {
         info->failed_col = fail == big ? -1 : fail;
         info->delta_x = delta_x;
+        info->status_detail = detail;
     }
     if (fail != big) return set_err(c, KKT_ERR_NOT_SPD, "factorization: non-positive pivot in column " + std::to_string(fail));
     c->factored = true;
@@ -1004,35 +1080,59 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
     double* ry = c->w_r + n;
     double* dx = c->w_d;
     double* dy = c->w_d + n;
-    CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
-    CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
-    CUDA_TRY(c, cudaMemcpyAsync(rx, d_rx, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(c, cudaMemcpyAsync(ry, d_ry, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<double> etas;
     int slow = 0, cg_total = 0, it = 0;
     kkt_status result = KKT_ERR_MAXIT;
     bool cg_failed = false;
-    for (it = 0; it <= c->opt.max_refine; ++it) {
-        if (c->opt.scheme == KKT_LIFTED) {
-            TRY(lifted_precond(c, rx, ry, dx, dy, st));
-        } else {
-            int its = 0;
-            bool ok = true;
-            TRY(hykkt_inner(c, rx, ry, dx, dy, st, &its, &ok));
-            cg_total += its;
-            if (!ok) cg_failed = true;
+    int detail = c->cur_prec;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
+        CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
+        CUDA_TRY(c, cudaMemcpyAsync(rx, d_rx, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(ry, d_ry, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        etas.clear();
+        slow = 0;
+        result = KKT_ERR_MAXIT;
+        cg_failed = false;
+        for (it = 0; it <= c->opt.max_refine; ++it) {
+            if (c->opt.scheme == KKT_LIFTED) {
+                TRY(lifted_precond(c, rx, ry, dx, dy, st));
+            } else {
+                int its = 0;
+                bool ok = true;
+                TRY(hykkt_inner(c, rx, ry, dx, dy, st, &its, &ok));
+                cg_total += its;
+                if (!ok) cg_failed = true;
+            }
+            c->stats.launches += 2;
+            axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, 1.0, dx, d_dx);
+            axpy_kernel<<<grid_for(m), kThreads, 0, st>>>(m, 1.0, dy, d_dy);
+            double eta = 0;
+            TRY(residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, st, &eta));
+            etas.push_back(eta);
+            if (eta <= c->opt.tol_refine) { result = KKT_OK; break; }
+            if (etas.size() >= 2 && eta > 0.9 * etas[etas.size() - 2]) {   // stagnation
+                if (++slow >= 2) { result = KKT_ERR_STALL; break; }
+            } else {
+                slow = 0;
+            }
         }
-        c->stats.launches += 2;
-        axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, 1.0, dx, d_dx);
-        axpy_kernel<<<grid_for(m), kThreads, 0, st>>>(m, 1.0, dy, d_dy);
-        double eta = 0;
-        TRY(residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, st, &eta));
-        etas.push_back(eta);
-        if (eta <= c->opt.tol_refine) { result = KKT_OK; break; }
-        if (etas.size() >= 2 && eta > 0.9 * etas[etas.size() - 2]) {   // stagnation
-            if (++slow >= 2) { result = KKT_ERR_STALL; break; }
-        } else {
-            slow = 0;
+        if (result == KKT_OK || c->cur_prec != 1) break;
+        // the FP32 factor did not carry the refinement to the tolerance:
+        // factorise the same system in FP64 and solve again
+        const int big = 0x7fffffff;
+        int fail = big;
+        TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, c->f_delta_x, st));
+        CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        c->cur_prec = 0;
+        c->stats.fp64_fallbacks++;
+        detail = 2;
+        if (fail != big) {
+            c->factored = false;
+            if (info) { info->failed_col = fail; info->status_detail = detail; }
+            return set_err(c, KKT_ERR_NOT_SPD, "FP64 refactorization after FP32 fallback: non-positive pivot in column " +
+                                                   std::to_string(fail));
         }
     }
     if (it > c->opt.max_refine) it = c->opt.max_refine;
@@ -1047,6 +1147,7 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
         info->refine_iters = it;
         info->cg_iters = cg_total;
         info->bwd_err = etas.empty() ? INFINITY : etas.back();
+        info->status_detail = detail;
     }
     if (result == KKT_OK && cg_failed) result = KKT_OK;   // refinement reached the tolerance anyway
     if (result != KKT_OK)
@@ -1101,9 +1202,16 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     double* xp = nullptr;
     TRY(noalloc_scratch(c, &xp));
     const int n = c->n;
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp, nullptr);
-    enqueue_triangular_solves(c, xp, st, nullptr);
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x, nullptr);
+    if (c->cur_prec == 1) {   // FP32 factor: the scratch holds n floats
+        float* xp32 = reinterpret_cast<float*>(xp);
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp32, nullptr);
+        enqueue_triangular_solves<float>(c, c->d_Lx32, c->d_dinv32, xp32, st, nullptr);
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp32, d_x, nullptr);
+    } else {
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp, nullptr);
+        enqueue_triangular_solves(c, xp, st, nullptr);
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, d_x, nullptr);
+    }
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
     return KKT_OK;
@@ -1114,7 +1222,13 @@ kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* v
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "no factor");
     const int ns = c->sym.ns();
     std::vector<double> Lh((size_t)c->panel), dv(c->n);
-    if (val) {
+    if (val && c->cur_prec == 1) {
+        std::vector<float> Lf((size_t)c->panel), df(c->n);
+        CUDA_TRY(c, cudaMemcpy(Lf.data(), c->d_Lx32, (size_t)c->panel * sizeof(float), cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(df.data(), c->d_dinv32, (size_t)c->n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < Lf.size(); ++i) Lh[i] = Lf[i];
+        for (int i = 0; i < c->n; ++i) dv[i] = df[i];
+    } else if (val) {
         CUDA_TRY(c, cudaMemcpy(Lh.data(), c->d_Lx, (size_t)c->panel * sizeof(double), cudaMemcpyDeviceToHost));
         CUDA_TRY(c, cudaMemcpy(dv.data(), c->d_dinv, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost));
     }
@@ -1158,6 +1272,10 @@ const char* kkt_last_error(const kkt_ctx* c) { return c ? c->err.c_str() : g_err
 
 void kkt_destroy(kkt_ctx* c) {
     if (!c) return;
+    if (c->tri_exec32) cudaGraphExecDestroy(c->tri_exec32);
+    if (c->tri_graph32) cudaGraphDestroy(c->tri_graph32);
+    if (c->cg_exec32) cudaGraphExecDestroy(c->cg_exec32);
+    if (c->cg_graph32) cudaGraphDestroy(c->cg_graph32);
     if (c->tri_exec) cudaGraphExecDestroy(c->tri_exec);
     if (c->tri_graph) cudaGraphDestroy(c->tri_graph);
     if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);

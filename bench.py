@@ -15,6 +15,11 @@ symbolic analysis is done once before timing (the paper's SYM column).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme lifted|hykkt]
         python bench.py --impl reference ...   (the CPU oracle, timed as it stands)
+
+--workload kkt times one KKT step instead (assembly, factor, solve and
+refinement at a seeded iterate with Sigma log-uniform on --sigma), e.g. the
+mixed-precision case: --workload kkt --T 20000 --sigma 1e-8,1e8 --precision
+fp32, which also runs the all-FP64 factor on the same input for comparison.
 """
 from __future__ import annotations
 
@@ -47,6 +52,8 @@ def parse():
     ap.add_argument("--gamma", type=float, default=1e4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
+    ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt"])
+    ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -344,11 +351,214 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- one KKT step
+KKT_METRIC = "KKT step time (assemble + factor + refined solve)"
+
+
+def oracle_kkt_sample(k, T_sample, scheme, sig, gamma, budget_s):
+    """Oracle KKT steps (condensed assembly, left-looking sparse Cholesky,
+    refined solve) at a bounded size: seconds per step."""
+    import numpy as np
+    from gen.tray import TrayParams, kkt_point
+    from oracle import kkt as okkt, symbolic, tray as otray
+    p = TrayParams(k=k, T=T_sample)
+    pt = kkt_point(p, 0, sig)
+    W = otray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = otray.jacobian_csr(p, pt.w)
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=64, relax_cols=32,
+                           relax_zeros=128, max_width=64)
+    n_done, t = 0, 0.0
+    while t < budget_s or n_done == 0:
+        t0 = time.perf_counter()
+        for dx in (0.0, 1e-4, 8e-4, 6.4e-3, 5.12e-2, 0.4096, 3.2768, 26.2144):
+            try:
+                if scheme == "lifted":
+                    okkt.lifted_solve(sym, p.n, p.m, W, J, pt.sigma, dx, np.full(p.m, 1e8), pt.rx, pt.ry)
+                else:
+                    okkt.hykkt_solve(sym, p.n, p.m, W, J, pt.sigma, dx, gamma, pt.rx, pt.ry)
+                break
+            except Exception:
+                continue
+        t += time.perf_counter() - t0
+        n_done += 1
+    return t / n_done, n_done
+
+
+def run_kkt(args, ws, rank, local):
+    import ctypes
+    import numpy as np
+    import torch
+    from gen.tray import TrayParams, kkt_point
+    from paper_2403_15913_gb300 import KKTSolver, TrayModel
+    from paper_2403_15913_gb300 import _native as nat
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sig = tuple(float(v) for v in args.sigma.split(","))
+    p = TrayParams(k=args.k, T=args.T)
+    pt = kkt_point(p, args.seed + rank, sig)
+    tm = TrayModel(p.as_array())
+    Wc, Wr, Jr, Jc = tm.pattern()
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64))
+    h_in = {k: f64(v).pin_memory() for k, v in (("w", pt.w), ("lam", pt.lam), ("sigma", pt.sigma),
+                                                 ("rx", pt.rx), ("ry", pt.ry))}
+    d_in = {k: v.cuda() for k, v in h_in.items()}
+    Wv = torch.zeros(tm.nnzW, dtype=torch.float64, device="cuda")
+    Jv = torch.zeros(tm.nnzJ, dtype=torch.float64, device="cuda")
+    dx = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
+                relax_zeros=128, max_width=64)
+
+    def make(prec):
+        t0 = time.perf_counter()
+        s = KKTSolver(p.n, p.m, Wc, Wr, Jr, Jc, precision=prec, **opts)
+        return s, time.perf_counter() - t0
+
+    def step(s, d, delta_x):
+        tm.eval(d["w"], d["lam"], 1.0, None, None, None, Jv, Wv)
+        st = s.factor(Wv, Jv, d["sigma"], None, delta_x)
+        if st != 0:
+            return st
+        return s.solve(d["rx"], d["ry"], dx, dy)
+
+    def find_delta(s):
+        delta_x = 0.0
+        while step(s, d_in, delta_x) == nat.KKT_ERR_NOT_SPD:
+            delta_x = 1e-4 if delta_x == 0 else delta_x * 8
+        torch.cuda.synchronize()
+        return delta_x
+
+    def timed(s, delta_x, steps):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(s, d_in, delta_x)
+        torch.cuda.synchronize()
+        s.reset_stats()
+        s.set_profiling(True)
+        ms, infos = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step(s, d_in, delta_x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(dict(s.info.as_dict(), status=st))
+        s.set_profiling(False)
+        return ms, infos, s.stats()
+
+    prec = 1 if args.precision == "fp32" else 0
+    solver, t_analyse = make(prec)
+    delta_x = find_delta(solver)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, infos, st = timed(solver, delta_x, args.steps)
+    clk = clocks.stop()
+    v = torch.cat([dx, dy]).cpu().numpy()
+    mean_ms = statistics.mean(ms)
+    if dist:
+        t = torch.tensor([mean_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = t.item()
+    fp64_cmp = None
+    if prec == 1:
+        s64, _ = make(0)
+        ms64, infos64, st64 = timed(s64, delta_x, args.steps)
+        v64 = torch.cat([dx, dy]).cpu().numpy()
+        fp64_cmp = {"ms": statistics.mean(ms64), "factor_ms": st64["factor_ms"] / max(1, st64["factor_calls"]),
+                    "bwd_err": max(i["bwd_err"] for i in infos64),
+                    "refine_iters": [i["refine_iters"] for i in infos64][:4],
+                    "rel_diff_vs_fp64_path": float(np.max(np.abs(v - v64)) / np.max(np.abs(v64)))}
+        s64.close()
+    # end to end: inputs host->device, step, (dx, dy) device->host
+    h_out = torch.empty(p.n + p.m, dtype=torch.float64).pin_memory()
+    d_e2e = {k: torch.empty_like(v) for k, v in d_in.items()}
+    e2e = []
+    for rep in range(max(2, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in d_e2e:
+            d_e2e[k].copy_(h_in[k], non_blocking=True)
+        step(solver, d_e2e, delta_x)
+        h_out[:p.n].copy_(dx, non_blocking=True)
+        h_out[p.n:].copy_(dy, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            e2e.append(e0.elapsed_time(e1))
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    sym = solver.sizes()
+    fcalls = max(1, st["factor_calls"])
+    factor_ms = st["factor_ms"] / fcalls
+    f32 = prec == 1
+    roof = {"kernel": "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+            "bound": "alu", "achieved": sym.flops / (factor_ms * 1e-3) / 1e9,
+            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "traffic": None,
+            "peak_source": ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
+                            if f32 else
+                            "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    in_bytes = sum(v.numel() * 8 for v in h_in.values())
+    line = {
+        "metric": KKT_METRIC, "value": mean_ms, "unit": "ms/step", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64", "data": "synthetic",
+        "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), one {args.scheme} "
+                               f"KKT step at a seeded iterate, Sigma log-uniform on [{sig[0]:g}, {sig[1]:g}]",
+                   "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
+                   "delta": 1e-8 if args.scheme == "lifted" else None, "delta_x": delta_x,
+                   "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
+                   "analyse_s": round(t_analyse, 3), "factor_gflop": sym.flops / 1e9,
+                   "factor_ms": factor_ms, "kinv_ms": st["solve_ms"] / max(1, st["kinv_calls"]),
+                   "fp32_factors": st["fp32_factors"], "fp64_fallbacks": st["fp64_fallbacks"],
+                   "status_detail": [i["status_detail"] for i in infos][:4],
+                   "max_bwd_err": max(i["bwd_err"] for i in infos),
+                   "refine_iters": [i["refine_iters"] for i in infos][:4],
+                   "cg_iters": [i["cg_iters"] for i in infos][:4],
+                   "statuses": sorted(set(i["status"] for i in infos)),
+                   "fp64_factor_path": fp64_cmp,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": statistics.mean(e2e), "unit": "ms/step", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": (p.n + p.m) * 8,
+                "scope": "iterate, Sigma and rhs host->device, eval + factor + solve, (dx, dy) device->host"},
+        "gpu_launches": int(st["launches"] / max(1, args.steps) * args.steps) + args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        T_s = 50
+        per, n_s = oracle_kkt_sample(args.k, T_s, args.scheme, sig, args.gamma, 15.0)
+        scale = (args.T + 1) / (T_s + 1)
+        line["cpu_baseline"] = {"value": per * scale * 1e3, "unit": "ms/step", "cores": 1, "kind": "oracle",
+                                "sample": f"{n_s} oracle {args.scheme} KKT steps at {args.k} trays, T={T_s}: "
+                                          f"{per*1e3:.1f} ms each, scaled x{scale:.1f} to T={args.T}"}
+    solver.close()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "kkt":
+        run_kkt(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -154,3 +154,52 @@ def test_fp32_backsolve():
     res = np.max(np.abs(K @ xg - b)) / (okkt.inf_norm(K) * np.max(np.abs(xg)) + np.max(np.abs(b)))
     assert res <= 1e-6, res
     assert res > 1e-14
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sigma_1e8_span_meets_bar(precision):
+    """Sigma log-uniform on [1e-8, 1e8] (late-IPM conditioning) at 32 trays,
+    T = 50: both precisions meet eta <= 1e-10, as does the dense LU
+    solution.  K_orig is nearly singular here (||v|| ~ 1e9 for an N(0,1)
+    right-hand side), so solutions with the same backward error differ at
+    O(1) relative and no forward agreement is asserted."""
+    torch = torch_cuda()
+    p, pt, W, J = instance(32, 50, 0, sigma_range=(1e-8, 1e8))
+    s, st = _factor(p, pt, W, J, None, 0.0, precision=precision)
+    delta_x = 0.0
+    while st == -4:
+        delta_x = 1e-4 if delta_x == 0 else delta_x * 8
+        st = s.factor(to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma), None, delta_x)
+    dx = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
+    st = s.solve(to_dev(torch, pt.rx), to_dev(torch, pt.ry), dx, dy)
+    assert st == 0 and s.info.bwd_err <= 1e-10
+    g = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
+    assert oracle_eta(p, W, J, pt.sigma, delta_x, g[:p.n], g[p.n:], pt.rx, pt.ry) <= 1e-10
+    K = okkt.kkt_matrix(p.n, p.m, W, J, pt.sigma, delta_x)
+    b = np.concatenate([pt.rx, pt.ry])
+    v = okkt.dense_solve(K, b, refine_steps=4)
+    assert okkt.backward_error(K, v, b) <= 1e-10
+
+
+@pytest.mark.parametrize("scheme", ["lifted", "hykkt"])
+def test_full_size_mixed_precision_workload(scheme):
+    """The mixed-precision workload (32 trays, T = 20000, n = 1,300,065,
+    Sigma on [1e-8, 1e8]) with precision = 1: the backward error recomputed
+    by the oracle on the CPU is <= 1e-10 whichever factor carried the solve."""
+    torch = torch_cuda()
+    p, pt, W, J = instance(32, 20000, 0, sigma_range=(1e-8, 1e8))
+    s = solver_for(p, W, J, scheme=scheme, gamma=1e4, max_cg=500, precision=1, **OPTS)
+    Wv, Jv, sigma = to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma)
+    st = s.factor(Wv, Jv, sigma, None, 0.0)
+    delta_x = 0.0
+    while st == -4:
+        delta_x = 1e-4 if delta_x == 0 else delta_x * 8
+        st = s.factor(Wv, Jv, sigma, None, delta_x)
+    dx = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
+    st = s.solve(to_dev(torch, pt.rx), to_dev(torch, pt.ry), dx, dy)
+    assert st == 0 and s.info.bwd_err <= 1e-10
+    assert s.info.status_detail in (1, 2)
+    eta = oracle_eta(p, W, J, pt.sigma, delta_x, dx.cpu().numpy(), dy.cpu().numpy(), pt.rx, pt.ry)
+    assert eta <= 1e-10

@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--gamma", type=float, default=1e4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
-    ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt"])
+    ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt", "batch"])
+    ap.add_argument("--batch", type=int, default=256, help="batch workload: instances")
     ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -552,6 +553,199 @@ def run_kkt(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- batched KKT
+BATCH_METRIC = "batched KKT solves/s"
+
+
+def batch_specs(count, seed):
+    """Instance shapes of the batched workload: trays uniform in
+    {16, 24, 32, 48, 64}, horizons uniform in [20, 400]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return [(int(rng.choice([16, 24, 32, 48, 64])), int(rng.integers(20, 401))) for _ in range(count)]
+
+
+def run_batch(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from gen.tray import TrayParams, kkt_point
+    from paper_2403_15913_gb300 import KKTBatchSolver, KKTSolver, TrayModel
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sig = tuple(float(v) for v in args.sigma.split(","))
+    specs = batch_specs(args.batch, args.seed + 1000 * rank)
+    params = [TrayParams(k=k, T=T) for k, T in specs]
+    models = [TrayModel(p.as_array()) for p in params]
+    pats = [tm.pattern() for tm in models]
+    pts = [kkt_point(p, args.seed + 17 * i + 100000 * rank, sig) for i, p in enumerate(params)]
+    stream = torch.cuda.current_stream()
+    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
+                relax_zeros=128, max_width=64)
+    prec = 1 if args.precision == "fp32" else 0
+    t0 = time.perf_counter()
+    bs = KKTBatchSolver([(p.n, p.m, *pt) for p, pt in zip(params, pats)], precision=prec, **opts)
+    t_analyse = time.perf_counter() - t0
+    xo, yo = bs.layout()
+    wo = np.concatenate([[0], np.cumsum([tm.nnzW for tm in models])])
+    jo = np.concatenate([[0], np.cumsum([tm.nnzJ for tm in models])])
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64))
+    # derivative values at every instance's seeded iterate, by the device kernels
+    Wv = torch.zeros(int(wo[-1]), dtype=torch.float64, device="cuda")
+    Jv = torch.zeros(int(jo[-1]), dtype=torch.float64, device="cuda")
+    for i, (tm, pt) in enumerate(zip(models, pts)):
+        w, lam = f64(pt.w).cuda(), f64(pt.lam).cuda()
+        tm.eval(w, lam, 1.0, None, None, None, Jv[jo[i]:jo[i + 1]], Wv[wo[i]:wo[i + 1]])
+    h_in = {"W": Wv.cpu().pin_memory(), "J": Jv.cpu().pin_memory(),
+            "sigma": f64(np.concatenate([pt.sigma for pt in pts])).pin_memory(),
+            "rx": f64(np.concatenate([pt.rx for pt in pts])).pin_memory(),
+            "ry": f64(np.concatenate([pt.ry for pt in pts])).pin_memory()}
+    d_in = {k: v.cuda() for k, v in h_in.items()}
+    dx = torch.zeros(bs.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(bs.m, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # per-instance delta_x (inertia correction ladder, untimed)
+    delta = np.zeros(args.batch)
+    while bs.factor_batch(d_in["W"], d_in["J"], d_in["sigma"], None, delta) != 0:
+        bad = bs.results()["failed_col"] >= 0
+        delta[bad] = np.where(delta[bad] == 0, 1e-4, delta[bad] * 8)
+
+    def step(d):
+        bs.factor_batch(d["W"], d["J"], d["sigma"], None, delta)
+        return bs.solve(d["rx"], d["ry"], dx, dy)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(d_in)
+    torch.cuda.synchronize()
+    bs.reset_stats()
+    bs.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, statuses, etas = [], set(), []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        statuses.add(step(d_in))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        etas.append(float(bs.results()["bwd_err"].max()))
+    clk = clocks.stop()
+    bs.set_profiling(False)
+    st = bs.stats()
+    res = bs.results()
+    mean_ms = statistics.mean(ms)
+    if dist:
+        t = torch.tensor([mean_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = t.item()
+    value = args.batch * ws / (mean_ms * 1e-3)
+
+    # the plain per-instance FP64 path on the same inputs: one context per
+    # instance, factor + solve one after the other
+    singles = []
+    for i, (p, pt) in enumerate(zip(params, pats)):
+        singles.append(KKTSolver(p.n, p.m, *pt, precision=0, **opts))
+    sx = [dx[xo[i]:xo[i + 1]] for i in range(args.batch)]
+    sy = [dy[yo[i]:yo[i + 1]] for i in range(args.batch)]
+    views = [{k: d_in[k][a:b] for k, (a, b) in (("W", (wo[i], wo[i + 1])), ("J", (jo[i], jo[i + 1])),
+                                                  ("sigma", (xo[i], xo[i + 1])), ("rx", (xo[i], xo[i + 1])),
+                                                  ("ry", (yo[i], yo[i + 1])))} for i in range(args.batch)]
+
+    def serial():
+        for i, s1 in enumerate(singles):
+            v = views[i]
+            s1.factor(v["W"], v["J"], v["sigma"], None, float(delta[i]))
+            s1.solve(v["rx"], v["ry"], sx[i], sy[i])
+
+    serial()
+    torch.cuda.synchronize()
+    ser_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        serial()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ser_ms.append(e0.elapsed_time(e1))
+    ser_eta = max(s1.info.bwd_err for s1 in singles)
+    for s1 in singles:
+        s1.close()
+    # end to end: values and right-hand sides host->device, batched factor +
+    # solve, (dx, dy) device->host
+    h_out = torch.empty(bs.n + bs.m, dtype=torch.float64).pin_memory()
+    d_e2e = {k: torch.empty_like(v) for k, v in d_in.items()}
+    e2e = []
+    for rep in range(4):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in d_e2e:
+            d_e2e[k].copy_(h_in[k], non_blocking=True)
+        step(d_e2e)
+        h_out[:bs.n].copy_(dx, non_blocking=True)
+        h_out[bs.n:].copy_(dy, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            e2e.append(e0.elapsed_time(e1))
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    sym = bs.sizes()
+    factor_ms = st["factor_ms"] / max(1, st["factor_calls"])
+    f32 = prec == 1
+    roof = {"kernel": "batched supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+            "bound": "alu", "achieved": sym.flops / (factor_ms * 1e-3) / 1e9,
+            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "traffic": None,
+            "peak_source": ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
+                            if f32 else
+                            "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    in_bytes = sum(v.numel() * 8 for v in h_in.values())
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.batch} independent tray-column KKT systems, trays uniform in "
+                               f"{{16,24,32,48,64}}, T uniform in [20,400] (n = {bs.n}, m = {bs.m} in "
+                               f"total), one {args.scheme} factor + refined solve of the whole batch per "
+                               f"step, Sigma log-uniform on [{sig[0]:g}, {sig[1]:g}]",
+                   "scheme": args.scheme, "precision": args.precision, "instances": args.batch,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "analyse_s": round(t_analyse, 3), "factor_gflop": sym.flops / 1e9,
+                   "factor_ms": factor_ms, "kinv_ms": st["solve_ms"] / max(1, st["kinv_calls"]),
+                   "tree_levels": sym.levels, "statuses": sorted(statuses),
+                   "max_bwd_err": max(etas), "max_refine_iters": int(res["refine_iters"].max()),
+                   "fp64_fallbacks": st["fp64_fallbacks"],
+                   "delta_x_nonzero": int((delta > 0).sum()),
+                   "per_instance_fp64_path": {"ms_per_batch": statistics.mean(ser_ms),
+                                              "solves_per_s": args.batch / (statistics.mean(ser_ms) * 1e-3),
+                                              "max_bwd_err": ser_eta},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": args.batch * ws / (statistics.mean(e2e) * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": (bs.n + bs.m) * 8,
+                "scope": "W, J, Sigma and rhs host->device, batched factor + solve, (dx, dy) device->host"},
+        "gpu_launches": int(st["launches"] / max(1, args.steps) * args.steps),
+        "clocks": clk,
+    }
+    bs.close()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -559,6 +753,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "kkt":
         run_kkt(args, ws, rank, local)
+    elif args.workload == "batch":
+        run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

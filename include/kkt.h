@@ -177,6 +177,57 @@ kkt_status kkt_solve(kkt_ctx* ctx, const double* d_rx, const double* d_ry,
                      double* d_dx, double* d_dy, double* d_ds,
                      cudaStream_t stream, kkt_info* info);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent systems (uneven sizes), solved together.  The
+ * paper's method reuses one symbolic factor across IPM iterations (Sec.
+ * V-B); a batch applies the same steps to the block-diagonal union of
+ * `count` instances (e.g. many NMPC problems of different horizons), so that
+ * every level of every instance's elimination tree is factorised and solved
+ * in the same launches.  Vectors and value arrays of a batch are the
+ * instances' own arrays concatenated in instance order (instance i owns
+ * variables [x_off[i], x_off[i+1]) and constraints [y_off[i], y_off[i+1]);
+ * its W and J values follow those of instance i-1).  kkt_factor, kkt_solve,
+ * kkt_backsolve and kkt_factor_export accept a batch context unchanged; the
+ * refinement and CG then run per instance (each with its own eta, stopping
+ * rule and CG scalars), and kkt_info carries maxima (refine_iters, bwd_err),
+ * the CG total and the first failing column.
+ * ---------------------------------------------------------------------- */
+
+/* Analysis of a batch: per instance the same arguments as kkt_analyse
+ * (arrays of `count` host pointers), analysed concurrently on host threads.
+ * The result equals kkt_analyse of the union's pattern.  The union must fit
+ * 32-bit indices (n + m, nnz(W), nnz(J) < 2^31), else KKT_ERR_ARG. */
+kkt_status kkt_analyse_batch(int count, const int* n, const int* m,
+                             const int* const* W_colptr, const int* const* W_rowind,
+                             const int* const* J_rowptr, const int* const* J_colind,
+                             const kkt_options* opt, kkt_ctx** out);
+
+/* Same, host only (see kkt_analyse_host). */
+kkt_status kkt_analyse_batch_host(int count, const int* n, const int* m,
+                                  const int* const* W_colptr, const int* const* W_rowind,
+                                  const int* const* J_rowptr, const int* const* J_colind,
+                                  const kkt_options* opt, kkt_ctx** out);
+
+/* count (1 for a context from kkt_analyse), x_off[count+1], y_off[count+1];
+ * any pointer may be NULL. */
+kkt_status kkt_batch_layout(const kkt_ctx* ctx, int* count, int* x_off, int* y_off);
+
+/* kkt_factor with one delta_x per instance (host array delta_x[count]).  An
+ * instance whose pivot fails does not affect the others: the call returns
+ * KKT_ERR_NOT_SPD, kkt_batch_results gives the failing instances, and
+ * kkt_solve still solves the rest (unless every instance failed). */
+kkt_status kkt_factor_batch(kkt_ctx* ctx, const double* d_Wval, const double* d_Jval,
+                            const double* d_sigma, const double* d_D, const double* delta_x,
+                            cudaStream_t stream, kkt_info* info);
+
+/* Per-instance results of the last kkt_factor / kkt_solve (host arrays of
+ * count entries, any may be NULL): status (KKT_OK, KKT_ERR_STALL,
+ * KKT_ERR_MAXIT, KKT_ERR_NOT_SPD), refinement sweeps, CG iterations,
+ * backward error eta (infinity for failed instances) and the first failing
+ * column (permuted numbering of the union, -1 if none). */
+kkt_status kkt_batch_results(const kkt_ctx* ctx, int* status, int* refine_iters,
+                             int* cg_iters, double* bwd_err, int* failed_col);
+
 /* Backsolve with the condensed matrix of the last successful kkt_factor
  * (the SOLVE column of Table I): d_x[n] = K^{-1} d_b[n], original ordering.
  * d_b and d_x may alias.  KKT_ERR_STATE without a factor. */

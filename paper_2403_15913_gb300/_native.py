@@ -30,7 +30,8 @@ KKT_HYKKT = 1
 EXPORTED = [
     "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
     "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_backsolve_noalloc",
-    "kkt_factor_export",
+    "kkt_factor_export", "kkt_analyse_batch", "kkt_analyse_batch_host", "kkt_batch_layout",
+    "kkt_factor_batch", "kkt_batch_results",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
     "kkt_ipm_default_options", "kkt_ipm_create", "kkt_ipm_init", "kkt_ipm_step", "kkt_ipm_solve",
@@ -114,6 +115,18 @@ def lib():
         f.argtypes = [ctypes.c_int, ctypes.c_int, I32P, I32P, I32P, I32P,
                       ctypes.POINTER(Options), ctypes.POINTER(P)]
         f.restype = ctypes.c_int
+    I32PP = ctypes.POINTER(I32P)
+    for name in ("kkt_analyse_batch", "kkt_analyse_batch_host"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_int, I32P, I32P, I32PP, I32PP, I32PP, I32PP,
+                      ctypes.POINTER(Options), ctypes.POINTER(P)]
+        f.restype = ctypes.c_int
+    L.kkt_batch_layout.argtypes = [P, I32P, I32P, I32P]
+    L.kkt_batch_layout.restype = ctypes.c_int
+    L.kkt_factor_batch.argtypes = [P, P, P, P, P, F64P, P, ctypes.POINTER(Info)]
+    L.kkt_factor_batch.restype = ctypes.c_int
+    L.kkt_batch_results.argtypes = [P, I32P, I32P, I32P, F64P, I32P]
+    L.kkt_batch_results.restype = ctypes.c_int
     L.kkt_symbolic_sizes.argtypes = [P, I32P, I64P, I64P, I64P, I32P, F64P]
     L.kkt_symbolic_sizes.restype = ctypes.c_int
     L.kkt_symbolic_export.argtypes = [P, I32P, I32P, I32P, I32P, I32P, I32P]

@@ -57,7 +57,7 @@ def build(verbose: bool = False, debug_checks: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + ["-o", tmp]
+    cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + ["-lpthread", "-o", tmp]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

@@ -22,7 +22,7 @@ constexpr int kThreads = 256;
         if ((active) && *(active) == 0) return; \
     } while (0)
 constexpr int kSubtreeThreads = 64;   // CTA size of the small-subtree kernels
-constexpr int kRedBlocks = 296;   // 2 x 148..152 SMs: partial-sum slots
+constexpr int kChunkRows = 2048;  // rows per reduction chunk (one CTA each)
 
 // Supernode plan (device pointers).  Panel of supernode s: column-major,
 // rows(s) x cols(s), leading dimension sn_r[s], at Lx + sn_lptr[s].
@@ -56,13 +56,15 @@ __global__ void scale_rows_sqrt_kernel(int nnz, const int* __restrict__ jrow,
 // One thread per stored entry of the lower triangle of P K P^T: sums its
 // sources (W entry, diagonal Sigma_x + delta_x, products Js_a Js_b) and
 // writes the panel slot.  Source encoding: b == -1 -> W[a];
-// b == -2 -> sigma[a] + delta_x; b >= 0 -> Js[a] * Js[b].
+// b == -2 -> sigma[a] + delta_x (dvec[a] when a per-variable vector is
+// given); b >= 0 -> Js[a] * Js[b].
 template <typename T>
 __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot,
                                 const long long* __restrict__ sptr,
                                 const int2* __restrict__ src, const double* __restrict__ W,
                                 const double* __restrict__ Js, const double* __restrict__ sigma,
-                                double delta_x, T* __restrict__ Lx) {
+                                double delta_x, const double* __restrict__ dvec,
+                                T* __restrict__ Lx) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
          e += (long long)gridDim.x * blockDim.x) {
         double v = 0.0;
@@ -71,7 +73,7 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
             if (s.y == -1) {
                 v += W[s.x];
             } else if (s.y == -2) {
-                v += sigma[s.x] + delta_x;
+                v += sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
             } else {
                 v = fma(Js[s.x], Js[s.y], v);
             }
@@ -114,14 +116,25 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 __device__ __forceinline__ double pivot_rsqrt(double d) { return rsqrt_newton(d); }
 __device__ __forceinline__ float pivot_rsqrt(float d) { return 1.0f / sqrtf(d); }
 
+// Where a non-positive pivot is reported: atomic minimum of the failing
+// column into word[0], or into word[inst] when col_inst maps every (permuted)
+// column to its instance of a block-diagonal batch.
+struct FailSink {
+    int* word;
+    const int* col_inst;
+    __device__ __forceinline__ void report(int col) const {
+        atomicMin(word + (col_inst ? col_inst[col] : 0), col);
+    }
+};
+
 // Pivot of column j: failure check, L_jj = d / sqrt(d), reciprocal stored
 // for the solves.
 template <typename T>
-__device__ __forceinline__ T take_pivot(T* A, int r, int f, int j, int* fail,
+__device__ __forceinline__ T take_pivot(T* A, int r, int f, int j, FailSink fail,
                                              T* dinv) {
     T d = A[j + (long long)j * r];
     if (!(d > 0.0) || !isfinite(d)) {
-        atomicMin(fail, f + j);
+        fail.report(f + j);
         d = 1.0;
     }
     const T inv = pivot_rsqrt(d);
@@ -136,7 +149,7 @@ __device__ __forceinline__ T take_pivot(T* A, int r, int f, int j, int* fail,
 // diagonal are skipped), with the thread that finishes (j+1, j+1) taking the
 // next pivot.  Two barriers per column.
 template <typename T>
-__device__ __forceinline__ void panel_factor(T* A, int f, int c, int r, int nrows, int* fail,
+__device__ __forceinline__ void panel_factor(T* A, int f, int c, int r, int nrows, FailSink fail,
                                              T* dinv) {
     __shared__ T s_inv[2];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -216,7 +229,7 @@ __device__ __forceinline__ int syrk_tiles_j(int rb) { return (rb + kTileJ - 1) /
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
-                    int* __restrict__ fail, long long smem_elems, T* __restrict__ dinv) {
+                    FailSink fail, long long smem_elems, T* __restrict__ dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
@@ -252,7 +265,7 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
-                  int* __restrict__ fail, T* __restrict__ dinv) {
+                  FailSink fail, T* __restrict__ dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
@@ -426,7 +439,7 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
 template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                      T* __restrict__ Lx, int* __restrict__ fail, T* __restrict__ dinv) {
+                      T* __restrict__ Lx, FailSink fail, T* __restrict__ dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -635,23 +648,33 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
+// ------------------------------------------------------------- segmented
+// Reductions and vector updates run over chunks: contiguous row ranges of one
+// instance of a block-diagonal batch (a single system is a batch of one).
+// Chunk = {lo, hi, inst, -}; one CTA per chunk, so every reduction result
+// belongs to one instance and the order of additions is fixed.
+// Rows of the "xy" space are the n primal rows followed by the m dual rows.
+
 // Residual of the original system: r = b - K_orig v, with
 //   K_orig = [[W + diag(sigma + delta_x), J^T], [J, -diag(C)]]
-// and the max-norms of r, v, b accumulated into out[0..2].
+// (delta_x per variable when dvec is given) and the max-norms of r, v, b
+// accumulated into red[3 inst + 0..2].
 __global__ void __launch_bounds__(kThreads)
-residual_kernel(int n, int m, const int* __restrict__ wf_ptr, const int* __restrict__ wf_col,
-                const int* __restrict__ wf_idx, const double* __restrict__ W,
-                const int* __restrict__ j_ptr, const int* __restrict__ j_col,
-                const int* __restrict__ jt_ptr, const int* __restrict__ jt_row,
-                const int* __restrict__ jt_idx, const double* __restrict__ J,
-                const double* __restrict__ sigma, double delta_x, const double* __restrict__ C,
+residual_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ wf_ptr,
+                const int* __restrict__ wf_col, const int* __restrict__ wf_idx,
+                const double* __restrict__ W, const int* __restrict__ j_ptr,
+                const int* __restrict__ j_col, const int* __restrict__ jt_ptr,
+                const int* __restrict__ jt_row, const int* __restrict__ jt_idx,
+                const double* __restrict__ J, const double* __restrict__ sigma, double delta_x,
+                const double* __restrict__ dvec, const double* __restrict__ C,
                 const double* __restrict__ bx, const double* __restrict__ by,
                 const double* __restrict__ vx, const double* __restrict__ vy,
-                double* __restrict__ rx, double* __restrict__ ry, double* __restrict__ out) {
+                double* __restrict__ rx, double* __restrict__ ry, double* __restrict__ red) {
+    const int4 ch = chunks[blockIdx.x];
     double mr = 0.0, mv = 0.0, mb = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
         if (i < n) {
-            double s = (sigma[i] + delta_x) * vx[i];
+            double s = (sigma[i] + (dvec ? dvec[i] : delta_x)) * vx[i];
             for (int q = wf_ptr[i]; q < wf_ptr[i + 1]; ++q) s += W[wf_idx[q]] * vx[wf_col[q]];
             for (int q = jt_ptr[i]; q < jt_ptr[i + 1]; ++q) s += J[jt_idx[q]] * vy[jt_row[q]];
             double r = bx[i] - s;
@@ -674,25 +697,27 @@ residual_kernel(int n, int m, const int* __restrict__ wf_ptr, const int* __restr
     mv = block_max(mv);
     mb = block_max(mb);
     if (threadIdx.x == 0) {
-        atomic_max_nonneg(out + 0, mr);
-        atomic_max_nonneg(out + 1, mv);
-        atomic_max_nonneg(out + 2, mb);
+        atomic_max_nonneg(red + 3 * ch.z + 0, mr);
+        atomic_max_nonneg(red + 3 * ch.z + 1, mv);
+        atomic_max_nonneg(red + 3 * ch.z + 2, mb);
     }
 }
 
-// ||K_orig||_inf (row sums of |K_orig|) into out[0] (atomic max).
+// ||K_orig||_inf (row sums of |K_orig|) per instance into knorm[inst].
 __global__ void __launch_bounds__(kThreads)
-knorm_kernel(int n, int m, const int* __restrict__ wf_ptr, const int* __restrict__ wf_col,
-             const int* __restrict__ wf_idx, const double* __restrict__ W,
-             const int* __restrict__ j_ptr, const int* __restrict__ jt_ptr,
-             const int* __restrict__ jt_idx, const double* __restrict__ J,
-             const double* __restrict__ sigma, double delta_x, const double* __restrict__ C,
-             double* __restrict__ out) {
+knorm_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ wf_ptr,
+             const int* __restrict__ wf_col, const int* __restrict__ wf_idx,
+             const double* __restrict__ W, const int* __restrict__ j_ptr,
+             const int* __restrict__ jt_ptr, const int* __restrict__ jt_idx,
+             const double* __restrict__ J, const double* __restrict__ sigma, double delta_x,
+             const double* __restrict__ dvec, const double* __restrict__ C,
+             double* __restrict__ knorm) {
+    const int4 ch = chunks[blockIdx.x];
     double mx = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
         double s = 0.0;
         if (i < n) {
-            double d = sigma[i] + delta_x;
+            double d = sigma[i] + (dvec ? dvec[i] : delta_x);
             for (int q = wf_ptr[i]; q < wf_ptr[i + 1]; ++q) {
                 if (wf_col[q] == i) d += W[wf_idx[q]];
                 else s += fabs(W[wf_idx[q]]);
@@ -707,13 +732,20 @@ knorm_kernel(int n, int m, const int* __restrict__ wf_ptr, const int* __restrict
         mx = fmax(mx, s);
     }
     mx = block_max(mx);
-    if (threadIdx.x == 0) atomic_max_nonneg(out, mx);
+    if (threadIdx.x == 0) atomic_max_nonneg(knorm + ch.z, mx);
 }
 
-// y += a * x over two concatenated segments
-__global__ void axpy_kernel(int n, double a, const double* __restrict__ x, double* __restrict__ y) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] += a * x[i];
+// (ux, uy) += (dx, dy) on the rows of instances with act[inst] != 0
+__global__ void __launch_bounds__(kThreads)
+seg_axpy_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ act,
+                const double* __restrict__ dx, const double* __restrict__ dy,
+                double* __restrict__ ux, double* __restrict__ uy) {
+    const int4 ch = chunks[blockIdx.x];
+    if (!act[ch.z]) return;
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
+        if (i < n) ux[i] += dx[i];
+        else uy[i - n] += dy[i - n];
+    }
 }
 
 __global__ void recip_kernel(int n, const double* __restrict__ x, double* __restrict__ y) {
@@ -725,75 +757,119 @@ __global__ void fill_kernel(int n, double v, double* __restrict__ y) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = v;
 }
 
-// Deterministic dot product: fixed grid of kRedBlocks CTAs writes partial
-// sums, a single CTA adds them in a fixed order.
+// out[i] = val[inst of i]: per-variable delta_x of a batch (x-space chunks)
+__global__ void expand_kernel(const int4* __restrict__ chunks, const double* __restrict__ val,
+                              double* __restrict__ out) {
+    const int4 ch = chunks[blockIdx.x];
+    const double v = val[ch.z];
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) out[i] = v;
+}
+
+// ---- per-instance CG on S_gamma (HyKKT, Eq. schurcomp), dual-space chunks.
+// cgs[4 inst + {0: rr, 1: rr_new, 2: p^T S p, 3: stop}], cgi[2 inst + {0:
+// active, 1: iterations}]; any[0] = some instance still active (guards the
+// graph-captured iteration), any[1] unused.
+
+// Deterministic dot products: per-chunk partial sums, then per instance the
+// partials of its chunks added in chunk order by one warp.
 __global__ void __launch_bounds__(kThreads)
-dot_partial_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
-                   double* __restrict__ part,
-    const int* __restrict__ active) {
+seg_dot_partial_kernel(const int4* __restrict__ chunks, const double* __restrict__ a,
+                       const double* __restrict__ b, double* __restrict__ part,
+                       const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
+    const int4 ch = chunks[blockIdx.x];
     double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s += a[i] * b[i];
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) s += a[i] * b[i];
     s = block_sum(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(kThreads)
-dot_final_kernel(int nparts, const double* __restrict__ part, double* __restrict__ out,
-    const int* __restrict__ active) {
+seg_dot_final_kernel(int nb, const int* __restrict__ inst_chunk_ptr, const double* __restrict__ part,
+                     double* __restrict__ cgs, int slot, const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
+    const int inst = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (inst >= nb) return;
     double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
-    s = block_sum(s);
-    if (threadIdx.x == 0) *out = s;
+    for (int q = inst_chunk_ptr[inst] + lane; q < inst_chunk_ptr[inst + 1]; q += 32) s += part[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) cgs[4 * inst + slot] = s;
 }
 
-// CG updates with scalars kept on the device.
-// x += alpha p; r -= alpha q   with alpha = sc[rr] / sc[pq]
-__global__ void cg_update_xr_kernel(int m, const double* __restrict__ sc, int i_rr, int i_pq,
-                                    const double* __restrict__ p, const double* __restrict__ q,
-                                    double* __restrict__ x, double* __restrict__ r,
-    const int* __restrict__ active) {
+// x += alpha p; r -= alpha q  with alpha = rr / pSp of the chunk's instance
+__global__ void __launch_bounds__(kThreads)
+cg_update_xr_kernel(const int4* __restrict__ chunks, const double* __restrict__ cgs,
+                    const int* __restrict__ cgi, const double* __restrict__ p,
+                    const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                    const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    const double alpha = sc[i_rr] / sc[i_pq];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int4 ch = chunks[blockIdx.x];
+    if (!cgi[2 * ch.z]) return;
+    const double alpha = cgs[4 * ch.z + 0] / cgs[4 * ch.z + 2];
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
         x[i] += alpha * p[i];
         r[i] -= alpha * q[i];
     }
 }
 
-// p = r + beta p   with beta = sc[rr_new] / sc[rr_old]
-__global__ void cg_update_p_kernel(int m, const double* __restrict__ sc, int i_new, int i_old,
-                                   const double* __restrict__ r, double* __restrict__ p,
-    const int* __restrict__ active) {
+// p = r + beta p  with beta = rr_new / rr
+__global__ void __launch_bounds__(kThreads)
+cg_update_p_kernel(const int4* __restrict__ chunks, const double* __restrict__ cgs,
+                   const int* __restrict__ cgi, const double* __restrict__ r, double* __restrict__ p,
+                   const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    const double beta = sc[i_new] / sc[i_old];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        p[i] = r[i] + beta * p[i];
+    const int4 ch = chunks[blockIdx.x];
+    if (!cgi[2 * ch.z]) return;
+    const double beta = cgs[4 * ch.z + 1] / cgs[4 * ch.z + 0];
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) p[i] = r[i] + beta * p[i];
 }
 
-// CG bookkeeping on the device (HyKKT, Eq. schurcomp): cg[0] = active flag,
-// cg[1] = iterations.  Start: stop = tol sqrt(rr0); active when
-// sqrt(rr0) > stop.  After each iteration: rr_old <- rr_new, iterations + 1,
-// active while sqrt(rr) > stop and iterations < max_cg.
-__global__ void cg_init_kernel(double* __restrict__ sc, int i_rr, int i_stop, double tol, int max_cg,
-                               int* __restrict__ cg) {
-    const double rr = sc[i_rr];
-    const double stop = tol * sqrt(rr);
-    sc[i_stop] = stop;
-    cg[0] = (sqrt(rr) > stop && max_cg > 0) ? 1 : 0;
-    cg[1] = 0;
+__device__ __forceinline__ int block_or(int v) {
+    return __syncthreads_or(v);
 }
 
-__global__ void cg_check_kernel(double* __restrict__ sc, int i_new, int i_old, int i_stop, int max_cg,
-                                int* __restrict__ cg) {
-    if (cg[0] == 0) return;
-    const double rr = sc[i_new];
-    sc[i_old] = rr;
-    const int it = cg[1] + 1;
-    cg[1] = it;
-    cg[0] = (sqrt(rr) > sc[i_stop] && it < max_cg) ? 1 : 0;
+// Start: stop = tol sqrt(rr0); an instance is active when act[inst] (its
+// refinement still runs), sqrt(rr0) > stop and max_cg > 0.  One CTA.
+__global__ void __launch_bounds__(kThreads)
+cg_init_kernel(int nb, double* __restrict__ cgs, int* __restrict__ cgi, const int* __restrict__ act,
+               double tol, int max_cg, int* __restrict__ any) {
+    int mine = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double rr = cgs[4 * i + 0];
+        const double stop = tol * sqrt(rr);
+        cgs[4 * i + 3] = stop;
+        const int a = (act[i] && sqrt(rr) > stop && max_cg > 0) ? 1 : 0;
+        cgi[2 * i] = a;
+        cgi[2 * i + 1] = 0;
+        mine |= a;
+    }
+    mine = block_or(mine);
+    if (threadIdx.x == 0) {
+        any[0] = mine;
+        any[1] = 0;
+    }
+}
+
+// After each iteration: rr <- rr_new, iterations + 1, active while
+// sqrt(rr) > stop and iterations < max_cg.  One CTA.
+__global__ void __launch_bounds__(kThreads)
+cg_check_kernel(int nb, double* __restrict__ cgs, int* __restrict__ cgi, int max_cg,
+                int* __restrict__ any) {
+    if (any[0] == 0) return;
+    int mine = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        if (!cgi[2 * i]) continue;
+        const double rr = cgs[4 * i + 1];
+        cgs[4 * i + 0] = rr;
+        const int it = cgi[2 * i + 1] + 1;
+        cgi[2 * i + 1] = it;
+        const int a = (sqrt(rr) > cgs[4 * i + 3] && it < max_cg) ? 1 : 0;
+        cgi[2 * i] = a;
+        mine |= a;
+    }
+    mine = block_or(mine);
+    if (threadIdx.x == 0) any[0] = mine;
 }
 
 }  // namespace kktgb

@@ -3,11 +3,13 @@
 #include "kkt.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -69,9 +71,7 @@ struct kkt_ctx {
     int *d_j_ptr = nullptr, *d_j_col = nullptr;
     int *d_jt_ptr = nullptr, *d_jt_row = nullptr, *d_jt_idx = nullptr;
     double* d_Lx = nullptr;
-    double* d_sc = nullptr;     // device scalars
     int* d_fail = nullptr;
-    double* d_part = nullptr;
     // work vectors
     double *w_xp = nullptr, *w_t = nullptr, *w_r = nullptr, *w_d = nullptr;
     double *w_q = nullptr, *w_p = nullptr, *w_sp = nullptr, *w_res = nullptr, *w_cgx = nullptr;
@@ -83,7 +83,6 @@ struct kkt_ctx {
     // FP32 factor (precision = 1): panels, reciprocal pivots, permuted vector
     float *d_Lx32 = nullptr, *d_dinv32 = nullptr, *w_xp32 = nullptr;
     int cur_prec = 0;           // precision of the current factor: 0 FP64, 1 FP32
-    double* h_sc = nullptr;     // pinned host scalars
     // factor inputs of the last kkt_factor
     bool factored = false;
     const double *f_W = nullptr, *f_J = nullptr, *f_sigma = nullptr, *f_D = nullptr;
@@ -97,8 +96,36 @@ struct kkt_ctx {
     cudaGraph_t tri_graph = nullptr, cg_graph = nullptr, tri_graph32 = nullptr, cg_graph32 = nullptr;
     cudaGraphExec_t tri_exec = nullptr, cg_exec = nullptr, tri_exec32 = nullptr, cg_exec32 = nullptr;
     size_t tri_nodes = 0, cg_nodes = 0, tri_nodes32 = 0, cg_nodes32 = 0;
-    int* d_cg = nullptr;        // [active, iterations]
+    int* d_cg = nullptr;        // [some instance's CG active, unused]
     int* h_cg = nullptr;        // pinned
+    // Block-diagonal batch of nb independent systems (nb = 1 for a single
+    // one): instance i owns primal rows [xoff[i], xoff[i+1]) and dual rows
+    // [yoff[i], yoff[i+1]).  Reductions run over chunks of rows of one
+    // instance: d_ch_xy covers the n + m rows (the nch_x primal chunks
+    // first), d_ch_y the m dual rows, instance i owning dual chunks
+    // [chy_ptr[i], chy_ptr[i+1]).
+    int nb = 1;
+    std::vector<int> h_xoff, h_yoff, h_chy_ptr;
+    int4 *d_ch_xy = nullptr, *d_ch_y = nullptr;
+    int nch_xy = 0, nch_x = 0, nch_y = 0;
+    int* d_chy_ptr = nullptr;
+    int* d_col_inst = nullptr;   // instance of every permuted column (nb > 1)
+    double* d_knorm = nullptr;   // ||K_orig,i||_inf per instance
+    double* d_red = nullptr;     // residual maxima, 3 per instance
+    int* d_act = nullptr;        // instances whose refinement still runs
+    double* d_cgs = nullptr;     // CG scalars, 4 per instance
+    int* d_cgi = nullptr;        // CG active flag and iterations, 2 per instance
+    double* d_part_y = nullptr;  // partial sums, one per dual chunk
+    double* d_dvec = nullptr;    // per-variable delta_x of a batch factor
+    double* d_dval = nullptr;    // per-instance delta_x
+    const double* f_dvec = nullptr;   // d_dvec when the last factor used it
+    double* h_red = nullptr;     // pinned: 3 nb residual maxima
+    int* h_act = nullptr;        // pinned: nb
+    int* h_int = nullptr;        // pinned: 2 nb
+    std::vector<double> h_knorm, h_delta;
+    // per-instance results of the last factor / solve
+    std::vector<int> r_status, r_refine, r_cg, r_fail;
+    std::vector<double> r_eta;
     // tracing
     bool profiling = false;
     kkt_stats stats{};
@@ -113,9 +140,6 @@ struct kkt_ctx {
 
 namespace {
 
-// device scalar slots
-enum { SC_RMAX = 0, SC_VMAX, SC_BMAX, SC_KNORM, SC_DOT0, SC_DOT1, SC_DOT2, SC_DOT3, SC_STOP,
-       SC_COUNT };
 constexpr int kCgBatch = 8;   // CG iterations enqueued between convergence checks
 
 thread_local std::string g_err;   // last error of calls that have no context
@@ -503,6 +527,57 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     for (int s = 0; s < ns; ++s)
         if (sn_c[s] > 64) return set_err(c, KKT_ERR_INTERNAL, "supernode wider than 64 columns");
 
+    // ---- reduction chunks (rows of one instance each) and column instances
+    const int nb = c->nb;
+    std::vector<int4> ch_xy, ch_y;
+    c->h_chy_ptr.assign(nb + 1, 0);
+    auto make_chunks = [](const std::vector<int>& off, int base, std::vector<int4>& out,
+                          std::vector<int>* inst_ptr) {
+        for (int i = 0; i + 1 < (int)off.size(); ++i) {
+            if (inst_ptr) (*inst_ptr)[i] = (int)out.size();
+            for (int lo = off[i]; lo < off[i + 1]; lo += kChunkRows)
+                out.push_back(make_int4(base + lo, base + std::min(off[i + 1], lo + kChunkRows), i, 0));
+        }
+        if (inst_ptr) inst_ptr->back() = (int)out.size();
+    };
+    make_chunks(c->h_xoff, 0, ch_xy, nullptr);
+    c->nch_x = (int)ch_xy.size();
+    make_chunks(c->h_yoff, n, ch_xy, nullptr);
+    c->nch_xy = (int)ch_xy.size();
+    make_chunks(c->h_yoff, 0, ch_y, &c->h_chy_ptr);
+    c->nch_y = (int)ch_y.size();
+    if (c->h_xoff.size() != (size_t)nb + 1 || c->h_xoff.back() != n || c->h_yoff.back() != m)
+        return set_err(c, KKT_ERR_INTERNAL, "batch offsets do not cover the system");
+    TRY(upload(c, &c->d_ch_xy, ch_xy));
+    TRY(upload(c, &c->d_ch_y, ch_y));
+    TRY(upload(c, &c->d_chy_ptr, c->h_chy_ptr));
+    if (nb > 1) {
+        std::vector<int> col_inst(n);
+        for (int j = 0; j < n; ++j) {
+            const int v = S.perm[j];
+            col_inst[j] = (int)(std::upper_bound(c->h_xoff.begin(), c->h_xoff.end(), v) - c->h_xoff.begin()) - 1;
+        }
+        TRY(upload(c, &c->d_col_inst, col_inst));
+        TRY(alloc(c, &c->d_dvec, n));
+        TRY(alloc(c, &c->d_dval, nb));
+    }
+    TRY(alloc(c, &c->d_knorm, nb));
+    TRY(alloc(c, &c->d_red, 3 * (size_t)nb));
+    TRY(alloc(c, &c->d_act, nb));
+    TRY(alloc(c, &c->d_cgs, 4 * (size_t)nb));
+    TRY(alloc(c, &c->d_cgi, 2 * (size_t)nb));
+    TRY(alloc(c, &c->d_part_y, std::max(1, c->nch_y)));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_red, 3 * (size_t)nb * sizeof(double)));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_act, (size_t)nb * sizeof(int)));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_int, 2 * (size_t)nb * sizeof(int)));
+    c->h_knorm.assign(nb, 0.0);
+    c->h_delta.assign(nb, 0.0);
+    c->r_status.assign(nb, 0);
+    c->r_refine.assign(nb, 0);
+    c->r_cg.assign(nb, 0);
+    c->r_fail.assign(nb, -1);
+    c->r_eta.assign(nb, 0.0);
+
     // ---- upload
     int *d_sn_f, *d_sn_c, *d_sn_r, *d_sn_rptr, *d_rows, *d_seg_ptr, *d_seg_t, *d_seg_a, *d_seg_b,
         *d_relmap;
@@ -548,9 +623,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(upload(c, &c->d_jt_row, jt_row));
     TRY(upload(c, &c->d_jt_idx, jt_idx));
     TRY(alloc(c, &c->d_Lx, (size_t)c->panel));
-    TRY(alloc(c, &c->d_sc, 16));
-    TRY(alloc(c, &c->d_fail, 4));
-    TRY(alloc(c, &c->d_part, kRedBlocks));
+    TRY(alloc(c, &c->d_fail, nb));
     const size_t nm = (size_t)n + m;
     TRY(alloc(c, &c->w_xp, n));
     TRY(alloc(c, &c->w_t, n));
@@ -568,7 +641,6 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(alloc(c, &c->v_Js, std::max(1, J_rowptr[m])));
     TRY(alloc(c, &c->v_sigma, n));
     TRY(alloc(c, &c->v_D, std::max(1, m)));
-    CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, 16 * sizeof(double)));
     TRY(alloc(c, &c->d_cg, 2));
     if (c->opt.precision == 1) {
         TRY(alloc(c, &c->d_Lx32, (size_t)c->panel));
@@ -636,29 +708,36 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
     return KKT_OK;
 }
 
-kkt_status dot(kkt_ctx* c, int len, const double* a, const double* b, int slot, cudaStream_t st,
-               const int* active = nullptr) {
+// Per-instance dot products of two dual-space vectors into cgs[4 i + slot].
+void seg_dot(kkt_ctx* c, const double* a, const double* b, int slot, cudaStream_t st,
+             const int* active = nullptr) {
     c->stats.launches += 2;
-    dot_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(len, a, b, c->d_part, active);
-    dot_final_kernel<<<1, kThreads, 0, st>>>(kRedBlocks, c->d_part, c->d_sc + slot, active);
-    return KKT_OK;
+    if (c->nch_y > 0)
+        seg_dot_partial_kernel<<<c->nch_y, kThreads, 0, st>>>(c->d_ch_y, a, b, c->d_part_y, active);
+    constexpr int kWarps = kThreads / 32;
+    seg_dot_final_kernel<<<(c->nb + kWarps - 1) / kWarps, kThreads, 0, st>>>(
+        c->nb, c->d_chy_ptr, c->d_part_y, c->d_cgs, slot, active);
 }
 
-// r = b - K_orig v and eta; returns eta through *eta (host sync)
+// r = b - K_orig v and the backward error of every instance (host sync):
+// eta_i = ||r_i||_inf / (||K_i||_inf ||v_i||_inf + ||b_i||_inf).
 kkt_status residual(kkt_ctx* c, const double* bx, const double* by, const double* vx,
-                    const double* vy, double* rx, double* ry, cudaStream_t st, double* eta) {
-    const int n = c->n, m = c->m;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_sc + SC_RMAX, 0, 3 * sizeof(double), st));
+                    const double* vy, double* rx, double* ry, cudaStream_t st, std::vector<double>& eta) {
+    const int n = c->n, nb = c->nb;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_red, 0, 3 * (size_t)nb * sizeof(double), st));
     c->stats.launches += 1;
-    residual_kernel<<<grid_for((long long)n + m), kThreads, 0, st>>>(
-        n, m, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_j_col, c->d_jt_ptr,
-        c->d_jt_row, c->d_jt_idx, c->f_J, c->f_sigma, c->f_delta_x, c->f_C, bx, by, vx, vy, rx, ry,
-        c->d_sc + SC_RMAX);
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    residual_kernel<<<c->nch_xy, kThreads, 0, st>>>(
+        c->d_ch_xy, n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_j_col,
+        c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->f_J, c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C,
+        bx, by, vx, vy, rx, ry, c->d_red);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_red, c->d_red, 3 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    const double rmax = c->h_sc[0], vmax = c->h_sc[1], bmax = c->h_sc[2];
-    const double den = c->knorm * vmax + bmax;
-    *eta = den > 0 ? rmax / den : (rmax > 0 ? INFINITY : 0.0);
+    eta.resize(nb);
+    for (int i = 0; i < nb; ++i) {
+        const double rmax = c->h_red[3 * i], vmax = c->h_red[3 * i + 1], bmax = c->h_red[3 * i + 2];
+        const double den = c->h_knorm[i] * vmax + bmax;
+        eta[i] = den > 0 ? rmax / den : (rmax > 0 ? INFINITY : 0.0);
+    }
     return KKT_OK;
 }
 
@@ -690,13 +769,14 @@ void enqueue_cg_iteration(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStr
     scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, c->w_tn, act);
     j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
                                                      nullptr, nullptr, 1.0, c->w_sp, act);
-    dot(c, m, c->w_p, c->w_sp, SC_DOT2, st, act);
-    cg_update_xr_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, SC_DOT0, SC_DOT2, c->w_p,
-                                                          c->w_sp, c->w_cgx, c->w_res, act);
-    dot(c, m, c->w_res, c->w_res, SC_DOT1, st, act);
-    cg_update_p_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_sc, SC_DOT1, SC_DOT0, c->w_res,
-                                                         c->w_p, act);
-    cg_check_kernel<<<1, 1, 0, st>>>(c->d_sc, SC_DOT1, SC_DOT0, SC_STOP, c->opt.max_cg, c->d_cg);
+    seg_dot(c, c->w_p, c->w_sp, 2, st, act);
+    if (c->nch_y > 0)
+        cg_update_xr_kernel<<<c->nch_y, kThreads, 0, st>>>(c->d_ch_y, c->d_cgs, c->d_cgi, c->w_p, c->w_sp,
+                                                           c->w_cgx, c->w_res, act);
+    seg_dot(c, c->w_res, c->w_res, 1, st, act);
+    if (c->nch_y > 0)
+        cg_update_p_kernel<<<c->nch_y, kThreads, 0, st>>>(c->d_ch_y, c->d_cgs, c->d_cgi, c->w_res, c->w_p, act);
+    cg_check_kernel<<<1, kThreads, 0, st>>>(c->nb, c->d_cgs, c->d_cgi, c->opt.max_cg, c->d_cg);
 }
 
 // Capture the triangular-solve sequence and (HyKKT) one CG iteration as
@@ -732,13 +812,14 @@ kkt_status capture_graphs(kkt_ctx* c) {
 }
 
 // HyKKT inner solve (Eq. hykkt / Eq. schurcomp): d = K_orig^{-1} r up to the
-// CG tolerance.  Returns CG iterations through *its.  The CG iterations run
-// as graph launches in batches of kCgBatch between convergence checks; the
-// device flag makes the iterations after convergence no-ops, so the iteration
-// count equals that of a check after every iteration.
+// CG tolerance, one CG per instance (instances with d_act = 0 keep dy = 0).
+// Adds every instance's CG iterations to its[i].  The CG iterations run as
+// graph launches in batches of kCgBatch between convergence checks; the
+// device flags make the iterations after convergence no-ops, so the counts
+// equal those of a check after every iteration.
 kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* dx, double* dy,
-                       cudaStream_t st, int* its, bool* cg_ok) {
-    const int n = c->n, m = c->m;
+                       cudaStream_t st, std::vector<int>& its) {
+    const int n = c->n, m = c->m, nb = c->nb;
     const double gamma = c->f_Dconst;
     c->stats.launches += 4;
     // r_gamma = r_x + gamma J^T r_y ; q = K_gamma^{-1} r_gamma
@@ -750,8 +831,9 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
                                                      nullptr, 1.0, c->w_res, nullptr);
     CUDA_TRY(c, cudaMemsetAsync(c->w_cgx, 0, m * sizeof(double), st));
     CUDA_TRY(c, cudaMemcpyAsync(c->w_p, c->w_res, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TRY(dot(c, m, c->w_res, c->w_res, SC_DOT0, st));
-    cg_init_kernel<<<1, 1, 0, st>>>(c->d_sc, SC_DOT0, SC_STOP, c->opt.tol_cg, c->opt.max_cg, c->d_cg);
+    seg_dot(c, c->w_res, c->w_res, 0, st);
+    cg_init_kernel<<<1, kThreads, 0, st>>>(nb, c->d_cgs, c->d_cgi, c->d_act, c->opt.tol_cg, c->opt.max_cg,
+                                           c->d_cg);
     const int sp = span_begin(c, 3, st);
     while (true) {
         const bool f32 = c->cur_prec == 1;
@@ -771,14 +853,14 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
         if (c->h_cg[0] == 0) break;
     }
     span_end(c, sp, st);
-    const int it = c->h_cg[1];
-    c->stats.kinv_calls += it;
-    *its = it;
-    // converged unless the iteration limit stopped it (same test as the loop)
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_DOT1, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc + 1, c->d_sc + SC_STOP, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_int, c->d_cgi, 2 * (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    *cg_ok = it < c->opt.max_cg || !(std::sqrt(c->h_sc[0]) > c->h_sc[1]);
+    int it_max = 0;
+    for (int i = 0; i < nb; ++i) {
+        its[i] += c->h_int[2 * i + 1];
+        it_max = std::max(it_max, c->h_int[2 * i + 1]);
+    }
+    c->stats.kinv_calls += it_max;
     // dx = K_gamma^{-1} (r_gamma - J^T dy)
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
                                                      c->f_J, c->w_rg, c->w_cgx, nullptr, 1.0, -1.0,
@@ -790,23 +872,27 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
 
 // Zero the panels, assemble, factorise (subtree tasks, levels), normalise to
 // unit diagonal: everything the numeric factorisation enqueues for the panel
-// precision T.  The fail word is reset first.
+// precision T.  The fail words (one per instance) are reset first to
+// kNoFail, above every column index.
+constexpr int kNoFail = 0x7f7f7f7f;
+
 template <typename T>
 kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
-    const int big = 0x7fffffff;
     const int sp_a = span_begin(c, 0, st);
     CUDA_TRY(c, cudaMemsetAsync(Lx, 0, (size_t)c->panel * sizeof(T), st));
     assemble_kernel<T><<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
-                                                             c->f_W, c->v_Js, c->f_sigma, delta_x, Lx);
+                                                             c->f_W, c->v_Js, c->f_sigma, delta_x,
+                                                             c->f_dvec, Lx);
     span_end(c, sp_a, st);
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_fail, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_fail, 0x7f, (size_t)c->nb * sizeof(int), st));
+    const FailSink fs{c->d_fail, c->nb > 1 ? c->d_col_inst : nullptr};
     const int sp_f = span_begin(c, 1, st);
     c->stats.factor_calls++;
     c->stats.launches += 2 + c->nlev;
     c->stats.factor_launches += c->nlev;
     if (c->ntasks > 0) {
         factor_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_rc * sizeof(T), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, Lx, c->d_fail, dinv);
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, fs, dinv);
         c->stats.launches += 1;
         c->stats.factor_launches += 1;
     }
@@ -816,11 +902,11 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
         if (!c->lvl_split[l]) {
             long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
             factor_level_kernel<T><<<cnt, kThreads, (size_t)need * sizeof(T), st>>>(
-                c->plan, lsn, Lx, c->d_fail, need, dinv);
+                c->plan, lsn, Lx, fs, need, dinv);
             continue;
         }
         const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
-        potrf_diag_kernel<T><<<cnt, kThreads, dsm, st>>>(c->plan, lsn, Lx, c->d_fail, dinv);
+        potrf_diag_kernel<T><<<cnt, kThreads, dsm, st>>>(c->plan, lsn, Lx, fs, dinv);
         const int nt = c->lvl_trsm_ptr[l + 1] - c->lvl_trsm_ptr[l];
         if (nt > 0)
             trsm_rows_kernel<T><<<nt, 32 * kTrsmWarps, 0, st>>>(
@@ -862,9 +948,7 @@ void kkt_default_options(kkt_options* o) {
 }
 
 namespace {
-kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind,
-                          const int* J_rowptr, const int* J_colind, const kkt_options* opt,
-                          bool device, kkt_ctx** out) {
+kkt_status new_ctx(const kkt_options* opt, kkt_ctx** out) {
     if (!out) return set_err(nullptr, KKT_ERR_ARG, "out is NULL");
     *out = nullptr;
     kkt_ctx* c = new (std::nothrow) kkt_ctx();
@@ -879,26 +963,23 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
         return set_err(nullptr, KKT_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32 factor)");
     }
     if (c->opt.max_width <= 0 || c->opt.max_width > 64) c->opt.max_width = 64;
-    c->n = n;
-    c->m = m;
-    Graph g;
-    std::string e = build_graph(n, m, W_colptr, W_rowind, J_rowptr, J_colind, g);
-    if (!e.empty()) {
-        delete c;
-        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
-    }
-    c->nnzW = W_colptr[n];
-    c->nnzJ = J_rowptr[m];
+    *out = c;
+    return KKT_OK;
+}
+
+SymbolicOptions symbolic_options(const kkt_options& o) {
     SymbolicOptions so;
-    so.leaf_size = c->opt.leaf_size;
-    so.relax_cols = c->opt.relax_cols;
-    so.relax_zeros = c->opt.relax_zeros;
-    so.max_width = c->opt.max_width;
-    e = analyse(g, so, c->sym);
-    if (!e.empty()) {
-        delete c;
-        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
-    }
+    so.leaf_size = o.leaf_size;
+    so.relax_cols = o.relax_cols;
+    so.relax_zeros = o.relax_zeros;
+    so.max_width = o.max_width;
+    return so;
+}
+
+// After c->sym, sizes and batch offsets are set: tree height, device plan,
+// kernel attributes and graphs.  Destroys c on failure.
+kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, const int* J_rowptr,
+                      const int* J_colind, bool device, kkt_ctx** out) {
     const int ns = c->sym.ns();
     c->h_sn_c.resize(ns);
     c->h_sn_r.resize(ns);
@@ -942,6 +1023,104 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
     *out = c;
     return KKT_OK;
 }
+
+kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind,
+                          const int* J_rowptr, const int* J_colind, const kkt_options* opt,
+                          bool device, kkt_ctx** out) {
+    if (!out) return set_err(nullptr, KKT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    kkt_ctx* c = nullptr;
+    TRY(new_ctx(opt, &c));
+    c->n = n;
+    c->m = m;
+    Graph g;
+    std::string e = build_graph(n, m, W_colptr, W_rowind, J_rowptr, J_colind, g);
+    if (!e.empty()) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
+    }
+    c->nnzW = W_colptr[n];
+    c->nnzJ = J_rowptr[m];
+    e = analyse(g, symbolic_options(c->opt), c->sym);
+    if (!e.empty()) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
+    }
+    c->nb = 1;
+    c->h_xoff = {0, n};
+    c->h_yoff = {0, m};
+    return finish_ctx(c, W_colptr, W_rowind, J_rowptr, J_colind, device, out);
+}
+
+// Batch: every instance analysed on its own (worker threads), the analyses
+// concatenated, the union's patterns built for the plan.
+kkt_status analyse_batch(int count, const int* n, const int* m, const int* const* W_colptr,
+                         const int* const* W_rowind, const int* const* J_rowptr,
+                         const int* const* J_colind, const kkt_options* opt, bool device,
+                         kkt_ctx** out) {
+    if (!out) return set_err(nullptr, KKT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !n || !m || !W_colptr || !W_rowind || !J_rowptr || !J_colind)
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse_batch: count < 1 or NULL array");
+    long long nt = 0, mt = 0, wt = 0, jt = 0;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || m[i] < 0 || !W_colptr[i] || !W_rowind[i] || !J_rowptr[i] || !J_colind[i])
+            return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse_batch: bad instance " + std::to_string(i));
+        nt += n[i];
+        mt += m[i];
+        wt += W_colptr[i][n[i]];
+        jt += J_rowptr[i][m[i]];
+    }
+    if (nt + mt > 0x7fffffffLL || wt > 0x7fffffffLL || jt > 0x7fffffffLL)
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse_batch: the union exceeds 32-bit indices");
+    kkt_ctx* c = nullptr;
+    TRY(new_ctx(opt, &c));
+    std::vector<Symbolic> parts(count);
+    std::vector<std::string> errs(count);
+    const SymbolicOptions so = symbolic_options(c->opt);
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int i = next++; i < count; i = next++) {
+            Graph g;
+            errs[i] = build_graph(n[i], m[i], W_colptr[i], W_rowind[i], J_rowptr[i], J_colind[i], g);
+            if (errs[i].empty()) errs[i] = analyse(g, so, parts[i]);
+        }
+    };
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nw = std::min(count, std::min(hw, 32));
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < count; ++i)
+        if (!errs[i].empty()) {
+            delete c;
+            return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse_batch: instance " + std::to_string(i) + ": " + errs[i]);
+        }
+    concat(parts, c->sym);
+    std::vector<Symbolic>().swap(parts);
+    c->n = (int)nt;
+    c->m = (int)mt;
+    c->nb = count;
+    c->h_xoff.assign(count + 1, 0);
+    c->h_yoff.assign(count + 1, 0);
+    std::vector<int> Wc(nt + 1, 0), Wr, Jr(mt + 1, 0), Jc;
+    Wr.reserve(wt);
+    Jc.reserve(jt);
+    for (int i = 0; i < count; ++i) {
+        const int x0 = c->h_xoff[i], y0 = c->h_yoff[i];
+        const int w0 = (int)Wr.size(), j0 = (int)Jc.size();
+        for (int k = 0; k < n[i]; ++k) Wc[x0 + k + 1] = w0 + W_colptr[i][k + 1];
+        for (int q = 0; q < W_colptr[i][n[i]]; ++q) Wr.push_back(W_rowind[i][q] + x0);
+        for (int r = 0; r < m[i]; ++r) Jr[y0 + r + 1] = j0 + J_rowptr[i][r + 1];
+        for (int q = 0; q < J_rowptr[i][m[i]]; ++q) Jc.push_back(J_colind[i][q] + x0);
+        c->h_xoff[i + 1] = x0 + n[i];
+        c->h_yoff[i + 1] = y0 + m[i];
+    }
+    c->nnzW = (int)wt;
+    c->nnzJ = (int)jt;
+    return finish_ctx(c, Wc.data(), Wr.data(), Jr.data(), Jc.data(), device, out);
+}
 }  // namespace
 
 kkt_status kkt_analyse(int n, int m, const int* W_colptr, const int* W_rowind, const int* J_rowptr,
@@ -953,6 +1132,38 @@ kkt_status kkt_analyse_host(int n, int m, const int* W_colptr, const int* W_rowi
                             const int* J_rowptr, const int* J_colind, const kkt_options* opt,
                             kkt_ctx** out) {
     return analyse_common(n, m, W_colptr, W_rowind, J_rowptr, J_colind, opt, false, out);
+}
+
+kkt_status kkt_analyse_batch(int count, const int* n, const int* m, const int* const* W_colptr,
+                             const int* const* W_rowind, const int* const* J_rowptr,
+                             const int* const* J_colind, const kkt_options* opt, kkt_ctx** out) {
+    return analyse_batch(count, n, m, W_colptr, W_rowind, J_rowptr, J_colind, opt, true, out);
+}
+
+kkt_status kkt_analyse_batch_host(int count, const int* n, const int* m, const int* const* W_colptr,
+                                  const int* const* W_rowind, const int* const* J_rowptr,
+                                  const int* const* J_colind, const kkt_options* opt, kkt_ctx** out) {
+    return analyse_batch(count, n, m, W_colptr, W_rowind, J_rowptr, J_colind, opt, false, out);
+}
+
+kkt_status kkt_batch_layout(const kkt_ctx* c, int* count, int* x_off, int* y_off) {
+    if (!c) return KKT_ERR_ARG;
+    if (count) *count = c->nb;
+    if (x_off) std::copy(c->h_xoff.begin(), c->h_xoff.end(), x_off);
+    if (y_off) std::copy(c->h_yoff.begin(), c->h_yoff.end(), y_off);
+    return KKT_OK;
+}
+
+kkt_status kkt_batch_results(const kkt_ctx* c, int* status, int* refine_iters, int* cg_iters,
+                             double* bwd_err, int* failed_col) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->device_ready) return KKT_ERR_STATE;
+    if (status) std::copy(c->r_status.begin(), c->r_status.end(), status);
+    if (refine_iters) std::copy(c->r_refine.begin(), c->r_refine.end(), refine_iters);
+    if (cg_iters) std::copy(c->r_cg.begin(), c->r_cg.end(), cg_iters);
+    if (bwd_err) std::copy(c->r_eta.begin(), c->r_eta.end(), bwd_err);
+    if (failed_col) std::copy(c->r_fail.begin(), c->r_fail.end(), failed_col);
+    return KKT_OK;
 }
 
 kkt_status kkt_symbolic_sizes(const kkt_ctx* c, int* ns, int64_t* nnz_L, int64_t* panel,
@@ -987,15 +1198,26 @@ kkt_status kkt_symbolic_export(const kkt_ctx* c, int* perm, int* parent, int* co
     return KKT_OK;
 }
 
-kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
-                      const double* d_D, double delta_x, cudaStream_t st, kkt_info* info) {
+// Numeric factorisation shared by kkt_factor (one delta_x) and
+// kkt_factor_batch (h_delta: one delta_x per instance, host).
+static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_Jval,
+                              const double* d_sigma, const double* d_D, double delta_x,
+                              const double* h_delta, cudaStream_t st, kkt_info* info) {
     if (!c) return KKT_ERR_ARG;
     if (!c->device_ready) return set_err(c, KKT_ERR_STATE, "context was analysed on the host only");
     if (!d_Wval && c->nnzW > 0) return set_err(c, KKT_ERR_ARG, "d_Wval is NULL");
     if (!d_Jval && c->nnzJ > 0) return set_err(c, KKT_ERR_ARG, "d_Jval is NULL");
     if (!d_sigma) return set_err(c, KKT_ERR_ARG, "d_sigma is NULL");
     if (c->opt.scheme == KKT_HYKKT && d_D) return set_err(c, KKT_ERR_ARG, "HyKKT takes D = gamma");
-    if (!(std::isfinite(delta_x) && delta_x >= 0)) return set_err(c, KKT_ERR_ARG, "bad delta_x");
+    const int nb = c->nb;
+    if (h_delta) {
+        for (int i = 0; i < nb; ++i)
+            if (!(std::isfinite(h_delta[i]) && h_delta[i] >= 0))
+                return set_err(c, KKT_ERR_ARG, "bad delta_x of instance " + std::to_string(i));
+        delta_x = 0.0;
+    } else if (!(std::isfinite(delta_x) && delta_x >= 0)) {
+        return set_err(c, KKT_ERR_ARG, "bad delta_x");
+    }
     c->factored = false;
     if (c->nnzW > 0)
         CUDA_TRY(c, cudaMemcpyAsync(c->v_W, d_Wval, (size_t)c->nnzW * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1011,6 +1233,19 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
     c->f_D = hasD ? c->v_D : nullptr;
     c->f_Dconst = c->opt.scheme == KKT_LIFTED ? 1.0 / c->opt.delta : c->opt.gamma;
     c->f_delta_x = delta_x;
+    c->f_dvec = nullptr;
+    if (h_delta) {
+        if (nb == 1) {
+            c->f_delta_x = delta_x = h_delta[0];
+        } else {
+            for (int i = 0; i < nb; ++i) c->h_delta[i] = h_delta[i];
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_dval, c->h_delta.data(), (size_t)nb * sizeof(double),
+                                        cudaMemcpyHostToDevice, st));
+            expand_kernel<<<c->nch_x, kThreads, 0, st>>>(c->d_ch_xy, c->d_dval, c->d_dvec);
+            c->f_dvec = c->d_dvec;
+        }
+    }
+    if (!c->f_dvec) std::fill(c->h_delta.begin(), c->h_delta.end(), c->f_delta_x);
     // dual block of the target system: C = 1/D (relaxed problem) or none
     c->f_C = nullptr;
     if (c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
@@ -1020,54 +1255,94 @@ kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, co
         }
         c->f_C = c->d_Cbuf.p;
     }
-    const int n = c->n, m = c->m;
+    const int m = c->m;
     const int sp_a = span_begin(c, 0, st);
     if (c->nnzJ > 0)
         scale_rows_sqrt_kernel<<<grid_for(c->nnzJ), kThreads, 0, st>>>(c->nnzJ, c->d_jrow, c->f_J, c->f_D,
                                                                        c->f_Dconst, c->v_Js);
     span_end(c, sp_a, st);
-    const int big = 0x7fffffff;
-    int fail = big;
+    auto fetch_fail = [&]() -> kkt_status {
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_int, c->d_fail, (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        return KKT_OK;
+    };
+    auto any_fail = [&]() {
+        for (int i = 0; i < nb; ++i)
+            if (c->h_int[i] != kNoFail) return true;
+        return false;
+    };
     int detail = 0;
     if (c->opt.precision == 1) {
         TRY(enqueue_numeric_factor<float>(c, c->d_Lx32, c->d_dinv32, delta_x, st));
-        CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(c, cudaStreamSynchronize(st));
+        TRY(fetch_fail());
         c->stats.fp32_factors++;
         c->cur_prec = 1;
         detail = 1;
-        if (fail != big) {            // FP32 pivot failed: factorise in FP64
+        if (any_fail()) {            // an FP32 pivot failed: factorise in FP64
             c->stats.fp64_fallbacks++;
             detail = 2;
-            fail = big;
         }
     }
     if (detail != 1) {
         TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, delta_x, st));
         c->cur_prec = 0;
     }
-    // ||K_orig||_inf
-    CUDA_TRY(c, cudaMemsetAsync(c->d_sc + SC_KNORM, 0, sizeof(double), st));
+    // ||K_orig,i||_inf
+    CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), st));
     if (c->f_C) {
         if (c->f_D) recip_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->f_D, c->d_Cbuf.p);
         else fill_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->opt.delta, c->d_Cbuf.p);
     }
-    knorm_kernel<<<grid_for((long long)n + m), kThreads, 0, st>>>(
-        n, m, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx,
-        c->f_J, c->f_sigma, delta_x, c->f_C, c->d_sc + SC_KNORM);
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc + SC_KNORM, sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (detail != 1) CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(c, cudaStreamSynchronize(st));
+    knorm_kernel<<<c->nch_xy, kThreads, 0, st>>>(c->d_ch_xy, c->n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx,
+                                                 c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx, c->f_J,
+                                                 c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C, c->d_knorm);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_red, c->d_knorm, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (detail == 1) {
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+    } else {
+        TRY(fetch_fail());   // synchronises
+    }
     spans_collect(c);
-    c->knorm = c->h_sc[0];
+    int first_fail = -1, nfail = 0;
+    for (int i = 0; i < nb; ++i) {
+        c->h_knorm[i] = c->h_red[i];
+        const int w = detail == 1 ? kNoFail : c->h_int[i];
+        c->r_fail[i] = w == kNoFail ? -1 : w;
+        c->r_status[i] = w == kNoFail ? KKT_OK : KKT_ERR_NOT_SPD;
+        if (w != kNoFail) {
+            ++nfail;
+            if (first_fail < 0) first_fail = w;
+        }
+    }
+    c->knorm = c->h_knorm[0];
     if (info) {
-        info->failed_col = fail == big ? -1 : fail;
-        info->delta_x = delta_x;
+        info->failed_col = first_fail;
+        info->delta_x = c->f_delta_x;
         info->status_detail = detail;
     }
-    if (fail != big) return set_err(c, KKT_ERR_NOT_SPD, "factorization: non-positive pivot in column " + std::to_string(fail));
+    if (nfail > 0) {
+        // a batch keeps the factors of its other instances usable
+        c->factored = nb > 1 && nfail < nb;
+        return set_err(c, KKT_ERR_NOT_SPD, "factorization: non-positive pivot in column " +
+                                               std::to_string(first_fail) +
+                                               (nb > 1 ? " (" + std::to_string(nfail) + " of " +
+                                                             std::to_string(nb) + " instances failed)"
+                                                       : std::string()));
+    }
     c->factored = true;
     return KKT_OK;
+}
+
+kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
+                      const double* d_D, double delta_x, cudaStream_t st, kkt_info* info) {
+    return factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, nullptr, st, info);
+}
+
+kkt_status kkt_factor_batch(kkt_ctx* c, const double* d_Wval, const double* d_Jval,
+                            const double* d_sigma, const double* d_D, const double* delta_x,
+                            cudaStream_t st, kkt_info* info) {
+    if (!delta_x) return set_err(c, KKT_ERR_ARG, "delta_x is NULL");
+    return factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, 0.0, delta_x, st, info);
 }
 
 kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
@@ -1075,67 +1350,98 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
     if (!c) return KKT_ERR_ARG;
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_solve called without a successful kkt_factor");
     if (!d_rx || !d_ry || !d_dx || !d_dy) return set_err(c, KKT_ERR_ARG, "NULL vector");
-    const int n = c->n, m = c->m;
+    const int n = c->n, m = c->m, nb = c->nb;
     double* rx = c->w_r;
     double* ry = c->w_r + n;
     double* dx = c->w_d;
     double* dy = c->w_d + n;
-    std::vector<double> etas;
-    int slow = 0, cg_total = 0, it = 0;
-    kkt_status result = KKT_ERR_MAXIT;
-    bool cg_failed = false;
+    // Richardson on every instance: an instance stops at eta <= tol_refine
+    // (KKT_OK), at two successive sweeps with eta > 0.9 eta_prev (STALL), or
+    // after max_refine sweeps (MAXIT); instances whose factor failed take no
+    // part (NOT_SPD).  Stopped instances keep their solution: the correction
+    // is added only where d_act is set.
+    constexpr int kRunning = 1;
+    std::vector<char> failed(nb);
+    for (int i = 0; i < nb; ++i) failed[i] = c->r_fail[i] >= 0;
+    std::vector<double> eta(nb, INFINITY), prev(nb, INFINITY);
+    std::vector<int> slow(nb, 0), state(nb, 0);
+    std::fill(c->r_cg.begin(), c->r_cg.end(), 0);
     int detail = c->cur_prec;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
         CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
         CUDA_TRY(c, cudaMemcpyAsync(rx, d_rx, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         CUDA_TRY(c, cudaMemcpyAsync(ry, d_ry, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        etas.clear();
-        slow = 0;
-        result = KKT_ERR_MAXIT;
-        cg_failed = false;
-        for (it = 0; it <= c->opt.max_refine; ++it) {
+        int running = 0;
+        for (int i = 0; i < nb; ++i) {
+            state[i] = failed[i] ? (int)KKT_ERR_NOT_SPD : kRunning;
+            slow[i] = 0;
+            prev[i] = INFINITY;
+            eta[i] = INFINITY;
+            c->r_refine[i] = 0;
+            c->h_act[i] = state[i] == kRunning;
+            running += c->h_act[i];
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_act, c->h_act, (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int it = 0; it <= c->opt.max_refine && running > 0; ++it) {
             if (c->opt.scheme == KKT_LIFTED) {
                 TRY(lifted_precond(c, rx, ry, dx, dy, st));
             } else {
-                int its = 0;
-                bool ok = true;
-                TRY(hykkt_inner(c, rx, ry, dx, dy, st, &its, &ok));
-                cg_total += its;
-                if (!ok) cg_failed = true;
+                TRY(hykkt_inner(c, rx, ry, dx, dy, st, c->r_cg));
             }
             c->stats.launches += 2;
-            axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, 1.0, dx, d_dx);
-            axpy_kernel<<<grid_for(m), kThreads, 0, st>>>(m, 1.0, dy, d_dy);
-            double eta = 0;
-            TRY(residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, st, &eta));
-            etas.push_back(eta);
-            if (eta <= c->opt.tol_refine) { result = KKT_OK; break; }
-            if (etas.size() >= 2 && eta > 0.9 * etas[etas.size() - 2]) {   // stagnation
-                if (++slow >= 2) { result = KKT_ERR_STALL; break; }
-            } else {
-                slow = 0;
+            seg_axpy_kernel<<<c->nch_xy, kThreads, 0, st>>>(c->d_ch_xy, n, c->d_act, dx, dy, d_dx, d_dy);
+            TRY(residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, st, eta));
+            running = 0;
+            for (int i = 0; i < nb; ++i) {
+                if (state[i] != kRunning) continue;
+                c->r_refine[i] = it;
+                if (eta[i] <= c->opt.tol_refine) {
+                    state[i] = KKT_OK;
+                } else if (it > 0 && eta[i] > 0.9 * prev[i]) {   // stagnation
+                    if (++slow[i] >= 2) state[i] = KKT_ERR_STALL;
+                } else {
+                    slow[i] = 0;
+                }
+                prev[i] = eta[i];
+                c->r_eta[i] = eta[i];
+                c->h_act[i] = state[i] == kRunning;
+                running += c->h_act[i];
             }
+            if (running > 0)
+                CUDA_TRY(c, cudaMemcpyAsync(c->d_act, c->h_act, (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, st));
         }
-        if (result == KKT_OK || c->cur_prec != 1) break;
+        bool all_ok = true;
+        for (int i = 0; i < nb; ++i) {
+            if (state[i] == kRunning) state[i] = KKT_ERR_MAXIT;
+            if (state[i] != KKT_OK && !failed[i]) all_ok = false;
+        }
+        if (all_ok || c->cur_prec != 1) break;
         // the FP32 factor did not carry the refinement to the tolerance:
         // factorise the same system in FP64 and solve again
-        const int big = 0x7fffffff;
-        int fail = big;
         TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, c->f_delta_x, st));
-        CUDA_TRY(c, cudaMemcpyAsync(&fail, c->d_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_int, c->d_fail, (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaStreamSynchronize(st));
         c->cur_prec = 0;
         c->stats.fp64_fallbacks++;
         detail = 2;
-        if (fail != big) {
+        int nfail = 0, first = -1;
+        for (int i = 0; i < nb; ++i) {
+            if (c->h_int[i] != kNoFail) {
+                failed[i] = 1;
+                c->r_fail[i] = c->h_int[i];
+                if (first < 0) first = c->h_int[i];
+            }
+            nfail += failed[i];
+        }
+        if (nfail == nb) {
             c->factored = false;
-            if (info) { info->failed_col = fail; info->status_detail = detail; }
+            for (int i = 0; i < nb; ++i) c->r_status[i] = KKT_ERR_NOT_SPD;
+            if (info) { info->failed_col = first; info->status_detail = detail; }
             return set_err(c, KKT_ERR_NOT_SPD, "FP64 refactorization after FP32 fallback: non-positive pivot in column " +
-                                                   std::to_string(fail));
+                                                   std::to_string(first));
         }
     }
-    if (it > c->opt.max_refine) it = c->opt.max_refine;
     if (d_ds && c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
         j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, d_dx, d_ry,
                                                          nullptr, 1.0, d_ds, nullptr);
@@ -1143,15 +1449,31 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
     spans_collect(c);
+    kkt_status result = KKT_OK;
+    int refine_max = 0, cg_total = 0;
+    double eta_max = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        c->r_status[i] = state[i];
+        cg_total += c->r_cg[i];
+        if (failed[i]) {
+            c->r_eta[i] = INFINITY;
+            result = KKT_ERR_NOT_SPD;
+            continue;
+        }
+        refine_max = std::max(refine_max, c->r_refine[i]);
+        eta_max = std::max(eta_max, c->r_eta[i]);
+        if (state[i] != KKT_OK && result == KKT_OK) result = (kkt_status)state[i];
+    }
     if (info) {
-        info->refine_iters = it;
+        info->refine_iters = refine_max;
         info->cg_iters = cg_total;
-        info->bwd_err = etas.empty() ? INFINITY : etas.back();
+        info->bwd_err = eta_max;
         info->status_detail = detail;
     }
-    if (result == KKT_OK && cg_failed) result = KKT_OK;   // refinement reached the tolerance anyway
     if (result != KKT_OK)
-        set_err(c, result, result == KKT_ERR_STALL ? "refinement stalled" : "refinement hit max_refine");
+        set_err(c, result, result == KKT_ERR_STALL ? "refinement stalled"
+                           : result == KKT_ERR_MAXIT ? "refinement hit max_refine"
+                                                     : "some instances have no factor (non-positive pivot)");
     return result;
 }
 
@@ -1283,7 +1605,9 @@ void kkt_destroy(kkt_ctx* c) {
     if (c->h_cg) cudaFreeHost(c->h_cg);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
-    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->h_act) cudaFreeHost(c->h_act);
+    if (c->h_int) cudaFreeHost(c->h_int);
     delete c;
 }
 

@@ -589,4 +589,49 @@ std::string analyse(const Graph& g, const SymbolicOptions& opt, Symbolic& out) {
     return "";
 }
 
+void concat(const std::vector<Symbolic>& parts, Symbolic& out) {
+    out = Symbolic();
+    int64_t n = 0, ns = 0, nrows = 0;
+    bool masks = true;
+    for (const Symbolic& p : parts) {
+        n += p.n;
+        ns += p.ns();
+        nrows += (int64_t)p.sn_rows.size();
+        masks = masks && p.sn_rowmask.size() == p.sn_rows.size();
+    }
+    out.n = (int)n;
+    out.perm.reserve(n);
+    out.iperm.reserve(n);
+    out.parent.reserve(n);
+    out.colcount.reserve(n);
+    out.sn_ptr.reserve(ns + 1);
+    out.sn_rowptr.reserve(ns + 1);
+    out.sn_rows.reserve(nrows);
+    out.sn_parent.reserve(ns);
+    if (masks) out.sn_rowmask.reserve(nrows);
+    out.sn_ptr.push_back(0);
+    out.sn_rowptr.push_back(0);
+    int col0 = 0, sn0 = 0, row0 = 0;
+    for (const Symbolic& p : parts) {
+        for (int k = 0; k < p.n; ++k) {
+            out.perm.push_back(p.perm[k] + col0);
+            out.iperm.push_back(p.iperm[k] + col0);
+            out.parent.push_back(p.parent[k] < 0 ? -1 : p.parent[k] + col0);
+            out.colcount.push_back(p.colcount[k]);
+        }
+        for (int s = 0; s < p.ns(); ++s) {
+            out.sn_ptr.push_back(p.sn_ptr[s + 1] + col0);
+            out.sn_rowptr.push_back(p.sn_rowptr[s + 1] + row0);
+            out.sn_parent.push_back(p.sn_parent[s] < 0 ? -1 : p.sn_parent[s] + sn0);
+        }
+        for (int r : p.sn_rows) out.sn_rows.push_back(r + col0);
+        if (masks) out.sn_rowmask.insert(out.sn_rowmask.end(), p.sn_rowmask.begin(), p.sn_rowmask.end());
+        out.flops += p.flops;
+        out.nnz_L += p.nnz_L;
+        col0 += p.n;
+        sn0 += p.ns();
+        row0 += (int)p.sn_rows.size();
+    }
+}
+
 }  // namespace kktgb

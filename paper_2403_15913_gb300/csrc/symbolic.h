@@ -51,4 +51,13 @@ std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
                         const int* J_rowptr, const int* J_colind, Graph& g);
 std::string analyse(const Graph& g, const SymbolicOptions& opt, Symbolic& out);
 
+// Analysis of a block-diagonal union from the analyses of its blocks, in
+// block order: labels, supernodes and row lists are offset and appended.
+// Equal to analysing the union's pattern, because the ordering takes
+// connected components in the order of their smallest vertex and every later
+// step (elimination tree, postorder with roots in increasing order, column
+// counts, supernodes, relaxation along tree edges, row lists) is local to
+// the elimination tree of one block.
+void concat(const std::vector<Symbolic>& parts, Symbolic& out);
+
 }  // namespace kktgb

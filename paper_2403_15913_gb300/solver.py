@@ -163,3 +163,69 @@ class KKTSolver:
             self.close()
         except Exception:
             pass
+
+
+class KKTBatchSolver(KKTSolver):
+    """A batch of independent systems of uneven sizes, factorised and solved
+    together (``kkt_analyse_batch``).  ``instances`` is a sequence of
+    (n, m, W_colptr, W_rowind, J_rowptr, J_colind); value arrays and vectors
+    are the instances' arrays concatenated in order (see ``layout``)."""
+
+    def __init__(self, instances, host_only=False, **options):
+        inst = [tuple(x) for x in instances]
+        self.count = len(inst)
+        ns = np.array([int(x[0]) for x in inst], np.int32)
+        ms = np.array([int(x[1]) for x in inst], np.int32)
+        self.n, self.m = int(ns.sum()), int(ms.sum())
+        self._keep = [[_i32(a) for a in x[2:6]] for x in inst]
+        ptrs = [(nat.I32P * self.count)(*[nat.ptr_i32(k[j]) for k in self._keep]) for j in range(4)]
+        self._keep_ptrs = (ns, ms, ptrs)
+        self.options = default_options(**options)
+        L = nat.lib()
+        ctx = ctypes.c_void_p()
+        fn = L.kkt_analyse_batch_host if host_only else L.kkt_analyse_batch
+        st = fn(self.count, nat.ptr_i32(ns), nat.ptr_i32(ms), *ptrs, ctypes.byref(self.options),
+                ctypes.byref(ctx))
+        if st != nat.KKT_OK:
+            raise KKTError(st, L.kkt_last_error(None).decode())
+        self._ctx = ctx
+        self.info = nat.Info()
+
+    def layout(self):
+        """(x_off, y_off): instance i owns variables x_off[i]:x_off[i+1] and
+        constraints y_off[i]:y_off[i+1] of the concatenated vectors."""
+        xo = np.empty(self.count + 1, np.int32)
+        yo = np.empty(self.count + 1, np.int32)
+        self._check(nat.lib().kkt_batch_layout(self._ctx, None, nat.ptr_i32(xo), nat.ptr_i32(yo)))
+        return xo, yo
+
+    def factor_batch(self, Wval, Jval, sigma, D=None, delta_x=None, stream=None):
+        """Refactorise with one delta_x per instance (default 0).  Returns
+        the status (KKT_ERR_NOT_SPD when some instance failed; see results)."""
+        d = np.zeros(self.count) if delta_x is None else np.ascontiguousarray(delta_x, np.float64)
+        st = nat.lib().kkt_factor_batch(self._ctx, _dptr(Wval), _dptr(Jval), _dptr(sigma), _dptr(D),
+                                        nat.ptr_f64(d), _stream(stream), ctypes.byref(self.info))
+        if st not in (nat.KKT_OK, nat.KKT_ERR_NOT_SPD):
+            self._check(st)
+        return st
+
+    def solve(self, rx, ry, dx, dy, ds=None, stream=None):
+        """Solve every instance that has a factor.  Returns the status
+        (KKT_ERR_NOT_SPD when some instances have none; see results)."""
+        st = nat.lib().kkt_solve(self._ctx, _dptr(rx), _dptr(ry), _dptr(dx), _dptr(dy), _dptr(ds),
+                                 _stream(stream), ctypes.byref(self.info))
+        if st not in (nat.KKT_OK, nat.KKT_ERR_MAXIT, nat.KKT_ERR_STALL, nat.KKT_ERR_NOT_SPD):
+            self._check(st)
+        return st
+
+    def results(self):
+        """Per-instance status, refinement sweeps, CG iterations, backward
+        error and first failing column of the last factor / solve."""
+        out = dict(status=np.empty(self.count, np.int32), refine_iters=np.empty(self.count, np.int32),
+                   cg_iters=np.empty(self.count, np.int32), bwd_err=np.empty(self.count),
+                   failed_col=np.empty(self.count, np.int32))
+        self._check(nat.lib().kkt_batch_results(
+            self._ctx, nat.ptr_i32(out["status"]), nat.ptr_i32(out["refine_iters"]),
+            nat.ptr_i32(out["cg_iters"]), nat.ptr_f64(out["bwd_err"]), nat.ptr_i32(out["failed_col"])))
+        return out
+

@@ -52,8 +52,14 @@ def parse():
     ap.add_argument("--gamma", type=float, default=1e4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
-    ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt", "batch"])
+    ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt", "batch", "serve"])
+    ap.add_argument("--clients", type=int, default=64, help="serve workload: controllers")
+    ap.add_argument("--requests", type=int, default=400, help="serve workload: timed requests")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrivals per s")
+    ap.add_argument("--slots", type=int, default=8, help="serve workload: concurrent solves")
     ap.add_argument("--batch", type=int, default=256, help="batch workload: instances")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch workload: pick the supernode partition with kkt_autotune_batch first")
     ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -569,7 +575,7 @@ def run_batch(args, ws, rank, local):
     import numpy as np
     import torch
     from gen.tray import TrayParams, kkt_point
-    from paper_2403_15913_gb300 import KKTBatchSolver, KKTSolver, TrayModel
+    from paper_2403_15913_gb300 import KKTBatchSolver, KKTSolver, TrayModel, autotune_batch
 
     torch.cuda.set_device(local)
     dist = None
@@ -586,6 +592,14 @@ def run_batch(args, ws, rank, local):
     opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
                 relax_zeros=128, max_width=64)
     prec = 1 if args.precision == "fp32" else 0
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        opts, tune_ms = autotune_batch([(p.n, p.m, *pt) for p, pt in zip(params, pats)], sample=32,
+                                       precision=prec, **opts)
+        opts.pop("precision", None)
+        tuned = {"sample_factor_ms": tune_ms, "seconds": round(time.perf_counter() - t0, 2),
+                 **{k: opts[k] for k in ("relax_cols", "relax_zeros", "max_width", "subtree_cols")}}
     t0 = time.perf_counter()
     bs = KKTBatchSolver([(p.n, p.m, *pt) for p, pt in zip(params, pats)], precision=prec, **opts)
     t_analyse = time.perf_counter() - t0
@@ -722,6 +736,7 @@ def run_batch(args, ws, rank, local):
                                f"total), one {args.scheme} factor + refined solve of the whole batch per "
                                f"step, Sigma log-uniform on [{sig[0]:g}, {sig[1]:g}]",
                    "scheme": args.scheme, "precision": args.precision, "instances": args.batch,
+                   "autotuned": tuned,
                    "l2": "flushed (256 MB write) between timed steps",
                    "analyse_s": round(t_analyse, 3), "factor_gflop": sym.flops / 1e9,
                    "factor_ms": factor_ms, "kinv_ms": st["solve_ms"] / max(1, st["kinv_calls"]),
@@ -746,6 +761,112 @@ def run_batch(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- NMPC serving
+SERVE_METRIC = "NMPC serving solves/s (full IPM solves, Poisson arrivals)"
+
+
+def run_serve(args, ws, rank, local):
+    """Open-loop Poisson stream of receding-horizon requests against the
+    native server; the same stream against one slot (serial FP64)."""
+    import numpy as np
+    import torch
+    from gen.tray import TrayParams
+    from paper_2403_15913_gb300 import NMPCServer
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rng = np.random.default_rng(args.seed + 7919 * rank)
+    params = [TrayParams(k=int(rng.choice([32, 64])), T=int(rng.integers(50, 2001)))
+              for _ in range(args.clients)]
+    gaps = rng.exponential(1.0 / args.rate, args.requests)
+    who = rng.integers(0, args.clients, args.requests)
+
+    def serve(slots, precision, rate=None, count=None):
+        gaps_, who_ = gaps, who
+        if rate is not None:
+            r2 = np.random.default_rng(args.seed + 31)
+            gaps_ = r2.exponential(1.0 / rate, count)
+            who_ = r2.integers(0, args.clients, count)
+        srv = NMPCServer(slots=slots, hbm_budget_gb=40.0, scheme=args.scheme, precision=precision,
+                         gamma=args.gamma)
+        cl = [srv.add_client(p.as_array()) for p in params]
+        t0 = time.perf_counter()
+        for t in [srv.submit(c) for c in cl]:        # contexts created, first solves (untimed)
+            srv.wait(t)
+        prewarm = time.perf_counter() - t0
+        clocks = ClockSampler(local)
+        clocks.start()
+        start = time.perf_counter()
+        tickets, due = [], start
+        for g, c in zip(gaps_, who_):
+            due += g
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(cl[c]))
+        res = [srv.wait(t) for t in tickets]
+        clk = clocks.stop()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+        span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) * 1e-3
+        return {"solves_per_s": len(res) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "iters_mean": float(np.mean([r["iters"] for r in res])),
+                "converged": int(sum(r["status"] == 1 for r in res)),
+                "warm": int(sum(r["warm"] for r in res)), "prewarm_s": round(prewarm, 2),
+                "contexts": st["contexts_created"], "evictions": st["evictions"],
+                "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "clocks": clk}
+
+    prec = 1 if args.precision == "fp32" else 0
+    conc = serve(args.slots, prec)
+    serial = serve(1, 0)
+    # service latency below saturation: the same server at 70% of the
+    # throughput it just sustained
+    light_rate = 0.7 * conc["solves_per_s"]
+    light = serve(args.slots, prec, rate=light_rate, count=min(args.requests, 200))
+    light.pop("clocks")
+    light["rate_per_s"] = light_rate
+    if dist:
+        t = torch.tensor([conc["solves_per_s"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        total = t.item()
+    else:
+        total = conc["solves_per_s"]
+    if rank == 0:
+        clk = conc.pop("clocks")
+        serial.pop("clocks")
+        n_total = sum(p.n for p in params)
+        line = {
+            "metric": SERVE_METRIC, "value": total, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.requests, "warmup": args.clients, "ms_per_step": conc["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 factor + f64 refinement" if prec else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.clients} NMPC clients (trays in {{32,64}}, T uniform in [50,2000], "
+                                   f"n = {n_total} in total), {args.requests} requests with Poisson arrivals at "
+                                   f"{args.rate:g}/s, each a full {args.scheme} IPM solve to 1e-8 warm-started "
+                                   f"from the shifted previous solution, 40 GB admission budget",
+                       "slots": args.slots, "concurrent": conc, "serial_fp64_one_slot": serial,
+                       "at_70pct_of_capacity": light,
+                       "speedup_vs_serial": conc["solves_per_s"] / serial["solves_per_s"],
+                       "step": "one request = one full IPM solve; value = requests / (last done - first "
+                               "submit); latency = done - submit (queueing included)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "e2e": {"value": total, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0,
+                    "scope": "host submit -> device solve -> host result per request (state from the "
+                             "previous solution on the device)"},
+            "gpu_launches": None,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -755,6 +876,8 @@ def main():
         run_kkt(args, ws, rank, local)
     elif args.workload == "batch":
         run_batch(args, ws, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

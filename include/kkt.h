@@ -220,6 +220,20 @@ kkt_status kkt_factor_batch(kkt_ctx* ctx, const double* d_Wval, const double* d_
                             const double* d_sigma, const double* d_D, const double* delta_x,
                             cudaStream_t stream, kkt_info* info);
 
+/* Autotuner of the supernode partition (the panel shapes the factor
+ * kernels work on) for a batch, on this GPU: up to `sample` instances
+ * (evenly spaced; <= 0 means 32) are analysed with each candidate setting of
+ * relax_cols, relax_zeros, max_width and subtree_cols, and the numeric
+ * factorisation of synthetic SPD values (K = I + J^T J) is timed with CUDA
+ * events on `stream`; *best = *base (defaults if NULL) with the fastest
+ * candidate's four fields, *best_ms (may be NULL) its median time.  The
+ * paper has no counterpart (its factorisation is a vendor library's). */
+kkt_status kkt_autotune_batch(int count, const int* n, const int* m,
+                              const int* const* W_colptr, const int* const* W_rowind,
+                              const int* const* J_rowptr, const int* const* J_colind,
+                              const kkt_options* base, int sample, cudaStream_t stream,
+                              kkt_options* best, double* best_ms);
+
 /* Per-instance results of the last kkt_factor / kkt_solve (host arrays of
  * count entries, any may be NULL): status (KKT_OK, KKT_ERR_STALL,
  * KKT_ERR_MAXIT, KKT_ERR_NOT_SPD), refinement sweeps, CG iterations,
@@ -385,6 +399,105 @@ kkt_status kkt_ipm_get(const kkt_ipm* ipm, double* d_x, double* d_y, double* d_z
 kkt_ctx* kkt_ipm_kkt(kkt_ipm* ipm);
 
 void kkt_ipm_destroy(kkt_ipm* ipm);
+
+/* Receding-horizon use (Sec. V-B: the symbolic factor is kept across
+ * solves).  Pins the stage-0 compositions to x0[k] (host; one value per
+ * tray) in the initial-condition rows, instead of xbar_0 on every tray;
+ * NULL restores xbar_0.  Takes effect at the next kkt_ipm_init. */
+kkt_status kkt_ipm_set_initial_state(kkt_ipm* ipm, const double* x0, cudaStream_t stream);
+
+/* kkt_ipm_init from a previous solution d_prev[n] shifted by one stage
+ * (stage t takes stage t+1's values, the last stage keeps its own): the
+ * warm start of the next receding-horizon solve. */
+kkt_status kkt_ipm_init_shifted(kkt_ipm* ipm, const double* d_prev, cudaStream_t stream);
+
+/* Warm start of the next receding-horizon solve from the driver's own last
+ * iterate: primal variables, constraint multipliers and bound multipliers
+ * (and, relaxed, slacks and their multipliers) shifted by one stage in
+ * place, the primal pushed inside its bounds, barrier parameter mu, empty
+ * filter; recenter = 1 resets the bound multipliers to mu / slack (the
+ * products start on the central path).  KKT_ERR_STATE before any
+ * kkt_ipm_init. */
+kkt_status kkt_ipm_init_warm(kkt_ipm* ipm, double mu, int recenter, cudaStream_t stream);
+
+/* Device memory held by the driver and its KKT context, in bytes. */
+kkt_status kkt_ipm_device_bytes(const kkt_ipm* ipm, int64_t* bytes);
+
+/* Device memory held by a KKT context, in bytes. */
+kkt_status kkt_device_bytes(const kkt_ctx* ctx, int64_t* bytes);
+
+/* ------------------------------------------------------------------------
+ * NMPC serving (no counterpart in the paper, whose use case it serves: a
+ * controller re-solves its horizon-T problem from each new state, reusing
+ * the symbolic factorisation, Sec. V-B).  A server holds clients (one
+ * column model each, fixed k and T) and runs their requests -- full IPM
+ * solves -- on `slots` worker threads, each with its own CUDA stream, so
+ * solves of different clients overlap on the device; a client's requests
+ * run in submission order.  A client's context (symbolic analysis, factor
+ * storage, IPM buffers, last solution) stays resident between requests
+ * while it fits in hbm_budget_gb (least recently used idle contexts are
+ * evicted to admit others); a request starts from the client's previous
+ * solution shifted one stage (warm_start = 1), with the stage-0 state
+ * given or, if omitted, taken from stage 1 of the previous solution.
+ * ---------------------------------------------------------------------- */
+typedef struct kkt_server kkt_server;
+
+typedef struct {
+    int slots;              /* concurrent solves (8)                              */
+    double hbm_budget_gb;   /* device memory of resident contexts (40)            */
+    int scheme;             /* KKT_LIFTED (default) or KKT_HYKKT                  */
+    int precision;          /* kkt_options.precision (0)                          */
+    double gamma;           /* HyKKT gamma (1e7)                                  */
+    double tol;             /* IPM tolerance (1e-8)                               */
+    int max_iter;           /* IPM iterations (200)                               */
+    double mu_init;         /* initial barrier parameter (0.1)                    */
+    int warm_start;         /* 1: start from the shifted previous iterate (1)     */
+    double warm_mu;         /* barrier parameter of warm starts (1e-4)            */
+    int warm_recenter;      /* 1: warm starts recentre the bound multipliers (1)  */
+} kkt_server_options;
+
+typedef struct {
+    int64_t id;
+    int client, slot;
+    int status;             /* KKT_CONVERGED, KKT_ERR_MAXIT or an error          */
+    int iters;
+    int cold;               /* 1: the client's context was created for it        */
+    int warm;               /* 1: warm-started from the previous solution        */
+    double objective, inf_pr, inf_du;
+    double t_submit_ms, t_start_ms, t_done_ms;   /* since kkt_server_create      */
+} kkt_request_result;
+
+typedef struct {
+    int64_t completed, failed, contexts_created, evictions;
+    int64_t resident_bytes, peak_resident_bytes, queued;
+    int resident_clients;
+} kkt_server_stats;
+
+void kkt_server_default_options(kkt_server_options* opt);
+
+/* Starts the worker threads on CUDA device `device`. */
+kkt_status kkt_server_create(const kkt_server_options* opt, int device, kkt_server** out);
+
+/* Registers a client with its 16 model parameters (as kkt_tray_sizes). */
+kkt_status kkt_server_add_client(kkt_server* srv, const double* params, int* client);
+
+/* Queues a solve for `client`; x0[k] (host) is the measured state, NULL takes
+ * it from the previous solution (or xbar_0 for the first request);
+ * keep_solution = 1 keeps x for kkt_server_wait. */
+kkt_status kkt_server_submit(kkt_server* srv, int client, const double* x0, int keep_solution,
+                             int64_t* id);
+
+/* Blocks until request `id` is done; copies its result and, if it was kept,
+ * its solution x[n] into h_x (may be NULL). */
+kkt_status kkt_server_wait(kkt_server* srv, int64_t id, kkt_request_result* out, double* h_x);
+
+/* Blocks until every queued request is done. */
+kkt_status kkt_server_drain(kkt_server* srv);
+
+kkt_status kkt_server_get_stats(kkt_server* srv, kkt_server_stats* stats);
+
+/* Finishes the running solves, stops the workers, frees every context. */
+void kkt_server_destroy(kkt_server* srv);
 
 #ifdef __cplusplus
 }

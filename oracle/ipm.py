@@ -379,10 +379,11 @@ class IPM:
 class TrayModel:
     """The column model of ``oracle.tray`` behind the IPM interface."""
 
-    def __init__(self, p):
+    def __init__(self, p, x0=None):
         from gen.tray import bounds
         from oracle import tray
         self.p, self.t = p, tray
+        self.x0 = None if x0 is None else np.asarray(x0, dtype=float)   # per-tray initial state
         self.n, self.m = p.n, p.m
         self.x_lo, self.x_hi = bounds(p)
 
@@ -393,7 +394,7 @@ class TrayModel:
         return self.t.objective_grad(self.p, x)
 
     def cons(self, x):
-        return self.t.constraints(self.p, x)
+        return self.t.constraints(self.p, x, self.x0)
 
     def jac_csr(self, x):
         return self.t.jacobian_csr(self.p, x)

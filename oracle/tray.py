@@ -147,13 +147,15 @@ def objective_grad(p: TrayParams, w):
     return g
 
 
-def constraints(p: TrayParams, w):
+def constraints(p: TrayParams, w, x0=None):
     """c(w), length m: initial condition / dynamics rows then equilibrium
-    rows, stage by stage."""
+    rows, stage by stage.  The initial condition pins the stage-0
+    compositions to x0 (one value per tray; default x0bar on every tray):
+    in receding-horizon use x0 is the measured state of the column."""
     x, y, u = split(p, w)
     c = np.zeros(p.m, dtype=w.dtype)
     cb = c.reshape(p.T + 1, 2 * p.k)
-    cb[0, :p.k] = x[0] - p.x0bar
+    cb[0, :p.k] = x[0] - (p.x0bar if x0 is None else np.asarray(x0, dtype=float))
     g = balance(p, x[1:], y[1:], u[1:])
     cb[1:, :p.k] = x[1:] - x[:-1] - (p.h / p.M) * g
     cb[:, p.k:] = y - vle(p, x)

@@ -31,12 +31,15 @@ EXPORTED = [
     "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
     "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_backsolve_noalloc",
     "kkt_factor_export", "kkt_analyse_batch", "kkt_analyse_batch_host", "kkt_batch_layout",
-    "kkt_factor_batch", "kkt_batch_results",
+    "kkt_factor_batch", "kkt_batch_results", "kkt_autotune_batch",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
     "kkt_ipm_default_options", "kkt_ipm_create", "kkt_ipm_init", "kkt_ipm_step", "kkt_ipm_solve",
     "kkt_ipm_get",
-    "kkt_ipm_kkt", "kkt_ipm_destroy",
+    "kkt_ipm_kkt", "kkt_ipm_destroy", "kkt_ipm_set_initial_state", "kkt_ipm_init_shifted", "kkt_ipm_init_warm",
+    "kkt_ipm_device_bytes", "kkt_device_bytes",
+    "kkt_server_default_options", "kkt_server_create", "kkt_server_add_client", "kkt_server_submit",
+    "kkt_server_wait", "kkt_server_drain", "kkt_server_get_stats", "kkt_server_destroy",
 ]
 
 
@@ -90,6 +93,34 @@ class IPMInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget_gb", ctypes.c_double), ("scheme", ctypes.c_int),
+                ("precision", ctypes.c_int), ("gamma", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double), ("warm_start", ctypes.c_int),
+                ("warm_mu", ctypes.c_double), ("warm_recenter", ctypes.c_int)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("client", ctypes.c_int), ("slot", ctypes.c_int),
+                ("status", ctypes.c_int), ("iters", ctypes.c_int), ("cold", ctypes.c_int),
+                ("warm", ctypes.c_int), ("objective", ctypes.c_double), ("inf_pr", ctypes.c_double),
+                ("inf_du", ctypes.c_double), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("contexts_created", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_int64), ("peak_resident_bytes", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("resident_clients", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 P = ctypes.c_void_p
@@ -125,6 +156,10 @@ def lib():
     L.kkt_batch_layout.restype = ctypes.c_int
     L.kkt_factor_batch.argtypes = [P, P, P, P, P, F64P, P, ctypes.POINTER(Info)]
     L.kkt_factor_batch.restype = ctypes.c_int
+    L.kkt_autotune_batch.argtypes = [ctypes.c_int, I32P, I32P, I32PP, I32PP, I32PP, I32PP,
+                                     ctypes.POINTER(Options), ctypes.c_int, P, ctypes.POINTER(Options),
+                                     F64P]
+    L.kkt_autotune_batch.restype = ctypes.c_int
     L.kkt_batch_results.argtypes = [P, I32P, I32P, I32P, F64P, I32P]
     L.kkt_batch_results.restype = ctypes.c_int
     L.kkt_symbolic_sizes.argtypes = [P, I32P, I64P, I64P, I64P, I32P, F64P]
@@ -174,6 +209,32 @@ def lib():
     L.kkt_ipm_kkt.restype = P
     L.kkt_ipm_destroy.argtypes = [P]
     L.kkt_ipm_destroy.restype = None
+    L.kkt_ipm_set_initial_state.argtypes = [P, F64P, P]
+    L.kkt_ipm_set_initial_state.restype = ctypes.c_int
+    L.kkt_ipm_init_shifted.argtypes = [P, P, P]
+    L.kkt_ipm_init_shifted.restype = ctypes.c_int
+    L.kkt_ipm_init_warm.argtypes = [P, ctypes.c_double, ctypes.c_int, P]
+    L.kkt_ipm_init_warm.restype = ctypes.c_int
+    L.kkt_ipm_device_bytes.argtypes = [P, I64P]
+    L.kkt_ipm_device_bytes.restype = ctypes.c_int
+    L.kkt_device_bytes.argtypes = [P, I64P]
+    L.kkt_device_bytes.restype = ctypes.c_int
+    L.kkt_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
+    L.kkt_server_default_options.restype = None
+    L.kkt_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.c_int, ctypes.POINTER(P)]
+    L.kkt_server_create.restype = ctypes.c_int
+    L.kkt_server_add_client.argtypes = [P, F64P, I32P]
+    L.kkt_server_add_client.restype = ctypes.c_int
+    L.kkt_server_submit.argtypes = [P, ctypes.c_int, F64P, ctypes.c_int, I64P]
+    L.kkt_server_submit.restype = ctypes.c_int
+    L.kkt_server_wait.argtypes = [P, ctypes.c_int64, ctypes.POINTER(RequestResult), F64P]
+    L.kkt_server_wait.restype = ctypes.c_int
+    L.kkt_server_drain.argtypes = [P]
+    L.kkt_server_drain.restype = ctypes.c_int
+    L.kkt_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    L.kkt_server_get_stats.restype = ctypes.c_int
+    L.kkt_server_destroy.argtypes = [P]
+    L.kkt_server_destroy.restype = None
     _lib = L
     return L
 

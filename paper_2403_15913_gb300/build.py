@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libkkt_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kkt.cu", "tray.cu", "ipm.cu", "symbolic.cpp"]
+SOURCES = ["kkt.cu", "tray.cu", "ipm.cu", "serve.cu", "symbolic.cpp"]
 
 
 def _nvcc():

@@ -333,6 +333,9 @@ struct kkt_ipm {
     int* ops;
     int *jt_cp, *jt_ri, *jt_idx;
     double* h_red = nullptr;   // pinned
+    double* x0v = nullptr;     // per-tray initial state (device, k), NULL: x0bar
+    double* x0buf = nullptr;
+    long long dev_bytes = 0;   // device memory of this driver (the KKT context's excluded)
     // host state
     double mu = 0.1, theta_max = 0, theta_min = 0, delta_last = 0;
     std::vector<std::pair<double, double>> filter;
@@ -360,6 +363,7 @@ template <class T>
 kkt_status dalloc(kkt_ipm* p, T** out, size_t count) {
     ICUDA(p, cudaMalloc((void**)out, std::max<size_t>(1, count) * sizeof(T)));
     p->allocs.push_back(*out);
+    p->dev_bytes += (long long)(std::max<size_t>(1, count) * sizeof(T));
     return KKT_OK;
 }
 
@@ -534,12 +538,12 @@ kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
     fill_kernel<<<grid(n), kT, 0, st>>>(n, 1.0, p->zl);
     fill_kernel<<<grid(n), kT, 0, st>>>(n, 1.0, p->zu);
     if (p->opt.relaxed) {
-        ITRY(kkt_tray_eval(p->params, p->x, nullptr, 1.0, nullptr, nullptr, p->s, nullptr, nullptr, st));
+        ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, nullptr, 1.0, nullptr, nullptr, p->s, nullptr, nullptr, st));
         push_kernel<<<grid(m), kT, 0, st>>>(m, nullptr, nullptr, -p->opt.tau_relax, p->opt.tau_relax, p->s);
         fill_kernel<<<grid(m), kT, 0, st>>>(m, 1.0, p->vl);
         fill_kernel<<<grid(m), kT, 0, st>>>(m, 1.0, p->vu);
     }
-    ITRY(kkt_tray_eval(p->params, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
+    ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
     double th = 0, ls = 0;
     ITRY(measures(p, p->x, p->s, p->c, st, &th, &ls));
     p->theta_max = 1e4 * std::max(1.0, th);
@@ -563,7 +567,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     inf.iter = p->it;
     cudaEventRecord(p->ev[0], st);
     // 1. derivatives
-    ITRY(kkt_tray_eval(p->params, p->x, p->y, 1.0, nullptr, p->grad, p->c, p->Jv, p->Wv, st));
+    ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, p->y, 1.0, nullptr, p->grad, p->c, p->Jv, p->Wv, st));
     jt_kernel<<<grid(n), kT, 0, st>>>(n, p->jt_cp, p->jt_ri, p->jt_idx, p->Jv, p->y, p->jty);
     cudaEventRecord(p->ev[1], st);
     // 2. optimality error and barrier update
@@ -639,7 +643,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     for (ls = 1; ls <= kMaxLs; ++ls) {
         trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, alpha, p->x, p->dx, p->s, p->ds,
                                                           p->xt, p->st);
-        ITRY(kkt_tray_eval(p->params, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
+        ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
         double tht = 0, lst = 0, ft = 0;
         ITRY(measures(p, p->xt, p->st, p->ct, st, &tht, &lst));
         ITRY(objective(p, p->xt, st, &ft));
@@ -703,6 +707,103 @@ kkt_status kkt_ipm_solve(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     }
     if (info) *info = last;
     return ierr(p, KKT_ERR_MAXIT, "kkt_ipm_solve: max_iter reached");
+}
+
+// stage t of the new start takes stage t + 1 of the previous solution; the
+// last stage keeps its own values
+__global__ void shift_stages_kernel(int n, int nst, const double* __restrict__ prev, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = i + nst < n ? prev[i + nst] : prev[i];
+}
+
+kkt_status kkt_ipm_set_initial_state(kkt_ipm* p, const double* x0, cudaStream_t st) {
+    if (!p) return KKT_ERR_ARG;
+    const int k = (int)p->params[0];
+    if (!x0) {
+        p->x0v = nullptr;
+        return KKT_OK;
+    }
+    for (int i = 0; i < k; ++i)
+        if (!std::isfinite(x0[i])) return ierr(p, KKT_ERR_ARG, "initial state is not finite");
+    if (!p->x0buf) ITRY(dalloc(p, &p->x0buf, k));
+    ICUDA(p, cudaMemcpyAsync(p->x0buf, x0, k * sizeof(double), cudaMemcpyHostToDevice, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    p->x0v = p->x0buf;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_init_shifted(kkt_ipm* p, const double* d_prev, cudaStream_t st) {
+    if (!p || !d_prev) return KKT_ERR_ARG;
+    const int nst = 2 * (int)p->params[0] + 1;
+    shift_stages_kernel<<<grid(p->n), kT, 0, st>>>(p->n, nst, d_prev, p->xt);
+    ICUDA(p, cudaGetLastError());
+    return kkt_ipm_init(p, p->xt, st);
+}
+
+// shift a stage-major vector by one stage in place (through scratch)
+static kkt_status shift_in_place(kkt_ipm* p, int len, int stride, double* v, double* scratch, cudaStream_t st) {
+    shift_stages_kernel<<<grid(len), kT, 0, st>>>(len, stride, v, scratch);
+    copy_kernel<<<grid(len), kT, 0, st>>>(len, scratch, v);
+    ICUDA(p, cudaGetLastError());
+    return KKT_OK;
+}
+
+// bound multipliers centred on the barrier parameter: z_L = mu / (x - lo),
+// z_U = mu / (hi - x) (infinite bounds: 0) -- the slack-multiplier
+// products start on the central path
+__global__ void center_kernel(int n, const double* __restrict__ x, const double* __restrict__ lo,
+                              const double* __restrict__ hi, double clo, double chi, double mu,
+                              double* __restrict__ zl, double* __restrict__ zu) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double l = lo ? lo[i] : clo, h = hi ? hi[i] : chi;
+        zl[i] = mu / fmax(x[i] - l, 1e-300);
+        zu[i] = mu / fmax(h - x[i], 1e-300);
+    }
+}
+
+kkt_status kkt_ipm_init_warm(kkt_ipm* p, double mu, int recenter, cudaStream_t st) {
+    if (!p) return KKT_ERR_ARG;
+    if (!p->started) return ierr(p, KKT_ERR_STATE, "kkt_ipm_init_warm needs a previous solve");
+    if (!(mu > 0 && std::isfinite(mu))) return ierr(p, KKT_ERR_ARG, "bad mu");
+    const int n = p->n, m = p->m, k = (int)p->params[0];
+    const int nst = 2 * k + 1, mst = 2 * k;
+    ITRY(shift_in_place(p, n, nst, p->x, p->xt, st));
+    ITRY(shift_in_place(p, n, nst, p->zl, p->xt, st));
+    ITRY(shift_in_place(p, n, nst, p->zu, p->xt, st));
+    ITRY(shift_in_place(p, m, mst, p->y, p->ct, st));
+    push_kernel<<<grid(n), kT, 0, st>>>(n, p->xlo, p->xhi, 0, 0, p->x);
+    if (p->opt.relaxed) {
+        ITRY(shift_in_place(p, m, mst, p->s, p->ct, st));
+        ITRY(shift_in_place(p, m, mst, p->vl, p->ct, st));
+        ITRY(shift_in_place(p, m, mst, p->vu, p->ct, st));
+        push_kernel<<<grid(m), kT, 0, st>>>(m, nullptr, nullptr, -p->opt.tau_relax, p->opt.tau_relax, p->s);
+    }
+    if (recenter) {
+        center_kernel<<<grid(n), kT, 0, st>>>(n, p->x, p->xlo, p->xhi, 0, 0, mu, p->zl, p->zu);
+        if (p->opt.relaxed)
+            center_kernel<<<grid(m), kT, 0, st>>>(m, p->s, nullptr, nullptr, -p->opt.tau_relax,
+                                                  p->opt.tau_relax, mu, p->vl, p->vu);
+    }
+    ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
+    double th = 0, ls = 0;
+    ITRY(measures(p, p->x, p->s, p->c, st, &th, &ls));
+    p->theta_max = 1e4 * std::max(1.0, th);
+    p->theta_min = 1e-4 * std::max(1.0, th);
+    p->mu = mu;
+    p->filter.clear();
+    p->delta_last = 0.0;
+    p->it = 0;
+    ICUDA(p, cudaGetLastError());
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_device_bytes(const kkt_ipm* p, int64_t* bytes) {
+    if (!p || !bytes) return KKT_ERR_ARG;
+    int64_t kb = 0;
+    kkt_status s = kkt_device_bytes(p->kkt, &kb);
+    if (s != KKT_OK) return s;
+    *bytes = kb + p->dev_bytes;
+    return KKT_OK;
 }
 
 kkt_status kkt_ipm_get(const kkt_ipm* p, double* d_x, double* d_y, double* d_zl, double* d_zu,

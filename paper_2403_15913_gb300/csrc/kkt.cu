@@ -59,8 +59,9 @@ struct kkt_ctx {
     int* d_task_ptr = nullptr;
     int* d_task_sn = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
-    // device allocations (all freed in kkt_destroy)
+    // device allocations (all freed in kkt_destroy) and their total size
     std::vector<void*> allocs;
+    long long dev_bytes = 0;
     Plan plan{};
     int* d_lvl_sn = nullptr;
     int *d_perm = nullptr, *d_iperm = nullptr;
@@ -163,6 +164,7 @@ kkt_status upload(kkt_ctx* c, T** dst, const std::vector<T>& src) {
     size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
     CUDA_TRY(c, cudaMalloc((void**)dst, bytes));
     c->allocs.push_back(*dst);
+    c->dev_bytes += (long long)bytes;
     if (!src.empty()) CUDA_TRY(c, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
     return KKT_OK;
 }
@@ -171,6 +173,7 @@ template <class T>
 kkt_status alloc(kkt_ctx* c, T** dst, size_t count) {
     CUDA_TRY(c, cudaMalloc((void**)dst, std::max<size_t>(1, count) * sizeof(T)));
     c->allocs.push_back(*dst);
+    c->dev_bytes += (long long)(std::max<size_t>(1, count) * sizeof(T));
     return KKT_OK;
 }
 
@@ -1154,6 +1157,97 @@ kkt_status kkt_batch_layout(const kkt_ctx* c, int* count, int* x_off, int* y_off
     return KKT_OK;
 }
 
+// Autotuner of the supernode partition for a batch: the candidates differ in
+// the relaxed amalgamation (width and explicit-zero budget), the width cut
+// and the small-subtree threshold, which together fix the panel (tile)
+// shapes every factor kernel works on.  Each candidate is analysed on an
+// evenly spaced sample of the instances and its numeric factorisation timed
+// on the device with synthetic SPD values (W = 0, Sigma = 1, J = 1, D = 1:
+// K = I + J^T J); the fastest wins.
+kkt_status kkt_autotune_batch(int count, const int* n, const int* m, const int* const* W_colptr,
+                              const int* const* W_rowind, const int* const* J_rowptr,
+                              const int* const* J_colind, const kkt_options* base, int sample,
+                              cudaStream_t stream, kkt_options* best, double* best_ms) {
+    if (count < 1 || !n || !m || !W_colptr || !W_rowind || !J_rowptr || !J_colind || !best)
+        return set_err(nullptr, KKT_ERR_ARG, "kkt_autotune_batch: bad arguments");
+    kkt_options b0;
+    if (base) b0 = *base; else kkt_default_options(&b0);
+    const int ns = std::max(1, std::min(count, sample > 0 ? sample : 32));
+    std::vector<int> pick(ns);
+    for (int i = 0; i < ns; ++i) pick[i] = (int)((long long)i * count / ns);
+    std::vector<int> sn(ns), sm(ns);
+    std::vector<const int*> wc(ns), wr(ns), jr(ns), jc(ns);
+    for (int i = 0; i < ns; ++i) {
+        const int q = pick[i];
+        sn[i] = n[q];
+        sm[i] = m[q];
+        wc[i] = W_colptr[q];
+        wr[i] = W_rowind[q];
+        jr[i] = J_rowptr[q];
+        jc[i] = J_colind[q];
+    }
+    struct Cand { int relax_cols, relax_zeros, max_width, subtree_cols; };
+    const Cand cands[] = {{32, 128, 64, 48}, {16, 64, 64, 48}, {48, 1024, 64, 48}, {64, 4096, 64, 48},
+                          {32, 128, 32, 48}, {32, 128, 64, 0},  {32, 128, 64, 24},  {0, 0, 64, 48}};
+    double best_t = INFINITY;
+    kkt_options won = b0;
+    for (const Cand& cd : cands) {
+        kkt_options o = b0;
+        o.scheme = KKT_LIFTED;
+        o.delta = 1.0;
+        o.precision = b0.precision;
+        o.relax_cols = cd.relax_cols;
+        o.relax_zeros = cd.relax_zeros;
+        o.max_width = cd.max_width;
+        o.subtree_cols = cd.subtree_cols;
+        kkt_ctx* c = nullptr;
+        TRY(analyse_batch(ns, sn.data(), sm.data(), wc.data(), wr.data(), jr.data(), jc.data(), &o, true, &c));
+        double* buf = nullptr;
+        const size_t nw = std::max(1, c->nnzW), nj = std::max(1, c->nnzJ);
+        cudaError_t e = cudaMalloc((void**)&buf, (nw + nj + c->n) * sizeof(double));
+        if (e != cudaSuccess) {
+            kkt_destroy(c);
+            return set_err(nullptr, KKT_ERR_OOM, "kkt_autotune_batch: device allocation failed");
+        }
+        double *dW = buf, *dJ = buf + nw, *dS = buf + nw + nj;
+        fill_kernel<<<grid_for((long long)nw), kThreads, 0, stream>>>((int)nw, 0.0, dW);
+        fill_kernel<<<grid_for((long long)nj), kThreads, 0, stream>>>((int)nj, 1.0, dJ);
+        fill_kernel<<<grid_for(c->n), kThreads, 0, stream>>>(c->n, 1.0, dS);
+        kkt_status st = kkt_factor(c, dW, dJ, dS, nullptr, 0.0, stream, nullptr);
+        std::vector<float> t;
+        cudaEvent_t a = nullptr, z = nullptr;
+        if (st == KKT_OK && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&z) == cudaSuccess) {
+            for (int r = 0; r < 3 && st == KKT_OK; ++r) {
+                cudaEventRecord(a, stream);
+                st = kkt_factor(c, dW, dJ, dS, nullptr, 0.0, stream, nullptr);
+                cudaEventRecord(z, stream);
+                cudaEventSynchronize(z);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, z);
+                t.push_back(ms);
+            }
+        }
+        if (a) cudaEventDestroy(a);
+        if (z) cudaEventDestroy(z);
+        cudaFree(buf);
+        kkt_destroy(c);
+        if (st != KKT_OK) return set_err(nullptr, st, "kkt_autotune_batch: factorisation failed");
+        std::sort(t.begin(), t.end());
+        const double med = t.empty() ? INFINITY : t[t.size() / 2];
+        if (med < best_t) {
+            best_t = med;
+            won = b0;
+            won.relax_cols = cd.relax_cols;
+            won.relax_zeros = cd.relax_zeros;
+            won.max_width = cd.max_width;
+            won.subtree_cols = cd.subtree_cols;
+        }
+    }
+    *best = won;
+    if (best_ms) *best_ms = best_t;
+    return KKT_OK;
+}
+
 kkt_status kkt_batch_results(const kkt_ctx* c, int* status, int* refine_iters, int* cg_iters,
                              double* bwd_err, int* failed_col) {
     if (!c) return KKT_ERR_ARG;
@@ -1587,6 +1681,12 @@ kkt_status kkt_get_stats(const kkt_ctx* c, kkt_stats* out) {
 kkt_status kkt_reset_stats(kkt_ctx* c) {
     if (!c) return KKT_ERR_ARG;
     c->stats = kkt_stats{};
+    return KKT_OK;
+}
+
+kkt_status kkt_device_bytes(const kkt_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return KKT_ERR_ARG;
+    *bytes = c->dev_bytes;
     return KKT_OK;
 }
 

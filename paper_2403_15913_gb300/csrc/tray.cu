@@ -55,9 +55,9 @@ __host__ __device__ inline long long j_stage_off(const TrayP& P, int t) {
 }
 __host__ __device__ inline int j_dyn_row_off(int i) { return i == 0 ? 0 : 4 + 6 * (i - 1); }
 
-__global__ void tray_eval_kernel(TrayP P, const double* __restrict__ w, const double* __restrict__ lam,
-                                 double objw, double* __restrict__ grad, double* __restrict__ c,
-                                 double* __restrict__ Jv, double* __restrict__ Wv) {
+__global__ void tray_eval_kernel(TrayP P, const double* __restrict__ x0v, const double* __restrict__ w,
+                                 const double* __restrict__ lam, double objw, double* __restrict__ grad,
+                                 double* __restrict__ c, double* __restrict__ Jv, double* __restrict__ Wv) {
     const int k = P.k;
     const long long total = (long long)(P.T + 1) * k;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -103,7 +103,7 @@ __global__ void tray_eval_kernel(TrayP P, const double* __restrict__ w, const do
             }
         }
         if (c) {
-            c[crow_dyn] = t == 0 ? x - P.x0bar : x - w[base - P.nst() + i] - hm * g;
+            c[crow_dyn] = t == 0 ? x - (x0v ? x0v[i] : P.x0bar) : x - w[base - P.nst() + i] - hm * g;
             c[crow_eq] = yt[i] - phi;
         }
         if (Jv) {
@@ -211,6 +211,27 @@ bool tray_objective_partials(const double* params, const double* d_w, double* d_
 }
 }  // namespace kktgb
 
+namespace kktgb {
+
+kkt_status tray_eval(const double* params, const double* d_x0, const double* d_w, const double* d_lam,
+                     double obj_weight, double* d_f, double* d_grad, double* d_c, double* d_Jval,
+                     double* d_Wval, cudaStream_t stream) {
+    TrayP P;
+    if (!unpack(params, P) || !d_w) return KKT_ERR_ARG;
+    if (d_Wval && !d_lam) return KKT_ERR_ARG;
+    if (d_grad || d_c || d_Jval || d_Wval) {
+        const long long total = (long long)(P.T + 1) * P.k;
+        long long g = (total + 255) / 256;
+        if (g > 152 * 32) g = 152 * 32;
+        tray_eval_kernel<<<(int)g, 256, 0, stream>>>(P, d_x0, d_w, d_lam, obj_weight, d_grad, d_c, d_Jval,
+                                                     d_Wval);
+    }
+    if (d_f) tray_objective_kernel<<<1, 256, 0, stream>>>(P, d_w, d_f);
+    return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_ERR_CUDA;
+}
+
+}  // namespace kktgb
+
 extern "C" {
 
 kkt_status kkt_tray_sizes(const double* params, int* n, int* m, int* nnzW, int* nnzJ) {
@@ -278,17 +299,8 @@ kkt_status kkt_tray_pattern(const double* params, int* W_colptr, int* W_rowind, 
 kkt_status kkt_tray_eval(const double* params, const double* d_w, const double* d_lam, double obj_weight,
                          double* d_f, double* d_grad, double* d_c, double* d_Jval, double* d_Wval,
                          cudaStream_t stream) {
-    TrayP P;
-    if (!unpack(params, P) || !d_w) return KKT_ERR_ARG;
-    if (d_Wval && !d_lam) return KKT_ERR_ARG;
-    if (d_grad || d_c || d_Jval || d_Wval) {
-        const long long total = (long long)(P.T + 1) * P.k;
-        long long g = (total + 255) / 256;
-        if (g > 152 * 32) g = 152 * 32;
-        tray_eval_kernel<<<(int)g, 256, 0, stream>>>(P, d_w, d_lam, obj_weight, d_grad, d_c, d_Jval, d_Wval);
-    }
-    if (d_f) tray_objective_kernel<<<1, 256, 0, stream>>>(P, d_w, d_f);
-    return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_ERR_CUDA;
+    return kktgb::tray_eval(params, nullptr, d_w, d_lam, obj_weight, d_f, d_grad, d_c, d_Jval, d_Wval,
+                            stream);
 }
 
 }  // extern "C"

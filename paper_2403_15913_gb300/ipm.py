@@ -34,6 +34,33 @@ class IPMSolver:
         self.n, self.m = n.value, m.value
         self.info = nat.IPMInfo()
 
+    def set_initial_state(self, x0=None, stream=None):
+        """Pin the stage-0 compositions to x0 (k values) for the next init;
+        None restores xbar_0."""
+        a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        st = nat.lib().kkt_ipm_set_initial_state(self._h, None if a is None else nat.ptr_f64(a),
+                                                 _stream(stream))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_set_initial_state failed")
+
+    def init_shifted(self, prev, stream=None):
+        """Start from a previous solution shifted by one stage."""
+        st = nat.lib().kkt_ipm_init_shifted(self._h, _dptr(prev), _stream(stream))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_init_shifted failed")
+
+    def init_warm(self, mu=1e-4, recenter=True, stream=None):
+        """Warm start from this solver's last iterate shifted one stage
+        (multipliers included, or recentred on mu), barrier parameter mu."""
+        st = nat.lib().kkt_ipm_init_warm(self._h, float(mu), int(bool(recenter)), _stream(stream))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_init_warm failed")
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        nat.lib().kkt_ipm_device_bytes(self._h, ctypes.byref(b))
+        return b.value
+
     def init(self, x0=None, stream=None):
         st = nat.lib().kkt_ipm_init(self._h, _dptr(x0), _stream(stream))
         if st != nat.KKT_OK:

@@ -229,3 +229,26 @@ class KKTBatchSolver(KKTSolver):
             nat.ptr_i32(out["cg_iters"]), nat.ptr_f64(out["bwd_err"]), nat.ptr_i32(out["failed_col"])))
         return out
 
+
+def autotune_batch(instances, sample=32, stream=None, **options):
+    """Options (relax_cols, relax_zeros, max_width, subtree_cols) whose
+    batch factorisation is fastest on this GPU (``kkt_autotune_batch``);
+    returns (options dict for KKTBatchSolver, median factor ms of the sample)."""
+    inst = [tuple(x) for x in instances]
+    cnt = len(inst)
+    ns = np.array([int(x[0]) for x in inst], np.int32)
+    ms = np.array([int(x[1]) for x in inst], np.int32)
+    keep = [[_i32(a) for a in x[2:6]] for x in inst]
+    ptrs = [(nat.I32P * cnt)(*[nat.ptr_i32(k[j]) for k in keep]) for j in range(4)]
+    base = default_options(**options)
+    best = nat.Options()
+    t = ctypes.c_double()
+    st = nat.lib().kkt_autotune_batch(cnt, nat.ptr_i32(ns), nat.ptr_i32(ms), *ptrs, ctypes.byref(base),
+                                      int(sample), _stream(stream), ctypes.byref(best), ctypes.byref(t))
+    if st != nat.KKT_OK:
+        raise KKTError(st, nat.lib().kkt_last_error(None).decode())
+    out = dict(options)
+    for f in ("relax_cols", "relax_zeros", "max_width", "subtree_cols"):
+        out[f] = getattr(best, f)
+    return out, t.value
+

@@ -186,3 +186,22 @@ def test_batch_256_uneven_instances():
     for i in rng.choice(256, 8, replace=False):
         p, pt, W, J = batch[i]
         assert oracle_eta(p, W, J, pt.sigma, s.delta_used[i], xs[i], ys[i], pt.rx, pt.ry) <= 1e-10
+
+
+def test_autotuned_partition_solves_batch():
+    """The autotuner returns one of its candidate partitions, and the batch
+    analysed with it still meets the bar on every instance."""
+    torch = torch_cuda()
+    from paper_2403_15913_gb300 import autotune_batch
+    batch = make_batch(SPECS, sigma_range=(1e-2, 1e2), seed0=11)
+    inst = [(p.n, p.m, W[0], W[1], J[0], J[1]) for p, pt, W, J in batch]
+    opts, ms = autotune_batch(inst, sample=4, **OPTS)
+    assert ms > 0 and np.isfinite(ms)
+    cands = {(32, 128, 64, 48), (16, 64, 64, 48), (48, 1024, 64, 48), (64, 4096, 64, 48),
+             (32, 128, 32, 48), (32, 128, 64, 0), (32, 128, 64, 24), (0, 0, 64, 48)}
+    assert (opts["relax_cols"], opts["relax_zeros"], opts["max_width"], opts["subtree_cols"]) in cands
+    s, st, sst, xs, ys = run_batch(batch, delta=np.full(len(batch), 10.0), **opts)
+    assert st == 0 and sst == 0
+    for i, (p, pt, W, J) in enumerate(batch):
+        assert oracle_eta(p, W, J, pt.sigma, 10.0, xs[i], ys[i], pt.rx, pt.ry) <= 1e-10
+

@@ -115,3 +115,18 @@ def test_table1_structure_is_a_different_variant():
     paper's nnz column does not apply: structure parity is unpinned."""
     p = TrayParams(k=32, T=100)
     assert p.n == 65 * 101 and p.n != 6767
+
+
+def test_initial_state_vector():
+    """A per-tray initial state changes only the stage-0 composition rows,
+    which become x_{i,0} - x0_i exactly; x0 = x0bar everywhere reproduces
+    the scalar form."""
+    p = TrayParams(k=6, T=4)
+    pt = kkt_point(p, 3)
+    x0 = np.linspace(0.1, 0.9, p.k)
+    c_scalar = tray.constraints(p, pt.w)
+    assert np.array_equal(tray.constraints(p, pt.w, np.full(p.k, p.x0bar)), c_scalar)
+    c = tray.constraints(p, pt.w, x0)
+    x, _, _ = tray.split(p, pt.w)
+    assert np.array_equal(c[:p.k], x[0] - x0)
+    assert np.array_equal(c[p.k:], c_scalar[p.k:])

@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--T", type=int, default=5000)
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--gamma", type=float, default=1e4)
+    ap.add_argument("--solver", default="supernodal", choices=["supernodal", "bcr"],
+                    help="K factorisation: supernodal Cholesky or block cyclic reduction of the stage blocks")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
     ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt", "batch", "serve"])
@@ -207,7 +209,8 @@ def run_ours(args, ws, rank, local):
     p = TrayParams(k=args.k, T=args.T)
     t0 = time.perf_counter()
     ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500,
-                    precision=1 if args.precision == "fp32" else 0)
+                    precision=1 if args.precision == "fp32" else 0,
+                    solver=1 if args.solver == "bcr" else 0, block=2 * args.k + 1)
     t_analyse = time.perf_counter() - t0
     kctx = nat.lib().kkt_ipm_kkt(ipm._h)
     ns, nnzL, panel, rows, lev, fl = (ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(),
@@ -307,7 +310,8 @@ def run_ours(args, ws, rank, local):
     factor_ms = st["factor_ms"] / fcalls
     kinv_ms = st["solve_ms"] / max(1, st["kinv_calls"])
     f32 = args.precision == "fp32"
-    roof = {"kernel": "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+    roof = {"kernel": ("block cyclic reduction (bcr_elim/bcr_update kernels)" if args.solver == "bcr" else
+                       "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)"),
             "bound": "alu", "achieved": fl.value / (factor_ms * 1e-3) / 1e9,
             "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -324,7 +328,7 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), full IPM "
                                f"iteration ({args.scheme}) from xbar_0 = {p.x0bar}, tol 1e-8",
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
-                   "precision": args.precision,
+                   "precision": args.precision, "solver": args.solver,
                    "fp32_factors": st["fp32_factors"], "fp64_fallbacks": st["fp64_fallbacks"],
                    "tau_relax": 1e-8 if args.scheme == "lifted" else None,
                    "l2": "flushed (256 MB write) between timed steps",
@@ -420,7 +424,8 @@ def run_kkt(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
-                relax_zeros=128, max_width=64)
+                relax_zeros=128, max_width=64, solver=1 if args.solver == "bcr" else 0,
+                block=2 * args.k + 1)
 
     def make(prec):
         t0 = time.perf_counter()
@@ -512,7 +517,8 @@ def run_kkt(args, ws, rank, local):
     fcalls = max(1, st["factor_calls"])
     factor_ms = st["factor_ms"] / fcalls
     f32 = prec == 1
-    roof = {"kernel": "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+    roof = {"kernel": ("block cyclic reduction (bcr_elim/bcr_update kernels)" if args.solver == "bcr" else
+                       "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)"),
             "bound": "alu", "achieved": sym.flops / (factor_ms * 1e-3) / 1e9,
             "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "traffic": None,
             "peak_source": ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
@@ -528,7 +534,7 @@ def run_kkt(args, ws, rank, local):
                                f"KKT step at a seeded iterate, Sigma log-uniform on [{sig[0]:g}, {sig[1]:g}]",
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
                    "delta": 1e-8 if args.scheme == "lifted" else None, "delta_x": delta_x,
-                   "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
+                   "precision": args.precision, "solver": args.solver, "l2": "flushed (256 MB write) between timed steps",
                    "analyse_s": round(t_analyse, 3), "factor_gflop": sym.flops / 1e9,
                    "factor_ms": factor_ms, "kinv_ms": st["solve_ms"] / max(1, st["kinv_calls"]),
                    "fp32_factors": st["fp32_factors"], "fp64_fallbacks": st["fp64_fallbacks"],

@@ -93,8 +93,19 @@ typedef struct {
                             the FP32 factor meets a non-positive pivot, or
                             the refinement stalls or hits max_refine, the
                             system is factorised again in FP64 and the solve
-                            is redone (mixed-precision factorisation, the
-                            direction Sec. VI names for future work)          */
+                            is redone (mixed-precision factorisation: an
+                            extension; the paper's pipeline is FP64)          */
+    int solver;          /* 0: supernodal Cholesky of the general pattern
+                            (default).  1: block cyclic reduction of the
+                            block-tridiagonal K of a stage-structured problem
+                            (stage-major variables, blocks of `block`
+                            variables; W within a stage, J rows within two
+                            consecutive stages): the structure-exploiting,
+                            parallel-in-time solver Sec. VII-B names as
+                            future work.  FP64, single instance, block <= 80; the
+                            analysis rejects other patterns (KKT_ERR_ARG);
+                            kkt_factor_export is not available               */
+    int block;           /* block size for solver 1 (2k+1 for the column)    */
 } kkt_options;
 
 /* Per-call report.  Fields not touched by a call keep their values. */
@@ -138,7 +149,10 @@ kkt_status kkt_analyse_host(int n, int m,
 /* Sizes of the symbolic result: supernodes, nonzeros of L, stored panel
  * entries (nnz(L) plus explicit zeros of relaxed supernodes), total row
  * indices over supernodes, levels of the supernodal elimination tree, and
- * the factorisation flop count sum_j cc_j^2 of the exact structure. */
+ * the factorisation flop count sum_j cc_j^2 of the exact structure.  With
+ * solver = 1 (after a device analysis), levels and flops are those of the
+ * block cyclic reduction (dense-block flops of every elimination and
+ * update). */
 kkt_status kkt_symbolic_sizes(const kkt_ctx* ctx, int* ns, int64_t* nnz_L,
                               int64_t* panel_entries, int64_t* row_entries,
                               int* levels, double* flops);

@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("tol_refine", ctypes.c_double),
                 ("tol_cg", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int),
-                ("subtree_cols", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("subtree_cols", ctypes.c_int), ("precision", ctypes.c_int),
+                ("solver", ctypes.c_int), ("block", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -12,6 +12,7 @@
 #include <thread>
 #include <vector>
 
+#include "bcr_kernels.cuh"
 #include "kernels.cuh"
 #include "symbolic.h"
 
@@ -127,6 +128,18 @@ struct kkt_ctx {
     // per-instance results of the last factor / solve
     std::vector<int> r_status, r_refine, r_cg, r_fail;
     std::vector<double> r_eta;
+    // block cyclic reduction (opt.solver == 1): N blocks of b variables;
+    // level l eliminates bcr_elim[elim_ptr[l] ..] then updates the survivors
+    // bcr_surv[surv_ptr[l] ..]; the last level eliminates the root alone
+    int bcr_b = 0, bcr_N = 0, bcr_nlev = 0;
+    std::vector<int> bcr_elim_ptr, bcr_surv_ptr;
+    int4 *d_bcr_elim = nullptr, *d_bcr_surv = nullptr;
+    double* d_bcr = nullptr;     // A blocks then C blocks (2 N b^2)
+    double* d_bcr_pn = nullptr;  // factor panels (3 N b^2)
+    long long bcr_nk = 0;
+    long long *d_bcr_slot = nullptr, *d_bcr_sptr = nullptr;
+    int2* d_bcr_src = nullptr;
+    double bcr_flops = 0.0;
     // tracing
     bool profiling = false;
     kkt_stats stats{};
@@ -224,6 +237,101 @@ void spans_collect(kkt_ctx* c) {
     }
     c->spans.clear();
     c->ev_used = 0;
+}
+
+// Plan of the block cyclic reduction: dense-block assembly map (every entry
+// of K lands in A[t] (both triangles) or in C[t] = K[t, t-1]), level
+// schedule, flop count.  Rejects patterns that are not block tridiagonal.
+kkt_status build_bcr(kkt_ctx* c, const int* W_colptr, const int* W_rowind, const int* J_rowptr,
+                     const int* J_colind) {
+    const int n = c->n, m = c->m, b = c->opt.block;
+    if (c->nb != 1) return set_err(c, KKT_ERR_ARG, "block-tridiagonal solver: single instance only");
+    if (c->opt.precision != 0) return set_err(c, KKT_ERR_ARG, "block-tridiagonal solver: FP64 only");
+    if (b < 1 || b > kBcrMaxBlock || n % b != 0)
+        return set_err(c, KKT_ERR_ARG, "block-tridiagonal solver: block must divide n and be <= " +
+                                           std::to_string(kBcrMaxBlock));
+    const int N = n / b;
+    const long long bb = (long long)b * b;
+    struct E {
+        long long slot;
+        int a, bsrc;
+    };
+    std::vector<E> ents;
+    bool ok = true;
+    auto put = [&](int i, int j, int a, int bs) {   // K[i, j] += source, i >= j in value
+        const int ti = i / b, tj = j / b;
+        if (ti == tj) {
+            ents.push_back({(long long)ti * bb + (i % b) + (long long)(j % b) * b, a, bs});
+            if (i != j) ents.push_back({(long long)ti * bb + (j % b) + (long long)(i % b) * b, a, bs});
+        } else if (ti == tj + 1) {
+            ents.push_back({(long long)(N + ti) * bb + (i % b) + (long long)(j % b) * b, a, bs});
+        } else if (tj == ti + 1) {
+            ents.push_back({(long long)(N + tj) * bb + (j % b) + (long long)(i % b) * b, a, bs});
+        } else {
+            ok = false;
+        }
+    };
+    for (int col = 0; col < n; ++col)
+        for (int p = W_colptr[col]; p < W_colptr[col + 1]; ++p) put(W_rowind[p], col, p, -1);
+    for (int v = 0; v < n; ++v) put(v, v, v, -2);
+    for (int r = 0; r < m && ok; ++r)
+        for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p)
+            for (int q = p; q < J_rowptr[r + 1]; ++q) put(J_colind[p], J_colind[q], p, q);
+    if (!ok) return set_err(c, KKT_ERR_ARG, "block-tridiagonal solver: K is not block tridiagonal for block " +
+                                                std::to_string(b));
+    std::stable_sort(ents.begin(), ents.end(), [](const E& x, const E& y) { return x.slot < y.slot; });
+    std::vector<long long> slot, sptr;
+    std::vector<int2> src;
+    src.reserve(ents.size());
+    for (size_t q = 0; q < ents.size(); ++q) {
+        if (q == 0 || ents[q].slot != ents[q - 1].slot) {
+            slot.push_back(ents[q].slot);
+            sptr.push_back((long long)q);
+        }
+        src.push_back(make_int2(ents[q].a, ents[q].bsrc));
+    }
+    sptr.push_back((long long)ents.size());
+    // level schedule: eliminate the even positions of the active chain
+    std::vector<int> active(N);
+    for (int t = 0; t < N; ++t) active[t] = t;
+    std::vector<int4> elim, surv;
+    c->bcr_elim_ptr.assign(1, 0);
+    c->bcr_surv_ptr.assign(1, 0);
+    double fl = 0.0;
+    const double b3 = (double)b * b * b;
+    while (true) {
+        const int A = (int)active.size();
+        std::vector<int> next;
+        for (int q = 0; q < A; ++q) {
+            const int prev = q > 0 ? active[q - 1] : -1, nxt = q + 1 < A ? active[q + 1] : -1;
+            if (A == 1 || q % 2 == 0) {
+                elim.push_back(make_int4(active[q], prev, nxt, 0));
+                const int nb2 = (prev >= 0) + (nxt >= 0);
+                // POTRF, TRSM of the neighbour rows, fill GEMM, neighbour updates
+                fl += b3 / 3.0 + b3 * nb2 + (prev >= 0 && nxt >= 0 ? 2.0 * b3 : 0.0) + 2.0 * b3 * nb2;
+            } else {
+                surv.push_back(make_int4(active[q], prev, nxt, 0));
+                next.push_back(active[q]);
+            }
+        }
+        c->bcr_elim_ptr.push_back((int)elim.size());
+        c->bcr_surv_ptr.push_back((int)surv.size());
+        if (A == 1) break;
+        active.swap(next);
+    }
+    c->bcr_nlev = (int)c->bcr_elim_ptr.size() - 1;
+    c->bcr_b = b;
+    c->bcr_N = N;
+    c->bcr_flops = fl;
+    c->bcr_nk = (long long)slot.size();
+    TRY(upload(c, &c->d_bcr_elim, elim));
+    TRY(upload(c, &c->d_bcr_surv, surv));
+    TRY(upload(c, &c->d_bcr_slot, slot));
+    TRY(upload(c, &c->d_bcr_sptr, sptr));
+    TRY(upload(c, &c->d_bcr_src, src));
+    TRY(alloc(c, &c->d_bcr, (size_t)2 * N * bb));
+    TRY(alloc(c, &c->d_bcr_pn, (size_t)3 * N * bb));
+    return KKT_OK;
 }
 
 // Build the device plan from the symbolic analysis and the input patterns.
@@ -654,6 +762,28 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     return KKT_OK;
 }
 
+// Block cyclic reduction: K^{-1} v in place (natural order), levels forward
+// then backward.
+void enqueue_bcr_solve(kkt_ctx* c, double* v, cudaStream_t st, const int* active) {
+    const int b = c->bcr_b;
+    for (int l = 0; l < c->bcr_nlev; ++l) {
+        const int ne = c->bcr_elim_ptr[l + 1] - c->bcr_elim_ptr[l];
+        const int ns = c->bcr_surv_ptr[l + 1] - c->bcr_surv_ptr[l];
+        if (ne > 0)
+            bcr_fwd_elim_kernel<<<ne, kThreads, 0, st>>>(b, c->d_bcr_elim + c->bcr_elim_ptr[l], c->d_bcr_pn,
+                                                         c->d_dinv, v, active);
+        if (ns > 0)
+            bcr_fwd_update_kernel<<<ns, kThreads, 0, st>>>(b, c->d_bcr_surv + c->bcr_surv_ptr[l], c->d_bcr_pn,
+                                                           v, active);
+    }
+    for (int l = c->bcr_nlev - 1; l >= 0; --l) {
+        const int ne = c->bcr_elim_ptr[l + 1] - c->bcr_elim_ptr[l];
+        if (ne > 0)
+            bcr_bwd_kernel<<<ne, kThreads, 0, st>>>(b, c->d_bcr_elim + c->bcr_elim_ptr[l], c->d_bcr_pn,
+                                                    c->d_dinv, v, active);
+    }
+}
+
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
 // levels bottom-up, then levels top-down and subtree tasks (panels Lx and
 // reciprocal pivots dinv of the precision T).
@@ -689,7 +819,15 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
     const int sp = span_begin(c, 2, st);
     c->stats.kinv_calls++;
     c->stats.launches += 2 + 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0);
-    if (c->cur_prec == 1) {
+    if (c->opt.solver == 1) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->w_xp, in, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (c->tri_exec) {
+            CUDA_TRY(c, cudaGraphLaunch(c->tri_exec, st));
+        } else {
+            enqueue_bcr_solve(c, c->w_xp, st, nullptr);
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(out, c->w_xp, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (c->cur_prec == 1) {
         gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp32, nullptr);
         if (c->tri_exec32) {
             CUDA_TRY(c, cudaGraphLaunch(c->tri_exec32, st));
@@ -767,9 +905,13 @@ void enqueue_cg_iteration(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStr
     const int* act = c->d_cg;
     jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->v_J,
                                                      nullptr, c->w_p, nullptr, 1.0, 1.0, c->w_tn, act);
-    gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, xp, act);
-    enqueue_triangular_solves<T>(c, Lx, dinv, xp, st, act);
-    scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, c->w_tn, act);
+    if (c->opt.solver == 1) {
+        enqueue_bcr_solve(c, c->w_tn, st, act);
+    } else {
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, xp, act);
+        enqueue_triangular_solves<T>(c, Lx, dinv, xp, st, act);
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, c->w_tn, act);
+    }
     j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
                                                      nullptr, nullptr, 1.0, c->w_sp, act);
     seg_dot(c, c->w_p, c->w_sp, 2, st, act);
@@ -797,8 +939,10 @@ kkt_status capture_graphs(kkt_ctx* c) {
         if (err != cudaSuccess) return err;
         return cudaGraphGetNodes(*g, nullptr, nodes);
     };
-    cudaError_t err = capture([&] { enqueue_triangular_solves(c, c->w_xp, cs, nullptr); },
-                              &c->tri_graph, &c->tri_exec, &c->tri_nodes);
+    cudaError_t err = capture([&] {
+        if (c->opt.solver == 1) enqueue_bcr_solve(c, c->w_xp, cs, nullptr);
+        else enqueue_triangular_solves(c, c->w_xp, cs, nullptr);
+    }, &c->tri_graph, &c->tri_exec, &c->tri_nodes);
     if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
         err = capture([&] { enqueue_cg_iteration<double>(c, c->d_Lx, c->d_dinv, c->w_xp, cs); },
                       &c->cg_graph, &c->cg_exec, &c->cg_nodes);
@@ -879,6 +1023,40 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
 // kNoFail, above every column index.
 constexpr int kNoFail = 0x7f7f7f7f;
 
+// Block cyclic reduction: assemble the dense blocks, then per level the
+// eliminations (factor panels, fill couplings) and the survivor updates.
+kkt_status enqueue_bcr_factor(kkt_ctx* c, double delta_x, cudaStream_t st) {
+    const int b = c->bcr_b, N = c->bcr_N;
+    const long long bb = (long long)b * b;
+    const int sp_a = span_begin(c, 0, st);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_bcr, 0, (size_t)2 * N * bb * sizeof(double), st));
+    assemble_kernel<double><<<grid_for(c->bcr_nk), kThreads, 0, st>>>(
+        c->bcr_nk, c->d_bcr_slot, c->d_bcr_sptr, c->d_bcr_src, c->f_W, c->v_Js, c->f_sigma, delta_x,
+        c->f_dvec, c->d_bcr);
+    span_end(c, sp_a, st);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_fail, 0x7f, sizeof(int), st));
+    const FailSink fs{c->d_fail, nullptr};
+    const int sp_f = span_begin(c, 1, st);
+    c->stats.factor_calls++;
+    double* A = c->d_bcr;
+    double* C = c->d_bcr + (size_t)N * bb;
+    for (int l = 0; l < c->bcr_nlev; ++l) {
+        const int ne = c->bcr_elim_ptr[l + 1] - c->bcr_elim_ptr[l];
+        const int ns = c->bcr_surv_ptr[l + 1] - c->bcr_surv_ptr[l];
+        if (ne > 0)
+            bcr_elim_kernel<<<ne, kThreads, (size_t)3 * bb * sizeof(double), st>>>(
+                b, c->d_bcr_elim + c->bcr_elim_ptr[l], A, C, c->d_bcr_pn, c->d_dinv, fs);
+        if (ns > 0)
+            bcr_update_kernel<<<ns, kThreads, (size_t)2 * bb * sizeof(double), st>>>(
+                b, c->d_bcr_surv + c->bcr_surv_ptr[l], A, c->d_bcr_pn);
+        c->stats.launches += 2;
+        c->stats.factor_launches += 2;
+    }
+    span_end(c, sp_f, st);
+    CUDA_TRY(c, cudaGetLastError());
+    return KKT_OK;
+}
+
 template <typename T>
 kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
     const int sp_a = span_begin(c, 0, st);
@@ -948,6 +1126,8 @@ void kkt_default_options(kkt_options* o) {
     o->target_relaxed = 0;
     o->subtree_cols = 48;
     o->precision = 0;
+    o->solver = 0;
+    o->block = 0;
 }
 
 namespace {
@@ -964,6 +1144,10 @@ kkt_status new_ctx(const kkt_options* opt, kkt_ctx** out) {
     if (c->opt.precision != 0 && c->opt.precision != 1) {
         delete c;
         return set_err(nullptr, KKT_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32 factor)");
+    }
+    if (c->opt.solver != 0 && c->opt.solver != 1) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_ARG, "solver must be 0 (supernodal) or 1 (block tridiagonal)");
     }
     if (c->opt.max_width <= 0 || c->opt.max_width > 64) c->opt.max_width = 64;
     *out = c;
@@ -1002,11 +1186,16 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     }
     if (device) {
         kkt_status st = build_plan(c, W_colptr, W_rowind, J_rowptr, J_colind);
+        if (st == KKT_OK && c->opt.solver == 1) st = build_bcr(c, W_colptr, W_rowind, J_rowptr, J_colind);
         if (st != KKT_OK) {
             set_err(nullptr, st, c->err);
             kkt_destroy(c);
             return st;
         }
+        cudaFuncSetAttribute(bcr_elim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(3 * kBcrMaxBlock * kBcrMaxBlock * sizeof(double)));
+        cudaFuncSetAttribute(bcr_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kBcrMaxBlock * kBcrMaxBlock * sizeof(double)));
         cudaFuncSetAttribute(factor_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(double)));
         cudaFuncSetAttribute(factor_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1274,8 +1463,8 @@ kkt_status kkt_symbolic_sizes(const kkt_ctx* c, int* ns, int64_t* nnz_L, int64_t
         *panel = p;
     }
     if (row_entries) *row_entries = (int64_t)c->sym.sn_rows.size();
-    if (levels) *levels = c->tree_levels;
-    if (flops) *flops = c->sym.flops;
+    if (levels) *levels = c->opt.solver == 1 ? c->bcr_nlev : c->tree_levels;
+    if (flops) *flops = c->opt.solver == 1 ? c->bcr_flops : c->sym.flops;
     return KKT_OK;
 }
 
@@ -1366,7 +1555,11 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
         return false;
     };
     int detail = 0;
-    if (c->opt.precision == 1) {
+    if (c->opt.solver == 1) {
+        TRY(enqueue_bcr_factor(c, delta_x, st));
+        c->cur_prec = 0;
+        detail = 3;   // marks the path below; reported as 0 (FP64)
+    } else if (c->opt.precision == 1) {
         TRY(enqueue_numeric_factor<float>(c, c->d_Lx32, c->d_dinv32, delta_x, st));
         TRY(fetch_fail());
         c->stats.fp32_factors++;
@@ -1377,10 +1570,11 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
             detail = 2;
         }
     }
-    if (detail != 1) {
+    if (detail == 0 || detail == 2) {
         TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, delta_x, st));
         c->cur_prec = 0;
     }
+    if (detail == 3) detail = 0;
     // ||K_orig,i||_inf
     CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), st));
     if (c->f_C) {
@@ -1618,7 +1812,11 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     double* xp = nullptr;
     TRY(noalloc_scratch(c, &xp));
     const int n = c->n;
-    if (c->cur_prec == 1) {   // FP32 factor: the scratch holds n floats
+    if (c->opt.solver == 1) {
+        CUDA_TRY(c, cudaMemcpyAsync(xp, d_b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        enqueue_bcr_solve(c, xp, st, nullptr);
+        CUDA_TRY(c, cudaMemcpyAsync(d_x, xp, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (c->cur_prec == 1) {   // FP32 factor: the scratch holds n floats
         float* xp32 = reinterpret_cast<float*>(xp);
         gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp32, nullptr);
         enqueue_triangular_solves<float>(c, c->d_Lx32, c->d_dinv32, xp32, st, nullptr);
@@ -1636,6 +1834,7 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
 kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* val) {
     if (!c) return KKT_ERR_ARG;
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "no factor");
+    if (c->opt.solver == 1) return set_err(c, KKT_ERR_STATE, "the block-tridiagonal factor has no supernodal form");
     const int ns = c->sym.ns();
     std::vector<double> Lh((size_t)c->panel), dv(c->n);
     if (val && c->cur_prec == 1) {

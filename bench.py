@@ -37,6 +37,8 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x DFMA/clk/SM x flops x GHz = 1258.6
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FFMA lanes/SM x flops x GHz = 80,548
 METRIC = "KKT solve time per IPM iteration"
+PREC = {"fp64": 0, "fp32": 1, "df64": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32 factor + f64 refinement", "df64": "df64 (float-pair) factor + f64 refinement"}
 UNIT = "ms/iter"
 
 
@@ -52,8 +54,9 @@ def parse():
     ap.add_argument("--gamma", type=float, default=1e4)
     ap.add_argument("--solver", default="supernodal", choices=["supernodal", "bcr"],
                     help="K factorisation: supernodal Cholesky or block cyclic reduction of the stage blocks")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
-                    help="factor precision; fp32 refines in FP64 and falls back to an FP64 factor")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"],
+                    help="factor precision; fp32 and df64 (float pairs) refine in FP64 and fall back "
+                         "to an FP64 factor")
     ap.add_argument("--workload", default="ipm", choices=["ipm", "kkt", "batch", "serve"])
     ap.add_argument("--clients", type=int, default=64, help="serve workload: controllers")
     ap.add_argument("--requests", type=int, default=400, help="serve workload: timed requests")
@@ -209,7 +212,7 @@ def run_ours(args, ws, rank, local):
     p = TrayParams(k=args.k, T=args.T)
     t0 = time.perf_counter()
     ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500,
-                    precision=1 if args.precision == "fp32" else 0,
+                    precision=PREC[args.precision],
                     solver=1 if args.solver == "bcr" else 0, block=2 * args.k + 1)
     t_analyse = time.perf_counter() - t0
     kctx = nat.lib().kkt_ipm_kkt(ipm._h)
@@ -323,7 +326,7 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64",
+        "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic",
         "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), full IPM "
                                f"iteration ({args.scheme}) from xbar_0 = {p.x0bar}, tol 1e-8",
@@ -466,7 +469,7 @@ def run_kkt(args, ws, rank, local):
         s.set_profiling(False)
         return ms, infos, s.stats()
 
-    prec = 1 if args.precision == "fp32" else 0
+    prec = PREC[args.precision]
     solver, t_analyse = make(prec)
     delta_x = find_delta(solver)
     clocks = ClockSampler(local)
@@ -483,7 +486,7 @@ def run_kkt(args, ws, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         mean_ms = t.item()
     fp64_cmp = None
-    if prec == 1:
+    if prec != 0:
         s64, _ = make(0)
         ms64, infos64, st64 = timed(s64, delta_x, args.steps)
         v64 = torch.cat([dx, dy]).cpu().numpy()
@@ -529,7 +532,7 @@ def run_kkt(args, ws, rank, local):
     line = {
         "metric": KKT_METRIC, "value": mean_ms, "unit": "ms/step", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), one {args.scheme} "
                                f"KKT step at a seeded iterate, Sigma log-uniform on [{sig[0]:g}, {sig[1]:g}]",
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
@@ -597,7 +600,7 @@ def run_batch(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
                 relax_zeros=128, max_width=64)
-    prec = 1 if args.precision == "fp32" else 0
+    prec = PREC[args.precision]
     tuned = None
     if args.autotune:
         t0 = time.perf_counter()
@@ -736,7 +739,7 @@ def run_batch(args, ws, rank, local):
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 factor + f64 refinement" if f32 else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": f"{args.batch} independent tray-column KKT systems, trays uniform in "
                                f"{{16,24,32,48,64}}, T uniform in [20,400] (n = {bs.n}, m = {bs.m} in "
                                f"total), one {args.scheme} factor + refined solve of the whole batch per "
@@ -827,7 +830,7 @@ def run_serve(args, ws, rank, local):
                 "contexts": st["contexts_created"], "evictions": st["evictions"],
                 "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "clocks": clk}
 
-    prec = 1 if args.precision == "fp32" else 0
+    prec = PREC[args.precision]
     conc = serve(args.slots, prec)
     serial = serve(1, 0)
     # service latency below saturation: the same server at 70% of the
@@ -850,7 +853,7 @@ def run_serve(args, ws, rank, local):
             "metric": SERVE_METRIC, "value": total, "unit": "solves/s", "n_gpus": ws,
             "steps": args.requests, "warmup": args.clients, "ms_per_step": conc["mean_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 factor + f64 refinement" if prec else "f64", "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": f"{args.clients} NMPC clients (trays in {{32,64}}, T uniform in [50,2000], "
                                    f"n = {n_total} in total), {args.requests} requests with Poisson arrivals at "
                                    f"{args.rate:g}/s, each a full {args.scheme} IPM solve to 1e-8 warm-started "

@@ -88,8 +88,10 @@ typedef struct {
     int subtree_cols;    /* subtrees of the supernodal tree with at most this
                             many columns are factorised and solved by one
                             CTA each (48); 0 disables                         */
-    int precision;       /* 0: factor in FP64 (default).  1: factor in FP32
-                            and refine in FP64 against the FP64 system; if
+    int precision;       /* 0: factor in FP64 (default).  1: factor in FP32,
+                            2: in double-float (pairs of FP32 numbers, ~48
+                            significand bits, on the FP32 pipe), and refine
+                            in FP64 against the FP64 system; if
                             the FP32 factor meets a non-positive pivot, or
                             the refinement stalls or hits max_refine, the
                             system is factorised again in FP64 and the solve
@@ -115,8 +117,9 @@ typedef struct {
     int failed_col;      /* first column (permuted order) with a non-positive
                             pivot in the last factor, -1 if none              */
     int status_detail;   /* precision of the factor in use: 0 FP64 (precision
-                            0), 1 FP32, 2 FP64 after an FP32 fallback; a
-                            solve that fell back sets 2 as well               */
+                            0), 1 FP32, 2 FP64 after a fallback from FP32 or
+                            double-float, 3 double-float; a solve that fell
+                            back sets 2 as well                               */
     double bwd_err;      /* eta = ||b - K_orig v||_inf /
                                   (||K_orig||_inf ||v||_inf + ||b||_inf)      */
     double delta_x;      /* delta_x used by the last factor                    */
@@ -304,7 +307,8 @@ typedef struct {
     int64_t factor_launches; /* of which numeric-factorisation kernels    */
     int64_t factor_calls;    /* kkt_factor calls                          */
     int64_t kinv_calls;      /* applications of K^{-1} (pairs of solves)  */
-    int64_t fp32_factors;    /* FP32 factorizations (precision = 1)       */
+    int64_t fp32_factors;    /* reduced-precision factorizations (FP32 or
+                                double-float, precision 1 or 2)           */
     int64_t fp64_fallbacks;  /* FP64 refactorizations after an FP32 factor
                                 failed or did not refine to tol_refine    */
 } kkt_stats;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "bcr_kernels.cuh"
+#include "df64.cuh"
 #include "kernels.cuh"
 #include "symbolic.h"
 
@@ -84,7 +85,10 @@ struct kkt_ctx {
     double* v_Js = nullptr;     // J scaled by sqrt(D) for the assembly
     // FP32 factor (precision = 1): panels, reciprocal pivots, permuted vector
     float *d_Lx32 = nullptr, *d_dinv32 = nullptr, *w_xp32 = nullptr;
-    int cur_prec = 0;           // precision of the current factor: 0 FP64, 1 FP32
+    // precision of the current factor: 0 FP64, 1 FP32, 2 double-float (kept
+    // in the FP64 buffers: a float pair is 8 bytes); the graphs of the
+    // reduced precision (1 or 2) are tri_exec32 / cg_exec32
+    int cur_prec = 0;
     // factor inputs of the last kkt_factor
     bool factored = false;
     const double *f_W = nullptr, *f_J = nullptr, *f_sigma = nullptr, *f_D = nullptr;
@@ -762,6 +766,8 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     return KKT_OK;
 }
 
+df64* as_df(double* p) { return reinterpret_cast<df64*>(p); }
+
 // Block cyclic reduction: K^{-1} v in place (natural order), levels forward
 // then backward.
 void enqueue_bcr_solve(kkt_ctx* c, double* v, cudaStream_t st, const int* active) {
@@ -827,6 +833,14 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
             enqueue_bcr_solve(c, c->w_xp, st, nullptr);
         }
         CUDA_TRY(c, cudaMemcpyAsync(out, c->w_xp, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (c->cur_prec == 2) {
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, as_df(c->w_xp), nullptr);
+        if (c->tri_exec32) {
+            CUDA_TRY(c, cudaGraphLaunch(c->tri_exec32, st));
+        } else {
+            enqueue_triangular_solves<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), as_df(c->w_xp), st, nullptr);
+        }
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, as_df(c->w_xp), out, nullptr);
     } else if (c->cur_prec == 1) {
         gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp32, nullptr);
         if (c->tri_exec32) {
@@ -946,6 +960,14 @@ kkt_status capture_graphs(kkt_ctx* c) {
     if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
         err = capture([&] { enqueue_cg_iteration<double>(c, c->d_Lx, c->d_dinv, c->w_xp, cs); },
                       &c->cg_graph, &c->cg_exec, &c->cg_nodes);
+    if (err == cudaSuccess && c->opt.precision == 2) {
+        err = capture([&] { enqueue_triangular_solves<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), as_df(c->w_xp), cs,
+                                                            nullptr); },
+                      &c->tri_graph32, &c->tri_exec32, &c->tri_nodes32);
+        if (err == cudaSuccess && c->opt.scheme == KKT_HYKKT)
+            err = capture([&] { enqueue_cg_iteration<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), as_df(c->w_xp), cs); },
+                          &c->cg_graph32, &c->cg_exec32, &c->cg_nodes32);
+    }
     if (err == cudaSuccess && c->opt.precision == 1) {
         err = capture([&] { enqueue_triangular_solves<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, cs, nullptr); },
                       &c->tri_graph32, &c->tri_exec32, &c->tri_nodes32);
@@ -983,11 +1005,13 @@ kkt_status hykkt_inner(kkt_ctx* c, const double* rx, const double* ry, double* d
                                            c->d_cg);
     const int sp = span_begin(c, 3, st);
     while (true) {
-        const bool f32 = c->cur_prec == 1;
+        const bool f32 = c->cur_prec != 0;
         for (int b = 0; b < kCgBatch; ++b) {
             cudaGraphExec_t ex = f32 ? c->cg_exec32 : c->cg_exec;
             if (ex) {
                 CUDA_TRY(c, cudaGraphLaunch(ex, st));
+            } else if (c->cur_prec == 2) {
+                enqueue_cg_iteration<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), as_df(c->w_xp), st);
             } else if (f32) {
                 enqueue_cg_iteration<float>(c, c->d_Lx32, c->d_dinv32, c->w_xp32, st);
             } else {
@@ -1141,9 +1165,9 @@ kkt_status new_ctx(const kkt_options* opt, kkt_ctx** out) {
         delete c;
         return set_err(nullptr, KKT_ERR_ARG, "unknown scheme");
     }
-    if (c->opt.precision != 0 && c->opt.precision != 1) {
+    if (c->opt.precision < 0 || c->opt.precision > 2) {
         delete c;
-        return set_err(nullptr, KKT_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32 factor)");
+        return set_err(nullptr, KKT_ERR_ARG, "precision must be 0 (FP64), 1 (FP32) or 2 (double-float factor)");
     }
     if (c->opt.solver != 0 && c->opt.solver != 1) {
         delete c;
@@ -1200,6 +1224,10 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                              (int)(kSmemCapElems * sizeof(double)));
         cudaFuncSetAttribute(factor_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(float)));
+        cudaFuncSetAttribute(factor_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemCapElems * sizeof(df64)));
+        cudaFuncSetAttribute(backward_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             160 * 1024);
         cudaFuncSetAttribute(backward_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              160 * 1024);
         cudaFuncSetAttribute(backward_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1554,27 +1582,36 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
             if (c->h_int[i] != kNoFail) return true;
         return false;
     };
+    // detail: 0 FP64, 1 FP32, 2 FP64 after a failed reduced-precision
+    // factor, 3 double-float
     int detail = 0;
+    bool need64 = true;
     if (c->opt.solver == 1) {
         TRY(enqueue_bcr_factor(c, delta_x, st));
         c->cur_prec = 0;
-        detail = 3;   // marks the path below; reported as 0 (FP64)
-    } else if (c->opt.precision == 1) {
-        TRY(enqueue_numeric_factor<float>(c, c->d_Lx32, c->d_dinv32, delta_x, st));
+        need64 = false;
+    } else if (c->opt.precision == 1 || c->opt.precision == 2) {
+        if (c->opt.precision == 1) {
+            TRY(enqueue_numeric_factor<float>(c, c->d_Lx32, c->d_dinv32, delta_x, st));
+        } else {
+            TRY(enqueue_numeric_factor<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), delta_x, st));
+        }
         TRY(fetch_fail());
         c->stats.fp32_factors++;
-        c->cur_prec = 1;
-        detail = 1;
-        if (any_fail()) {            // an FP32 pivot failed: factorise in FP64
+        c->cur_prec = c->opt.precision;
+        detail = c->opt.precision == 1 ? 1 : 3;
+        need64 = false;
+        if (any_fail()) {            // a reduced-precision pivot failed: factorise in FP64
             c->stats.fp64_fallbacks++;
             detail = 2;
+            need64 = true;
         }
     }
-    if (detail == 0 || detail == 2) {
+    if (need64) {
         TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, delta_x, st));
         c->cur_prec = 0;
     }
-    if (detail == 3) detail = 0;
+    const bool reduced_ok = detail == 1 || detail == 3;
     // ||K_orig,i||_inf
     CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), st));
     if (c->f_C) {
@@ -1585,7 +1622,7 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
                                                  c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx, c->f_J,
                                                  c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C, c->d_knorm);
     CUDA_TRY(c, cudaMemcpyAsync(c->h_red, c->d_knorm, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (detail == 1) {
+    if (reduced_ok) {
         CUDA_TRY(c, cudaStreamSynchronize(st));
     } else {
         TRY(fetch_fail());   // synchronises
@@ -1594,7 +1631,7 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
     int first_fail = -1, nfail = 0;
     for (int i = 0; i < nb; ++i) {
         c->h_knorm[i] = c->h_red[i];
-        const int w = detail == 1 ? kNoFail : c->h_int[i];
+        const int w = reduced_ok ? kNoFail : c->h_int[i];
         c->r_fail[i] = w == kNoFail ? -1 : w;
         c->r_status[i] = w == kNoFail ? KKT_OK : KKT_ERR_NOT_SPD;
         if (w != kNoFail) {
@@ -1654,7 +1691,7 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
     std::vector<double> eta(nb, INFINITY), prev(nb, INFINITY);
     std::vector<int> slow(nb, 0), state(nb, 0);
     std::fill(c->r_cg.begin(), c->r_cg.end(), 0);
-    int detail = c->cur_prec;
+    int detail = c->cur_prec == 2 ? 3 : c->cur_prec;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
         CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
@@ -1704,7 +1741,7 @@ kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double*
             if (state[i] == kRunning) state[i] = KKT_ERR_MAXIT;
             if (state[i] != KKT_OK && !failed[i]) all_ok = false;
         }
-        if (all_ok || c->cur_prec != 1) break;
+        if (all_ok || c->cur_prec == 0) break;
         // the FP32 factor did not carry the refinement to the tolerance:
         // factorise the same system in FP64 and solve again
         TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, c->f_delta_x, st));
@@ -1816,6 +1853,11 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
         CUDA_TRY(c, cudaMemcpyAsync(xp, d_b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         enqueue_bcr_solve(c, xp, st, nullptr);
         CUDA_TRY(c, cudaMemcpyAsync(d_x, xp, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else if (c->cur_prec == 2) {   // double-float factor: n pairs
+        df64* xd = as_df(xp);
+        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xd, nullptr);
+        enqueue_triangular_solves<df64>(c, as_df(c->d_Lx), as_df(c->d_dinv), xd, st, nullptr);
+        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xd, d_x, nullptr);
     } else if (c->cur_prec == 1) {   // FP32 factor: the scratch holds n floats
         float* xp32 = reinterpret_cast<float*>(xp);
         gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, d_b, xp32, nullptr);
@@ -1837,7 +1879,13 @@ kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* v
     if (c->opt.solver == 1) return set_err(c, KKT_ERR_STATE, "the block-tridiagonal factor has no supernodal form");
     const int ns = c->sym.ns();
     std::vector<double> Lh((size_t)c->panel), dv(c->n);
-    if (val && c->cur_prec == 1) {
+    if (val && c->cur_prec == 2) {
+        std::vector<df64> Lf((size_t)c->panel), df(c->n);
+        CUDA_TRY(c, cudaMemcpy(Lf.data(), c->d_Lx, (size_t)c->panel * sizeof(df64), cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(df.data(), c->d_dinv, (size_t)c->n * sizeof(df64), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < Lf.size(); ++i) Lh[i] = (double)Lf[i];
+        for (int i = 0; i < c->n; ++i) dv[i] = (double)df[i];
+    } else if (val && c->cur_prec == 1) {
         std::vector<float> Lf((size_t)c->panel), df(c->n);
         CUDA_TRY(c, cudaMemcpy(Lf.data(), c->d_Lx32, (size_t)c->panel * sizeof(float), cudaMemcpyDeviceToHost));
         CUDA_TRY(c, cudaMemcpy(df.data(), c->d_dinv32, (size_t)c->n * sizeof(float), cudaMemcpyDeviceToHost));

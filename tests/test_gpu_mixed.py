@@ -203,3 +203,62 @@ def test_full_size_mixed_precision_workload(scheme):
     assert s.info.status_detail in (1, 2)
     eta = oracle_eta(p, W, J, pt.sigma, delta_x, dx.cpu().numpy(), dy.cpu().numpy(), pt.rx, pt.ry)
     assert eta <= 1e-10
+
+
+# ---- double-float factor (precision = 2): pairs of FP32 numbers, ~48 bits
+
+@pytest.mark.parametrize("k,T", [(32, 50), (7, 13)])
+def test_df64_factor_matches_oracle(k, T):
+    """The double-float factor agrees with the oracle's FP64 factor to
+    ~1e-13 relative (unit roundoff ~2^-47), and is not the FP64 factor."""
+    p, pt, W, J = instance(k, T, seed=1, sigma_range=(1e-2, 1e2))
+    D = np.full(p.m, 1e2)
+    s, st = _factor(p, pt, W, J, D, 10.0, precision=2)
+    assert st == 0 and s.info.status_detail == 3
+    colptr, rowind, val = s.factor_export()
+    sym, _, ch = _oracle_factor(p, pt, W, J, D, 10.0)
+    worst = 0.0
+    for j in range(p.n):
+        ref = dict(zip(sym.structs[j].tolist(), ch.vals[j].tolist()))
+        scale = max(abs(v) for v in ref.values())
+        for r, v in zip(rowind[colptr[j]:colptr[j + 1]].tolist(), val[colptr[j]:colptr[j + 1]].tolist()):
+            worst = max(worst, abs(v - ref.get(r, 0.0)) / scale)
+    assert worst <= 1e-12, worst
+    assert worst > 1e-16
+
+
+@pytest.mark.parametrize("scheme", ["lifted", "hykkt"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_df64_config1_meets_fp64_bar(scheme, seed):
+    """32 trays, T = 50, Sigma on [1e-6, 1e6], delta = 1e-8 (the case where
+    an FP32 factor falls back): the double-float factor carries the solve to
+    eta <= 1e-10 without falling back; the oracle confirms eta."""
+    torch = torch_cuda()
+    p, pt, W, J = instance(32, 50, seed)
+    s, st = _factor(p, pt, W, J, None, 0.0, precision=2, scheme=scheme, gamma=1e7, max_cg=500)
+    assert st == 0 and s.info.status_detail == 3
+    dx = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
+    st = s.solve(to_dev(torch, pt.rx), to_dev(torch, pt.ry), dx, dy)
+    assert st == 0 and s.info.bwd_err <= 1e-10 and s.info.status_detail == 3
+    assert oracle_eta(p, W, J, pt.sigma, 0.0, dx.cpu().numpy(), dy.cpu().numpy(), pt.rx, pt.ry) <= 1e-10
+
+
+def test_df64_ipm_matches_fp64_ipm():
+    """The device IPM with double-float factors takes the FP64 IPM's
+    iterations to the same optimum (16 trays, T = 40)."""
+    torch_cuda()
+    from gen.tray import TrayParams
+    from paper_2403_15913_gb300 import IPMSolver
+    p = TrayParams(k=16, T=40)
+    out = {}
+    for prec in (0, 2):
+        g = IPMSolver(p.as_array(), scheme="lifted", precision=prec, **OPTS)
+        g.init()
+        h = g.solve()
+        assert h[-1]["status"] == 1
+        out[prec] = (h[-1]["iter"], h[-1]["objective"], g.get()[0].cpu().numpy())
+        g.close()
+    assert abs(out[2][0] - out[0][0]) <= 1
+    assert abs(out[2][1] - out[0][1]) <= 1e-8 * abs(out[0][1])
+    assert np.max(np.abs(out[2][2] - out[0][2])) <= 1e-6

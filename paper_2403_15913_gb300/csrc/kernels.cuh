@@ -22,7 +22,7 @@ constexpr int kThreads = 256;
         if ((active) && *(active) == 0) return; \
     } while (0)
 constexpr int kSubtreeThreads = 64;   // CTA size of the small-subtree kernels
-constexpr int kChunkRows = 2048;  // rows per reduction chunk (one CTA each)
+constexpr int kChunkRows = 512;   // rows per reduction chunk (one CTA each)
 
 // Supernode plan (device pointers).  Panel of supernode s: column-major,
 // rows(s) x cols(s), leading dimension sn_r[s], at Lx + sn_lptr[s].

@@ -38,9 +38,10 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x DFMA/clk/SM x flops x GHz = 125
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FFMA lanes/SM x flops x GHz = 80,548
 METRIC = "KKT solve time per IPM iteration"
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
-# DRAM bytes (read + write) of one numeric factorisation from an ncu capture
-# of the same kernels (profiles/factor_traffic_fp64_tray_T5000.md); keyed by
-# (trays, stages, solver, precision); other configurations report null
+# DRAM bytes of one numeric factorisation (dram__bytes_read.sum +
+# dram__bytes_write.sum of its kernels in one ncu capture of this
+# benchmark), keyed by (trays, stages, solver, precision); other
+# configurations report null
 FACTOR_TRAFFIC = {(32, 5000, "supernodal", "fp64"): 712.2e6}
 DTYPE = {"fp64": "f64", "fp32": "f32 factor + f64 refinement", "df64": "df64 (float-pair) factor + f64 refinement"}
 UNIT = "ms/iter"

@@ -76,6 +76,18 @@ def parse():
     return ap.parse_args()
 
 
+def across_ranks(value, op, dist=None, device="cuda"):
+    """A per-rank scalar combined over the process group: "max" for times
+    (the slowest rank sets the job time), "sum" for throughputs (whole-job
+    aggregate).  Without a group the value itself."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.item()
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -280,10 +292,7 @@ def run_ours(args, ws, rank, local):
     st = nat.Stats()
     nat.lib().kkt_get_stats(kctx, ctypes.byref(st))
     st = st.as_dict()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = across_ranks(ms, "max", dist)
     ipm.set_profiling(False)
 
     # ---- end to end through the public API: whole solves from a host x0
@@ -485,11 +494,7 @@ def run_kkt(args, ws, rank, local):
     ms, infos, st = timed(solver, delta_x, args.steps)
     clk = clocks.stop()
     v = torch.cat([dx, dy]).cpu().numpy()
-    mean_ms = statistics.mean(ms)
-    if dist:
-        t = torch.tensor([mean_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = t.item()
+    mean_ms = across_ranks(statistics.mean(ms), "max", dist)
     fp64_cmp = None
     if prec != 0:
         s64, _ = make(0)
@@ -670,11 +675,7 @@ def run_batch(args, ws, rank, local):
     bs.set_profiling(False)
     st = bs.stats()
     res = bs.results()
-    mean_ms = statistics.mean(ms)
-    if dist:
-        t = torch.tensor([mean_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = t.item()
+    mean_ms = across_ranks(statistics.mean(ms), "max", dist)
     value = args.batch * ws / (mean_ms * 1e-3)
 
     # the plain per-instance FP64 path on the same inputs: one context per
@@ -844,12 +845,7 @@ def run_serve(args, ws, rank, local):
     light = serve(args.slots, prec, rate=light_rate, count=min(args.requests, 200))
     light.pop("clocks")
     light["rate_per_s"] = light_rate
-    if dist:
-        t = torch.tensor([conc["solves_per_s"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        total = t.item()
-    else:
-        total = conc["solves_per_s"]
+    total = across_ranks(conc["solves_per_s"], "sum", dist)
     if rank == 0:
         clk = conc.pop("clocks")
         serial.pop("clocks")

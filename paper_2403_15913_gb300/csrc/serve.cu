@@ -293,10 +293,12 @@ void worker(kkt_server* S, int slot) {
         Client& c2 = S->clients[r.client];
         c2.busy = false;
         c2.last_used = ++S->tick;
-        if (res.status == KKT_CONVERGED || res.status == KKT_OK || res.status == KKT_ERR_MAXIT)
+        if (res.status == KKT_CONVERGED || res.status == KKT_OK || res.status == KKT_ERR_MAXIT) {
             c2.has_prev = true;
-        else
+        } else {
+            c2.has_prev = false;   // its iterate may be unusable: the next request starts cold
             S->failed++;
+        }
         S->completed++;
         S->done[r.id] = res;
         if (r.keep) S->solutions[r.id] = std::move(sol);

@@ -84,6 +84,8 @@ __device__ __forceinline__ bool operator>(df64 x, double v) {
 
 __device__ __forceinline__ bool isfinite(df64 x) { return ::isfinite(x.hi) && ::isfinite(x.lo); }
 
+__device__ __forceinline__ bool pivot_ok(df64 d) { return d > 0.0 && isfinite(d); }
+
 // 1/sqrt(d): FP32 seed (the library reciprocal square root), then two Newton
 // steps y <- y + y (1 - d y^2) / 2 in double-float arithmetic, each roughly
 // doubling the correct bits (~22 -> ~44 -> ~48).

@@ -99,22 +99,39 @@ __device__ __forceinline__ void fast_divmod(int e, int len, float rcp, int& q, i
     else if (rem >= len) { ++q; rem -= len; }
 }
 
-// 1/sqrt(d) by Newton-Raphson for the reciprocal square root,
-// y <- y (3/2 - d y^2 / 2), started from the single-precision estimate:
-// two steps take the ~2^-22 relative error of the seed below double
-// rounding.  Eight FP64 operations instead of a square root and a division,
-// which matters on the column-sequential pivot chain of the factorisation.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
-    const double h = 0.5 * d;
-    y = y * fma(-h * y, y, 1.5);
-    y = y * fma(-h * y, y, 1.5);
-    return y;
+// The pivot is a column-sequential chain, and on GB300 every FP64
+// instruction on it holds the sub-partition's FP64 unit for 64 cycles, so it
+// is kept short: range tests on the bit pattern (integer unit), and the
+// reciprocal square root from the single-precision estimate y0 (relative
+// error ~2^-22) refined by one third-order step of the Householder family:
+// with r = 1 - d y0^2, 1/sqrt(d) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3r^2/8
+// + O(r^3)), truncation ~2^-64 -- five FP64 operations.
+constexpr long long kPivotFastLo = 0x39b4484bfeebc2a0LL;   // bits of 1e-30
+constexpr long long kPivotFastHi = 0x46293e5939a08ceaLL;   // bits of 1e30
+constexpr long long kBitsInf = 0x7ff0000000000000LL;
+
+__device__ __forceinline__ double rsqrt_householder(double d) {
+    const long long b = __double_as_longlong(d);
+    if (!(b > kPivotFastLo && b < kPivotFastHi)) return 1.0 / sqrt(d);
+    const double y0 = (double)rsqrtf((float)d);
+    const double t = d * y0;
+    const double r = fma(-t, y0, 1.0);
+    const double p = fma(0.375, r, 0.5);
+    return fma(y0 * r, p, y0);
 }
 
-__device__ __forceinline__ double pivot_rsqrt(double d) { return rsqrt_newton(d); }
+__device__ __forceinline__ double pivot_rsqrt(double d) { return rsqrt_householder(d); }
 __device__ __forceinline__ float pivot_rsqrt(float d) { return 1.0f / sqrtf(d); }
+
+// positive, finite (and nonzero): a usable pivot
+__device__ __forceinline__ bool pivot_ok(double d) {
+    const long long b = __double_as_longlong(d);
+    return b > 0 && b < kBitsInf;
+}
+__device__ __forceinline__ bool pivot_ok(float d) {
+    const int b = __float_as_int(d);
+    return b > 0 && b < 0x7f800000;
+}
 
 // Where a non-positive pivot is reported: atomic minimum of the failing
 // column into word[0], or into word[inst] when col_inst maps every (permuted)
@@ -127,18 +144,19 @@ struct FailSink {
     }
 };
 
-// Pivot of column j: failure check, L_jj = d / sqrt(d), reciprocal stored
-// for the solves.
+// Pivot of column j: failure check and the reciprocal 1/L_jj, stored for the
+// solves.  L_jj itself is never read again (the trailing updates use the
+// scaled column below it, the solves a unit diagonal and the reciprocals),
+// so the diagonal slot is left as it is.
 template <typename T>
 __device__ __forceinline__ T take_pivot(T* A, int r, int f, int j, FailSink fail,
                                              T* dinv) {
     T d = A[j + (long long)j * r];
-    if (!(d > 0.0) || !isfinite(d)) {
+    if (!pivot_ok(d)) {
         fail.report(f + j);
         d = 1.0;
     }
     const T inv = pivot_rsqrt(d);
-    A[j + (long long)j * r] = d * inv;
     dinv[f + j] = inv;
     return inv;
 }

@@ -1903,8 +1903,9 @@ kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* v
         for (int j = 0; j < cc; ++j) {
             for (int i = j; i < rr; ++i) {
                 if (rowind) rowind[q] = rows[i];
-                // the device keeps Lhat = L diag(1/l); export L
-                if (val) val[q] = Lh[c->h_sn_lptr[s] + (long long)j * rr + i] / dv[f + j];
+                // the device keeps Lhat = L diag(1/l) below the diagonal and
+                // the reciprocals 1/l; export L
+                if (val) val[q] = i == j ? 1.0 / dv[f + j] : Lh[c->h_sn_lptr[s] + (long long)j * rr + i] / dv[f + j];
                 ++q;
             }
             if (colptr) colptr[f + j + 1] = q;

@@ -295,6 +295,51 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) g[(e % c) + (long long)(e / c) * r] = sm[e];
 }
 
+// Warp substitutions with two values per lane (rows lane and lane + 32 of a
+// block of c <= 64 columns).  A warp FP64 instruction costs the same issue
+// slot whatever the number of active lanes, so the loops are split where a
+// half has no work: columns < 32 update both halves (the upper half only
+// when c > 32), columns >= 32 only the upper half; blocks of <= 32 columns
+// never touch the upper half.
+// Unit lower triangular: z := Lhat11^{-1} z, Lhat11(x, j) = D[x + j * ldd].
+template <typename T>
+__device__ __forceinline__ void warp_lower_solve(const T* D, int ldd, int c, int lane, T& z0, T& z1) {
+    const int c0 = min(c, 32);
+    if (c <= 32) {
+        for (int j = 0; j < c0; ++j) {
+            const T zj = __shfl_sync(0xffffffffu, z0, j);
+            if (lane > j && lane < c) z0 = fma(-D[lane + j * ldd], zj, z0);
+        }
+        return;
+    }
+    for (int j = 0; j < 32; ++j) {
+        const T zj = __shfl_sync(0xffffffffu, z0, j);
+        if (lane > j) z0 = fma(-D[lane + j * ldd], zj, z0);
+        if (lane + 32 < c) z1 = fma(-D[lane + 32 + j * ldd], zj, z1);
+    }
+    for (int j = 32; j < c; ++j) {
+        const T zj = __shfl_sync(0xffffffffu, z1, j - 32);
+        if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * ldd], zj, z1);
+    }
+}
+
+// Unit upper triangular with the transpose of Lhat11: t := Lhat11^{-T} t,
+// Lhat11(j, x) = D[j + x * ldd].
+template <typename T>
+__device__ __forceinline__ void warp_upper_solve(const T* D, int ldd, int c, int lane, T& t0, T& t1) {
+    if (c > 32) {
+        for (int j = c - 1; j >= 32; --j) {
+            const T wj = __shfl_sync(0xffffffffu, t1, j - 32);
+            t0 = fma(-D[j + lane * ldd], wj, t0);
+            if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * ldd], wj, t1);
+        }
+    }
+    for (int j = min(c, 32) - 1; j >= 0; --j) {
+        const T wj = __shfl_sync(0xffffffffu, t0, j);
+        if (lane < j) t0 = fma(-D[j + lane * ldd], wj, t0);
+    }
+}
+
 constexpr int kTrsmWarps = 8;   // rows per TRSM CTA (one per warp)
 
 // X L11^T = A21: task = (supernode, first below-row); warp w solves row
@@ -321,11 +366,7 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
     T* row = g + c + i;                       // element k at row[k * r]
     T a0 = lane < c ? row[(long long)lane * r] : 0.0;
     T a1 = lane + 32 < c ? row[(long long)(lane + 32) * r] : 0.0;
-    for (int k = 0; k < c; ++k) {
-        const T ak = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
-        if (lane > k && lane < c) a0 = fma(-ak, D[lane + k * c], a0);
-        if (lane + 32 > k && lane + 32 < c) a1 = fma(-ak, D[lane + 32 + k * c], a1);
-    }
+    warp_lower_solve(D, c, c, lane, a0, a1);   // a := a Lhat11^{-T} in row form
     if (lane < c) row[(long long)lane * r] = a0 * dinv[f + lane];
     if (lane + 32 < c) row[(long long)(lane + 32) * r] = a1 * dinv[f + lane + 32];
 }
@@ -378,11 +419,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
         const int lane = tid;
         T z0 = lane < c ? x[f + lane] : 0.0;
         T z1 = lane + 32 < c ? x[f + lane + 32] : 0.0;
-        for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
-            const T zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
-            if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
-            if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
-        }
+        warp_lower_solve(D, c, c, lane, z0, z1);   // unit lower triangular (normalised factor)
         if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
         if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
     }
@@ -439,11 +476,7 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
         const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
         t0 = lane < c ? x[f + lane] * di0 * di0 - t0 : 0.0;
         t1 = lane + 32 < c ? x[f + lane + 32] * di1 * di1 - t1 : 0.0;
-        for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
-            const T wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
-            if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
-            if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
-        }
+        warp_upper_solve(D, c, c, lane, t0, t1);   // unit upper triangular
         if (lane < c) x[f + lane] = t0;
         if (lane + 32 < c) x[f + lane + 32] = t1;
     }
@@ -506,11 +539,7 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
             const int lane = tid;
             T z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
             T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
-            for (int j = 0; j < c; ++j) {   // unit lower triangular (normalised factor)
-                const T zj = __shfl_sync(0xffffffffu, j < 32 ? z0 : z1, j & 31);
-                if (lane > j && lane < c) z0 = fma(-D[lane + j * c], zj, z0);
-                if (lane + 32 > j && lane + 32 < c) z1 = fma(-D[lane + 32 + j * c], zj, z1);
-            }
+            warp_lower_solve(D, c, c, lane, z0, z1);   // unit lower triangular (normalised factor)
             if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
             if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
         }
@@ -567,11 +596,7 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
             const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
             t0 = lane < c ? __ldcg(x + f + lane) * di0 * di0 - t0 : 0.0;
             t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) * di1 * di1 - t1 : 0.0;
-            for (int j = c - 1; j >= 0; --j) {   // unit upper triangular
-                const T wj = __shfl_sync(0xffffffffu, j < 32 ? t0 : t1, j & 31);
-                if (lane < j) t0 = fma(-D[j + lane * c], wj, t0);
-                if (lane + 32 < j) t1 = fma(-D[j + (lane + 32) * c], wj, t1);
-            }
+            warp_upper_solve(D, c, c, lane, t0, t1);   // unit upper triangular
             if (lane < c) x[f + lane] = t0;
             if (lane + 32 < c) x[f + lane + 32] = t1;
         }

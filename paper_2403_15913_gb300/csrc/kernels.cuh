@@ -292,6 +292,13 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
     __syncthreads();
     panel_factor(sm, f, c, c, c, fail, dinv);
+    // the unused upper triangle receives the transpose of L11 diag(dinv)
+    // (column-scaled by the reciprocal pivots), once, for the TRSM CTAs
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+        const int row = e % c, col = e / c;
+        if (row > col) sm[col + row * c] = sm[e] * dinv[f + col];
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) g[(e % c) + (long long)(e / c) * r] = sm[e];
 }
 
@@ -344,7 +351,8 @@ constexpr int kTrsmWarps = 8;   // rows per TRSM CTA (one per warp)
 
 // X L11^T = A21: task = (supernode, first below-row); warp w solves row
 // task.y + w with lanes over the columns (two per lane).  The columns of L11
-// are pre-scaled by the reciprocal pivots, so a step is one shuffle and one
+// come pre-scaled by the reciprocal pivots (the diagonal-block kernel leaves
+// them transposed in the upper triangle), so a step is one shuffle and one
 // FMA: a_l -= a_k (L_lk / L_kk); the final x_k = a_k / L_kk is one multiply.
 template <typename T>
 __global__ void __launch_bounds__(32 * kTrsmWarps)
@@ -355,10 +363,8 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
     const int s = task.x;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     T* g = Lx + P.sn_lptr[s];
-    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
-        const int col = e / c;
-        D[e] = g[(e % c) + (long long)col * r] * dinv[f + col];
-    }
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x)   // L11(row, col) dinv(col), row > col,
+        D[e] = g[e / c + (long long)(e % c) * r];            // stored transposed above the diagonal
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = task.y + warp;

@@ -280,6 +280,39 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
 // Levels with few supernodes run in three launches spread over many CTAs:
 // (1) POTRF of each diagonal block, (2) TRSM of the rows below, one row per
 // warp, (3) SYRK tiles, one tile per warp.
+// Cholesky of a square c x c block (c <= 64) in shared memory.  The trailing
+// update runs over the lower triangle only, through a table of its (row,
+// column) pairs ordered by column descending: the pairs still active at step
+// j (column > j) are then the first (c-1-j)(c-j)/2 entries, so every lane of
+// every FP64 warp instruction has work.
+template <typename T>
+__device__ __forceinline__ void square_factor(T* A, int f, int c, FailSink fail, T* dinv) {
+    __shared__ T s_inv[2];
+    __shared__ short2 tab[64 * 63 / 2];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < c * c; e += nt) {
+        const int ii = e % c, kk = e / c;
+        if (kk >= 1 && ii >= kk) tab[(c - 1 - kk) * (c - kk) / 2 + (ii - kk)] = make_short2((short)ii, (short)kk);
+    }
+    if (tid == 0) s_inv[0] = take_pivot(A, c, f, 0, fail, dinv);
+    __syncthreads();
+    for (int j = 0; j < c; ++j) {
+        const T inv = s_inv[j & 1];
+        T* colj = A + (long long)j * c;
+        for (int i = j + 1 + tid; i < c; i += nt) colj[i] *= inv;
+        __syncthreads();
+        const int active = (c - 1 - j) * (c - j) / 2;
+        for (int e = tid; e < active; e += nt) {
+            const short2 pr = tab[e];
+            const int ii = pr.x, kk = pr.y;
+            T* p = A + ii + kk * c;
+            *p = fma(-colj[ii], colj[kk], *p);
+            if (ii == j + 1 && kk == j + 1) s_inv[(j + 1) & 1] = take_pivot(A, c, f, j + 1, fail, dinv);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
@@ -291,7 +324,7 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
     __syncthreads();
-    panel_factor(sm, f, c, c, c, fail, dinv);
+    square_factor(sm, f, c, fail, dinv);
     // the unused upper triangle receives the transpose of L11 diag(dinv)
     // (column-scaled by the reciprocal pivots), once, for the TRSM CTAs
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) {

@@ -132,6 +132,9 @@ struct kkt_ctx {
     // per-instance results of the last factor / solve
     std::vector<int> r_status, r_refine, r_cg, r_fail;
     std::vector<double> r_eta;
+    // side stream: ||K_orig||_inf is computed while the factorisation runs
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_side = nullptr;
     // block cyclic reduction (opt.solver == 1): N blocks of b variables;
     // level l eliminates bcr_elim[elim_ptr[l] ..] then updates the survivors
     // bcr_surv[surv_ptr[l] ..]; the last level eliminates the root alone
@@ -1211,6 +1214,10 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     if (device) {
         kkt_status st = build_plan(c, W_colptr, W_rowind, J_rowptr, J_colind);
         if (st == KKT_OK && c->opt.solver == 1) st = build_bcr(c, W_colptr, W_rowind, J_rowptr, J_colind);
+        if (st == KKT_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming) != cudaSuccess))
+            st = set_err(c, KKT_ERR_CUDA, "side stream or events could not be created");
         if (st != KKT_OK) {
             set_err(nullptr, st, c->err);
             kkt_destroy(c);
@@ -1582,6 +1589,19 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
             if (c->h_int[i] != kNoFail) return true;
         return false;
     };
+    // ||K_orig,i||_inf (and the dual block C of the relaxed target) on the side
+    // stream, overlapping the factorisation, which does not read them
+    CUDA_TRY(c, cudaEventRecord(c->ev_in, st));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_in, 0));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), c->side));
+    if (c->f_C) {
+        if (c->f_D) recip_kernel<<<grid_for(m), kThreads, 0, c->side>>>(m, c->f_D, c->d_Cbuf.p);
+        else fill_kernel<<<grid_for(m), kThreads, 0, c->side>>>(m, c->opt.delta, c->d_Cbuf.p);
+    }
+    knorm_kernel<<<c->nch_xy, kThreads, 0, c->side>>>(c->d_ch_xy, c->n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx,
+                                                      c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx, c->f_J,
+                                                      c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C, c->d_knorm);
+    CUDA_TRY(c, cudaEventRecord(c->ev_side, c->side));
     // detail: 0 FP64, 1 FP32, 2 FP64 after a failed reduced-precision
     // factor, 3 double-float
     int detail = 0;
@@ -1612,15 +1632,7 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
         c->cur_prec = 0;
     }
     const bool reduced_ok = detail == 1 || detail == 3;
-    // ||K_orig,i||_inf
-    CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), st));
-    if (c->f_C) {
-        if (c->f_D) recip_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->f_D, c->d_Cbuf.p);
-        else fill_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->opt.delta, c->d_Cbuf.p);
-    }
-    knorm_kernel<<<c->nch_xy, kThreads, 0, st>>>(c->d_ch_xy, c->n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx,
-                                                 c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx, c->f_J,
-                                                 c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C, c->d_knorm);
+    CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev_side, 0));   // ||K_orig,i||_inf done on the side stream
     CUDA_TRY(c, cudaMemcpyAsync(c->h_red, c->d_knorm, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (reduced_ok) {
         CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1951,6 +1963,9 @@ void kkt_destroy(kkt_ctx* c) {
     if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
     if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
     if (c->h_cg) cudaFreeHost(c->h_cg);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_side) cudaEventDestroy(c->ev_side);
+    if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);

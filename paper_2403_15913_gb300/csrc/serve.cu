@@ -19,9 +19,7 @@
 // wait while resident clients proceed.  A context larger than the whole
 // budget is admitted only when nothing else is resident.
 #include <algorithm>
-#include <atomic>
 #include <chrono>
-#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -77,7 +75,6 @@ struct kkt_server {
     long long created = 0, evicted = 0, completed = 0, failed = 0;
     std::map<int, double> bytes_per_var;   // learned footprint per tray count
     std::vector<std::thread> workers;
-    std::string err;
     // evicted contexts and their solution buffers, freed outside the lock
     std::vector<std::pair<kkt_ipm*, double*>> graveyard;
 

@@ -262,9 +262,9 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
         __syncthreads();
     }
     panel_factor(A, f, c, r, r, fail, dinv);
-    if (in_smem) {
+    if (in_smem) {   // written back normalised (Lhat = L diag(dinv)); the SYRK below reads the smem copy
         T* g = Lx + lp;
-        for (long long e = tid; e < (long long)r * c; e += nt) g[e] = A[e];
+        for (long long e = tid; e < (long long)r * c; e += nt) g[e] = A[e] * dinv[f + (int)(e / r)];
     }
     const int rb = r - c;
     if (rb <= 0) return;
@@ -427,8 +427,10 @@ syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, T* __restri
 // Lhat^T w = u / l^2.  One CTA per supernode.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-normalize_panels_kernel(Plan P, int ns, T* __restrict__ Lx, const T* __restrict__ dinv) {
-    for (int s = blockIdx.x; s < ns; s += gridDim.x) {
+normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __restrict__ Lx,
+                        const T* __restrict__ dinv) {
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const int s = list[q];
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         T* A = Lx + P.sn_lptr[s];
         for (int e = threadIdx.x; e < r * c; e += blockDim.x) A[e] *= dinv[f + e / r];
@@ -541,7 +543,8 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
         for (int e = tid; e < r * c; e += nt) sm[e] = __ldcg(g + e);
         __syncthreads();
         panel_factor(sm, f, c, r, r, fail, dinv);
-        for (int e = tid; e < r * c; e += nt) g[e] = sm[e];
+        // written back normalised (Lhat = L diag(dinv)); the SYRK below reads the smem copy
+        for (int e = tid; e < r * c; e += nt) g[e] = sm[e] * dinv[f + e / r];
         const int rb = r - c;
         if (rb > 0) {
             const int nti = syrk_tiles_i(rb), ntj = syrk_tiles_j(rb);

@@ -60,6 +60,8 @@ struct kkt_ctx {
     int ntasks = 0;
     int* d_task_ptr = nullptr;
     int* d_task_sn = nullptr;
+    int n_norm = 0;               // supernodes normalised after the factorisation
+    int* d_norm_list = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
     // device allocations (all freed in kkt_destroy) and their total size
     std::vector<void*> allocs;
@@ -570,6 +572,20 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         }
         c->lvl_trsm_ptr[l + 1] = (int)trsm_tasks.size();
         c->lvl_syrk_ptr[l + 1] = (int)syrk_tasks.size();
+    }
+
+    // ---- supernodes whose panels the factor kernels do not write back
+    // normalised (split narrow levels, panels too large for shared memory):
+    // the normalisation pass after the factorisation covers only these
+    {
+        std::vector<int> norm_list;
+        for (int s = 0; s < ns; ++s) {
+            if (in_task[s]) continue;
+            const bool fused_smem = !c->lvl_split[level[s]] && (long long)sn_r[s] * sn_c[s] <= kSmemCapElems;
+            if (!fused_smem) norm_list.push_back(s);
+        }
+        c->n_norm = (int)norm_list.size();
+        TRY(upload(c, &c->d_norm_list, norm_list));
     }
 
     // ---- SpMV structures (original labels)
@@ -1125,9 +1141,11 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
                 c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, Lx);
         c->stats.launches += 2;
     }
-    normalize_panels_kernel<T><<<std::min(c->sym.ns(), 152 * 16), kThreads, 0, st>>>(
-        c->plan, c->sym.ns(), Lx, dinv);
-    c->stats.launches += 1;
+    if (c->n_norm > 0) {
+        normalize_panels_kernel<T><<<std::min(c->n_norm, 152 * 16), kThreads, 0, st>>>(
+            c->plan, c->d_norm_list, c->n_norm, Lx, dinv);
+        c->stats.launches += 1;
+    }
     span_end(c, sp_f, st);
     CUDA_TRY(c, cudaGetLastError());
     return KKT_OK;

@@ -107,6 +107,10 @@ __device__ __forceinline__ df64 __shfl_down_sync(unsigned mask, df64 v, unsigned
     return df64(::__shfl_down_sync(mask, v.hi, delta), ::__shfl_down_sync(mask, v.lo, delta));
 }
 
+__device__ __forceinline__ df64 __shfl_xor_sync(unsigned mask, df64 v, int lanemask) {
+    return df64(::__shfl_xor_sync(mask, v.hi, lanemask), ::__shfl_xor_sync(mask, v.lo, lanemask));
+}
+
 __device__ __forceinline__ df64 __ldcg(const df64* p) {
     const float2 f = ::__ldcg(reinterpret_cast<const float2*>(p));
     return df64(f.x, f.y);

@@ -438,10 +438,55 @@ normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __re
 }
 
 // ------------------------------------------------------------- solves
+// x[rows below] -= Lhat21 u: lanes over 32 consecutive rows (coalesced
+// loads), the warps given to a row block split its columns, and their partial
+// sums meet in shared memory.  Each thread's column loads are issued in
+// batches of eight, so a batch costs one memory latency and the dependent
+// FMA chain per thread is c / (warps per row block) long, not c.
+template <typename T>
+__device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, int r,
+                                              const T* __restrict__ u, const int* __restrict__ rows,
+                                              T* __restrict__ x, T (*part)[32]) {
+    const int tid = threadIdx.x, nw = blockDim.x >> 5, warp = tid >> 5, lane = tid & 31;
+    const int rb = r - c;
+    for (int i0 = 0; i0 < rb; i0 += 32 * nw) {
+        const int nrb = min(nw, (rb - i0 + 31) >> 5);   // row blocks in this pass
+        const int wpr = nw / nrb;                        // warps per row block
+        const int blk = warp % nrb, q = warp / nrb;
+        const int i = i0 + 32 * blk + lane;
+        T sum = 0.0;
+        if (q < wpr && i < rb) {
+            const T* a = A + c + i;
+            for (int k0 = q; k0 < c; k0 += 8 * wpr) {
+                T v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k = k0 + j * wpr;
+                    v[j] = k < c ? a[(long long)k * r] : T(0.0);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k = k0 + j * wpr;
+                    if (k < c) sum = fma(v[j], u[k], sum);
+                }
+            }
+        }
+        part[warp][lane] = sum;
+        __syncthreads();
+        if (tid < 32 * nrb && i0 + tid < rb) {
+            const int b = tid >> 5;
+            T t = part[b][lane];
+            for (int qq = 1; qq < wpr; ++qq) t += part[b + qq * nrb][lane];
+            atomicAdd(x + rows[c + i0 + tid], -t);
+        }
+        __syncthreads();
+    }
+}
+
 // Forward substitution L z = b, one CTA per supernode of a level: the
 // diagonal block in shared memory, one warp substitutes with shuffles
-// (reciprocal pivots from the factorisation), then one thread per row of
-// L21 forms its product with z and scatters it.
+// (unit diagonal; the reciprocal pivots are applied in the backward pass),
+// then all warps form Lhat21 u and scatter it.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
@@ -450,6 +495,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
     KKT_RETURN_IF_INACTIVE(active);
     __shared__ T D[64 * 64];
     __shared__ T z[64];
+    __shared__ T part[kThreads / 32][32];
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const T* A = Lx + P.sn_lptr[s];
@@ -465,12 +511,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
         if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
     }
     __syncthreads();
-    const int* rows = P.rows + P.sn_rptr[s];
-    for (int i = tid; i < r - c; i += nt) {
-        T sum = 0.0;
-        for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
-        atomicAdd(x + rows[c + i], -sum);
-    }
+    scatter_below(A, c, r, z, P.rows + P.sn_rptr[s], x, part);
 }
 
 // Backward substitution L^T w = z, one CTA per supernode of a level
@@ -621,10 +662,38 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
         for (int i = tid; i < rb; i += nt) xb[i] = __ldcg(x + rows[c + i]);
         __syncthreads();
+        if (c <= 32) {
+            // narrow supernode: a warp instruction covers 32 / cp rows (lane =
+            // row group g, column k < cp), so few FP64 issue slots go to idle
+            // lanes; the row groups are summed with butterfly shuffles
+            const int cp = c == 1 ? 1 : 1 << (32 - __clz(c - 1));
+            const int k = lane & (cp - 1), G = 32 / cp;
+            T s0 = 0.0;
+            if (k < c)
+                for (int i = warp * G + lane / cp; i < rb; i += nw * G)
+                    s0 = fma(A[c + i + (long long)k * r], xb[i], s0);
+            for (int off = cp; off < 32; off <<= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+            if (lane < cp) part[warp][lane] = s0;
+            __syncthreads();
+            if (tid < 32) {
+                T t0 = 0.0, t1 = 0.0;
+                if (lane < c) {
+                    t0 = part[0][lane];
+                    for (int w = 1; w < nw; ++w) t0 += part[w][lane];
+                    const T di = dinv[f + lane];
+                    t0 = fma(__ldcg(x + f + lane) * di, di, -t0);   // u / l^2 - L21^T w
+                }
+                warp_upper_solve(D, c, c, lane, t0, t1);
+                if (lane < c) x[f + lane] = t0;
+            }
+            __threadfence();
+            __syncthreads();
+            continue;
+        }
         T s0 = 0.0, s1 = 0.0;
         for (int i = warp; i < rb; i += nw) {
             const T xv = xb[i];
-            if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
+            s0 = fma(A[c + i + (long long)lane * r], xv, s0);
             if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
         }
         part[warp][lane] = s0;

@@ -19,10 +19,13 @@
 #include <utility>
 #include <vector>
 
+#include "fp64_lean.cuh"
 #include "kkt.h"
 #include "tray_internal.h"
 
 namespace {
+
+using kktgb::rcp_pos;
 
 constexpr int kT = 256;
 constexpr int kRB = 296;            // CTAs of the reduction kernels (fixed: deterministic sums)
@@ -98,6 +101,18 @@ struct LogSum {
     __device__ __forceinline__ double value() const {
         return log(mant) + (double)expo * 0.69314718055994530942;
     }
+};
+
+// Running minimum of ratios a / b (a >= 0, b > 0) compared by cross products
+// (a b' < a' b), divided once at the end: a division costs several FP64
+// instructions, a comparison by products two multiplies.  The minimum is the
+// same rounded quotient a / b of the selected pair.
+struct MinRatio {
+    double a = 1.0, b = 1.0;
+    __device__ __forceinline__ void add(double na, double nb) {
+        if (na * b < a * nb) { a = na; b = nb; }
+    }
+    __device__ __forceinline__ double value() const { return a / b; }
 };
 
 struct Bounds {
@@ -178,17 +193,17 @@ __global__ void prepare_kernel(int n, int m, int relaxed, Bounds B, double mu,
                                double* __restrict__ ry, double* __restrict__ D) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
-            const double igl = 1.0 / (x[i] - B.xlo[i]), igu = 1.0 / (B.xhi[i] - x[i]);
+            const double igl = rcp_pos(x[i] - B.xlo[i]), igu = rcp_pos(B.xhi[i] - x[i]);
             sigma[i] = zl[i] * igl + zu[i] * igu;
             rx[i] = -(grad[i] - mu * igl + mu * igu + jty[i]);
         } else {
             const int k = i - n;
             if (relaxed) {
-                const double ihl = 1.0 / (s[k] + B.tau), ihu = 1.0 / (B.tau - s[k]);
+                const double ihl = rcp_pos(s[k] + B.tau), ihu = rcp_pos(B.tau - s[k]);
                 const double sig = vl[k] * ihl + vu[k] * ihu;
                 const double gphi = -mu * ihl + mu * ihu;
                 D[k] = sig;
-                ry[k] = -(c[k] - s[k]) - (gphi - y[k]) / sig;
+                ry[k] = -(c[k] - s[k]) - (gphi - y[k]) * rcp_pos(sig);
             } else {
                 ry[k] = -c[k];
             }
@@ -209,39 +224,42 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
                double* __restrict__ dvl, double* __restrict__ dvu, double* __restrict__ part) {
     double v[3] = {1.0, 1.0, 0.0};
     const int ops[3] = {MIN, MIN, SUM};
+    MinRatio apr, adu;   // tau gap / |step| over the blocking steps
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
             const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
-            const double igl = 1.0 / gl, igu = 1.0 / gu;
+            const double igl = rcp_pos(gl), igu = rcp_pos(gu);
             const double d = dx[i];
             const double a = mu * igl - zl[i] - (zl[i] * igl) * d;
             const double b = mu * igu - zu[i] + (zu[i] * igu) * d;
             dzl[i] = a;
             dzu[i] = b;
-            if (d < 0) v[0] = fmin(v[0], -tau * gl / d);
-            if (d > 0) v[0] = fmin(v[0], tau * gu / d);
-            if (a < 0) v[1] = fmin(v[1], -tau * zl[i] / a);
-            if (b < 0) v[1] = fmin(v[1], -tau * zu[i] / b);
+            if (d < 0) apr.add(tau * gl, -d);
+            if (d > 0) apr.add(tau * gu, d);
+            if (a < 0) adu.add(tau * zl[i], -a);
+            if (b < 0) adu.add(tau * zu[i], -b);
             v[2] += (grad[i] - mu * igl + mu * igu) * d;
         } else if (relaxed) {
             const int k = i - n;
             const double hl = s[k] + B.tau, hu = B.tau - s[k];
-            const double ihl = 1.0 / hl, ihu = 1.0 / hu;
+            const double ihl = rcp_pos(hl), ihu = rcp_pos(hu);
             const double sig = vl[k] * ihl + vu[k] * ihu;
             const double gphi = -mu * ihl + mu * ihu;
-            const double d = (dy[k] - gphi + y[k]) / sig;
+            const double d = (dy[k] - gphi + y[k]) * rcp_pos(sig);
             ds[k] = d;
             const double a = mu * ihl - vl[k] - (vl[k] * ihl) * d;
             const double b = mu * ihu - vu[k] + (vu[k] * ihu) * d;
             dvl[k] = a;
             dvu[k] = b;
-            if (d < 0) v[0] = fmin(v[0], -tau * hl / d);
-            if (d > 0) v[0] = fmin(v[0], tau * hu / d);
-            if (a < 0) v[1] = fmin(v[1], -tau * vl[k] / a);
-            if (b < 0) v[1] = fmin(v[1], -tau * vu[k] / b);
+            if (d < 0) apr.add(tau * hl, -d);
+            if (d > 0) apr.add(tau * hu, d);
+            if (a < 0) adu.add(tau * vl[k], -a);
+            if (b < 0) adu.add(tau * vu[k], -b);
             v[2] += gphi * d;
         }
     }
+    v[0] = apr.value();
+    v[1] = adu.value();
     store_partials<3>(v, ops, part);
 }
 
@@ -292,7 +310,7 @@ __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, do
         if (i < n) {
             const double xn = x[i] + alpha * dx[i];
             x[i] = xn;
-            const double igl = 1.0 / (xn - B.xlo[i]), igu = 1.0 / (B.xhi[i] - xn);
+            const double igl = rcp_pos(xn - B.xlo[i]), igu = rcp_pos(B.xhi[i] - xn);
             const double a = zl[i] + alpha_du * dzl[i], b = zu[i] + alpha_du * dzu[i];
             zl[i] = fmax(fmin(a, k * mu * igl), (mu / k) * igl);
             zu[i] = fmax(fmin(b, k * mu * igu), (mu / k) * igu);
@@ -302,7 +320,7 @@ __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, do
             if (relaxed) {
                 const double sn = s[q] + alpha * ds[q];
                 s[q] = sn;
-                const double ihl = 1.0 / (sn + B.tau), ihu = 1.0 / (B.tau - sn);
+                const double ihl = rcp_pos(sn + B.tau), ihu = rcp_pos(B.tau - sn);
                 const double a = vl[q] + alpha_du * dvl[q], b = vu[q] + alpha_du * dvu[q];
                 vl[q] = fmax(fmin(a, k * mu * ihl), (mu / k) * ihl);
                 vu[q] = fmax(fmin(b, k * mu * ihu), (mu / k) * ihu);

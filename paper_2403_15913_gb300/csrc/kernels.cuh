@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "fp64_lean.cuh"
+
 namespace kktgb {
 
 constexpr int kThreads = 256;
@@ -45,12 +47,15 @@ struct Plan {
 // ------------------------------------------------------------- assembly
 // Js = J scaled row-wise by sqrt(D) (D > 0 in both schemes), so that every
 // J^T D J product of the assembly is one FMA: D_r J_ra J_rb = Js_a Js_b.
-__global__ void scale_rows_sqrt_kernel(int nnz, const int* __restrict__ jrow,
+// One thread per row of J (CSR): one square root per row, not per entry.
+__global__ void scale_rows_sqrt_kernel(int m, const int* __restrict__ jp,
                                        const double* __restrict__ J, const double* __restrict__ D,
                                        double Dconst, double* __restrict__ Js) {
     const double sc = sqrt(Dconst);
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x)
-        Js[q] = J[q] * (D ? sqrt(D[jrow[q]]) : sc);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const double sr = D ? sqrt(D[r]) : sc;
+        for (int q = jp[r]; q < jp[r + 1]; ++q) Js[q] = J[q] * sr;
+    }
 }
 
 // One thread per stored entry of the lower triangle of P K P^T: sums its
@@ -103,17 +108,13 @@ __device__ __forceinline__ void fast_divmod(int e, int len, float rcp, int& q, i
 // instruction on it holds the sub-partition's FP64 unit for 64 cycles, so it
 // is kept short: range tests on the bit pattern (integer unit), and the
 // reciprocal square root from the single-precision estimate y0 (relative
-// error ~2^-22) refined by one third-order step of the Householder family:
-// with r = 1 - d y0^2, 1/sqrt(d) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3r^2/8
-// + O(r^3)), truncation ~2^-64 -- five FP64 operations.
-constexpr long long kPivotFastLo = 0x39b4484bfeebc2a0LL;   // bits of 1e-30
-constexpr long long kPivotFastHi = 0x46293e5939a08ceaLL;   // bits of 1e30
-constexpr long long kBitsInf = 0x7ff0000000000000LL;
-
+// error below 2^-21, the conversions done on the bit patterns) refined by
+// one third-order step of the Householder family: with r = 1 - d y0^2,
+// 1/sqrt(d) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3r^2/8 + O(r^3)),
+// truncation below 2^-60 -- five FP64 operations.
 __device__ __forceinline__ double rsqrt_householder(double d) {
-    const long long b = __double_as_longlong(d);
-    if (!(b > kPivotFastLo && b < kPivotFastHi)) return 1.0 / sqrt(d);
-    const double y0 = (double)rsqrtf((float)d);
+    if (!lean_range(d)) return 1.0 / sqrt(d);
+    const double y0 = f64_of(rsqrtf(f32_of(d)));   // conversions on the integer units
     const double t = d * y0;
     const double r = fma(-t, y0, 1.0);
     const double p = fma(0.375, r, 0.5);
@@ -122,6 +123,8 @@ __device__ __forceinline__ double rsqrt_householder(double d) {
 
 __device__ __forceinline__ double pivot_rsqrt(double d) { return rsqrt_householder(d); }
 __device__ __forceinline__ float pivot_rsqrt(float d) { return 1.0f / sqrtf(d); }
+
+constexpr long long kBitsInf = 0x7ff0000000000000LL;
 
 // positive, finite (and nonzero): a usable pivot
 __device__ __forceinline__ bool pivot_ok(double d) {
@@ -541,23 +544,34 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
     // warp w sums rows i = w, w + nw, ... for columns k = lane, lane + 32
     {
         T s0 = 0.0, s1 = 0.0;
-        for (int i = warp; i < rb; i += nw) {
-            const T xv = xb[i];
-            if (lane < c) s0 = fma(A[c + i + (long long)lane * r], xv, s0);
-            if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
+        if (c > 32) {
+            for (int i = warp; i < rb; i += nw) {
+                const T xv = xb[i];
+                s0 = fma(A[c + i + (long long)lane * r], xv, s0);
+                if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
+            }
+        } else if (lane < c) {
+            for (int i = warp; i < rb; i += nw) s0 = fma(A[c + i + (long long)lane * r], xb[i], s0);
         }
         part[warp][lane] = s0;
         part[warp][lane + 32] = s1;
     }
     __syncthreads();
     if (tid < 32) {
-        T t0 = 0.0, t1 = 0.0;
-        for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
         // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
-        const T di0 = lane < c ? dinv[f + lane] : 0.0;
-        const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-        t0 = lane < c ? x[f + lane] * di0 * di0 - t0 : 0.0;
-        t1 = lane + 32 < c ? x[f + lane + 32] * di1 * di1 - t1 : 0.0;
+        T t0 = 0.0, t1 = 0.0;
+        if (lane < c) {
+            t0 = part[0][lane];
+            for (int w = 1; w < nw; ++w) t0 += part[w][lane];
+            const T di = dinv[f + lane];
+            t0 = fma(x[f + lane] * di, di, -t0);
+        }
+        if (lane + 32 < c) {   // second half only for supernodes wider than a warp
+            t1 = part[0][lane + 32];
+            for (int w = 1; w < nw; ++w) t1 += part[w][lane + 32];
+            const T di = dinv[f + lane + 32];
+            t1 = fma(x[f + lane + 32] * di, di, -t1);
+        }
         warp_upper_solve(D, c, c, lane, t0, t1);   // unit upper triangular
         if (lane < c) x[f + lane] = t0;
         if (lane + 32 < c) x[f + lane + 32] = t1;

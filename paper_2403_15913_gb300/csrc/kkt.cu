@@ -71,7 +71,6 @@ struct kkt_ctx {
     int *d_perm = nullptr, *d_iperm = nullptr;
     long long *d_k_slot = nullptr, *d_k_sptr = nullptr;
     int2* d_k_src = nullptr;
-    int* d_jrow = nullptr;
     int *d_wf_ptr = nullptr, *d_wf_col = nullptr, *d_wf_idx = nullptr;
     int *d_j_ptr = nullptr, *d_j_col = nullptr;
     int *d_jt_ptr = nullptr, *d_jt_row = nullptr, *d_jt_idx = nullptr;
@@ -397,10 +396,8 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             raw.push_back({std::max(a, b), std::min(a, b), p, -1});
         }
     for (int v = 0; v < n; ++v) raw.push_back({S.iperm[v], S.iperm[v], v, -2});
-    std::vector<int> jrow(std::max(1, J_rowptr[m]));
     for (int r = 0; r < m; ++r)
         for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p) {
-            jrow[p] = r;
             for (int q = p; q < J_rowptr[r + 1]; ++q) {
                 int a = S.iperm[J_colind[p]], b = S.iperm[J_colind[q]];
                 raw.push_back({std::max(a, b), std::min(a, b), p, q});
@@ -747,7 +744,6 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(upload(c, &c->d_k_slot, k_slot));
     TRY(upload(c, &c->d_k_sptr, k_sptr));
     TRY(upload(c, &c->d_k_src, k_src));
-    TRY(upload(c, &c->d_jrow, jrow));
     TRY(upload(c, &c->d_wf_ptr, wf_ptr));
     TRY(upload(c, &c->d_wf_col, wf_col));
     TRY(upload(c, &c->d_wf_idx, wf_idx));
@@ -1594,8 +1590,8 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
     const int m = c->m;
     const int sp_a = span_begin(c, 0, st);
     if (c->nnzJ > 0)
-        scale_rows_sqrt_kernel<<<grid_for(c->nnzJ), kThreads, 0, st>>>(c->nnzJ, c->d_jrow, c->f_J, c->f_D,
-                                                                       c->f_Dconst, c->v_Js);
+        scale_rows_sqrt_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->f_J, c->f_D,
+                                                                 c->f_Dconst, c->v_Js);
     span_end(c, sp_a, st);
     auto fetch_fail = [&]() -> kkt_status {
         CUDA_TRY(c, cudaMemcpyAsync(c->h_int, c->d_fail, (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <string>
 
+#include "fp64_lean.cuh"
 #include "kkt.h"
 #include "tray_internal.h"
 
@@ -25,6 +26,7 @@ namespace {
 struct TrayP {
     int k, T;
     double h, alpha, D, F, xf, M, xbar, ubar, rho, x0bar;
+    double hm;   // h / M, formed once on the host
     __host__ __device__ int feed() const { return k / 2; }
     __host__ __device__ int nst() const { return 2 * k + 1; }
 };
@@ -44,6 +46,7 @@ bool unpack(const double* p, TrayP& q) {
     q.ubar = p[9];
     q.rho = p[10];
     q.x0bar = p[11];
+    q.hm = q.h / q.M;
     if ((double)q.k != p[0] || (double)q.T != p[1]) return false;
     double n = (2.0 * q.k + 1) * (q.T + 1);
     return n < 2e9;
@@ -69,9 +72,10 @@ __global__ void tray_eval_kernel(TrayP P, const double* __restrict__ x0v, const 
         const double u = w[base + 2 * k];
         const double x = xt[i];
         const double den = 1.0 + (P.alpha - 1.0) * x;
-        const double phi = P.alpha * x / den;
-        const double dphi = P.alpha / (den * den);
-        const double d2phi = -2.0 * P.alpha * (P.alpha - 1.0) / (den * den * den);
+        const double rden = kktgb::rcp_pos(den);   // one reciprocal for phi and its derivatives
+        const double phi = P.alpha * x * rden;
+        const double dphi = P.alpha * rden * rden;
+        const double d2phi = -2.0 * P.alpha * (P.alpha - 1.0) * (rden * rden * rden);
         const long long crow_dyn = (long long)t * 2 * k + i;
         const long long crow_eq = crow_dyn + k;
         if (grad) {
@@ -80,7 +84,7 @@ __global__ void tray_eval_kernel(TrayP P, const double* __restrict__ x0v, const 
             if (i == 0) grad[base + 2 * k] = 2.0 * P.rho * (u - P.ubar);
         }
         const double Lf = u * P.D, Vf = Lf + P.D, Sf = P.F + Lf;
-        const double hm = P.h / P.M;
+        const double hm = P.hm;
         const int kf = P.feed();
         // partials of g_i (same stage): dxm = d/dx_{i-1}, dx = d/dx_i,
         // dy = d/dy_i, dyp = d/dy_{i+1}, du = d/du

@@ -241,6 +241,33 @@ __device__ __forceinline__ void syrk_tile(const Plan& P, int s, int c, int r, co
     }
 }
 
+// SYRK of the rows below the diagonal block, L21 L21^T, over the packed
+// lower triangle: thread -> outputs p = tid, tid + nt, ... with p = ii (ii +
+// 1) / 2 + jj (row by row, jj <= ii), so every lane of a warp has an output
+// (8 x 4 tiles leave the lanes above the diagonal idle, a third of them when
+// rb is small).  The pair is decoded with an FP32 square root and an integer
+// correction; each output is then the same c-term FMA chain as a tile lane's.
+template <typename T>
+__device__ __forceinline__ void syrk_packed(const Plan& P, int s, int c, int r, const T* A, T* Lx) {
+    const int rb = r - c;
+    const int npairs = rb * (rb + 1) / 2;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        int ii = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+        while (ii * (ii + 1) / 2 > p) --ii;
+        while ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
+        const int jj = p - ii * (ii + 1) / 2;
+        const T* ai = A + c + ii;
+        const T* aj = A + c + jj;
+        T sum = 0.0;
+        for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * r], aj[(long long)k * r], sum);
+        long long base;
+        const int* rm;
+        int a;
+        update_target(P, s, c, jj, base, rm, a);
+        atomicAdd(Lx + base + rm[ii - a], -sum);
+    }
+}
+
 __device__ __forceinline__ int syrk_tiles_i(int rb) { return (rb + kTileI - 1) / kTileI; }
 __device__ __forceinline__ int syrk_tiles_j(int rb) { return (rb + kTileJ - 1) / kTileJ; }
 
@@ -269,15 +296,7 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
         T* g = Lx + lp;
         for (long long e = tid; e < (long long)r * c; e += nt) g[e] = A[e] * dinv[f + (int)(e / r)];
     }
-    const int rb = r - c;
-    if (rb <= 0) return;
-    const int nti = syrk_tiles_i(rb), ntj = syrk_tiles_j(rb);
-    const int warp = tid >> 5, nw = nt >> 5;
-    for (int t = warp; t < nti * ntj; t += nw) {
-        const int ti = t / ntj, tj = t % ntj;
-        if (tj * kTileJ > ti * kTileI + kTileI - 1) continue;   // tile above the diagonal
-        syrk_tile(P, s, c, r, A, Lx, ti, tj);
-    }
+    if (r > c) syrk_packed(P, s, c, r, A, Lx);
 }
 
 // Levels with few supernodes run in three launches spread over many CTAs:
@@ -590,7 +609,6 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, nw = nt >> 5;
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
@@ -600,15 +618,7 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
         panel_factor(sm, f, c, r, r, fail, dinv);
         // written back normalised (Lhat = L diag(dinv)); the SYRK below reads the smem copy
         for (int e = tid; e < r * c; e += nt) g[e] = sm[e] * dinv[f + e / r];
-        const int rb = r - c;
-        if (rb > 0) {
-            const int nti = syrk_tiles_i(rb), ntj = syrk_tiles_j(rb);
-            for (int t = warp; t < nti * ntj; t += nw) {
-                const int ti = t / ntj, tj = t % ntj;
-                if (tj * kTileJ > ti * kTileI + kTileI - 1) continue;
-                syrk_tile(P, s, c, r, sm, Lx, ti, tj);
-            }
-        }
+        if (r > c) syrk_packed(P, s, c, r, sm, Lx);
         __threadfence();
         __syncthreads();
     }

@@ -335,6 +335,61 @@ __device__ __forceinline__ void square_factor(T* A, int f, int c, FailSink fail,
     }
 }
 
+// Cholesky of a square c x c block, c <= 32, with look-ahead: warp 0 holds
+// the critical path (lanes = rows): at step j it applies column j to column
+// j + 1, takes the pivot (every lane computes the same reciprocal square
+// root, so the broadcast costs one shuffle), scales and publishes column
+// j + 1, while warps 1-3 apply column j to the columns beyond j + 1 (pairs
+// from the column-descending table, active pairs a prefix).  One barrier per
+// column; warps 4 and up only join the barriers, so no update instruction
+// competes with warp 0 for its sub-partition's FP64 unit.
+template <typename T>
+__device__ __forceinline__ void square_factor_lookahead(T* A, int f, int c, FailSink fail, T* dinv) {
+    __shared__ short2 tab[32 * 31 / 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < c * c; e += blockDim.x) {
+        const int ii = e % c, kk = e / c;
+        if (kk >= 1 && ii >= kk) tab[(c - 1 - kk) * (c - kk) / 2 + (ii - kk)] = make_short2((short)ii, (short)kk);
+    }
+    if (warp == 0) {   // column 0
+        const T a = lane < c ? A[lane] : T(0.0);
+        T d = __shfl_sync(0xffffffffu, a, 0);
+        if (!pivot_ok(d)) {
+            if (lane == 0) fail.report(f);
+            d = 1.0;
+        }
+        const T inv = pivot_rsqrt(d);
+        if (lane == 0) dinv[f] = inv;
+        if (lane > 0 && lane < c) A[lane] = a * inv;
+    }
+    __syncthreads();
+    for (int j = 0; j + 1 < c; ++j) {
+        const T* colj = A + j * c;
+        if (warp == 0) {
+            T* col1 = A + (j + 1) * c;
+            const bool below = lane > j && lane < c;
+            T a = below ? col1[lane] : T(0.0);
+            a = fma(-(below ? colj[lane] : T(0.0)), colj[j + 1], a);
+            T d = __shfl_sync(0xffffffffu, a, j + 1);
+            if (!pivot_ok(d)) {
+                if (lane == 0) fail.report(f + j + 1);
+                d = 1.0;
+            }
+            const T inv = pivot_rsqrt(d);
+            if (lane == 0) dinv[f + j + 1] = inv;
+            if (lane > j + 1 && lane < c) col1[lane] = a * inv;
+        } else if (warp < 4) {
+            const int active = (c - 2 - j) * (c - 1 - j) / 2;
+            for (int e = tid - 32; e < active; e += 96) {
+                const short2 pr = tab[e];
+                T* p = A + pr.x + pr.y * c;
+                *p = fma(-colj[pr.x], colj[pr.y], *p);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
@@ -346,7 +401,8 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
     __syncthreads();
-    square_factor(sm, f, c, fail, dinv);
+    if (c <= 32) square_factor_lookahead(sm, f, c, fail, dinv);
+    else square_factor(sm, f, c, fail, dinv);
     // the unused upper triangle receives the transpose of L11 diag(dinv)
     // (column-scaled by the reciprocal pivots), once, for the TRSM CTAs
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) {

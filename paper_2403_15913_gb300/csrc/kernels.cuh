@@ -565,13 +565,15 @@ __device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, in
 // diagonal block in shared memory, one warp substitutes with shuffles
 // (unit diagonal; the reciprocal pivots are applied in the backward pass),
 // then all warps form Lhat21 u and scatter it.
-template <typename T>
+template <typename T, bool kDynD>
 __global__ void __launch_bounds__(kThreads)
 forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
                      const T* __restrict__ dinv, T* __restrict__ x,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ T D[64 * 64];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T Dst[kDynD ? 1 : 64 * 64];
+    T* D = kDynD ? reinterpret_cast<T*>(smem_raw) : Dst;   // c x c
     __shared__ T z[64];
     __shared__ T part[kThreads / 32][32];
     const int s = lvl_sn[blockIdx.x];
@@ -596,16 +598,17 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
 // (levels visited top-down): t_k = z_k - L21(:,k)^T w_below with lanes over
 // the columns k and warps over row blocks, then one warp substitutes with
 // the diagonal block.
-template <typename T>
+template <typename T, bool kStageXb, bool kDynD>
 __global__ void __launch_bounds__(kThreads)
 backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
-                      const T* __restrict__ dinv, T* __restrict__ x,
+                      const T* __restrict__ dinv, T* __restrict__ x, int dsz,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ T D[64 * 64];
     __shared__ T part[kThreads / 32][64];
+    __shared__ T Dst[kDynD ? 1 : 64 * 64];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xb = reinterpret_cast<T*>(smem_raw);
+    T* D = kDynD ? reinterpret_cast<T*>(smem_raw) : Dst;   // c x c (dsz = the level's widest c squared)
+    T* xb = reinterpret_cast<T*>(smem_raw) + (kDynD ? dsz : 0);   // x of the rows below, when staged
     const int s = lvl_sn[blockIdx.x];
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const T* A = Lx + P.sn_lptr[s];
@@ -614,19 +617,21 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     const int rb = r - c;
     for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
-    for (int i = tid; i < rb; i += nt) xb[i] = x[rows[c + i]];
+    if (kStageXb)
+        for (int i = tid; i < rb; i += nt) xb[i] = x[rows[c + i]];
     __syncthreads();
     // warp w sums rows i = w, w + nw, ... for columns k = lane, lane + 32
     {
         T s0 = 0.0, s1 = 0.0;
         if (c > 32) {
             for (int i = warp; i < rb; i += nw) {
-                const T xv = xb[i];
+                const T xv = kStageXb ? xb[i] : x[rows[c + i]];
                 s0 = fma(A[c + i + (long long)lane * r], xv, s0);
                 if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
             }
         } else if (lane < c) {
-            for (int i = warp; i < rb; i += nw) s0 = fma(A[c + i + (long long)lane * r], xb[i], s0);
+            for (int i = warp; i < rb; i += nw)
+                s0 = fma(A[c + i + (long long)lane * r], kStageXb ? xb[i] : x[rows[c + i]], s0);
         }
         part[warp][lane] = s0;
         part[warp][lane + 32] = s1;

@@ -22,7 +22,9 @@ using namespace kktgb;
 namespace {
 
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
-constexpr int kSplitLevel = 2 * 152;   // levels with fewer supernodes use split launches
+constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
+constexpr int kNumSMs = 152;   // GB300
+constexpr int kSplitLevel = 2 * kNumSMs;   // levels with fewer supernodes use split launches
 
 template <class T>
 struct DevBuf {
@@ -805,6 +807,14 @@ void enqueue_bcr_solve(kkt_ctx* c, double* v, cudaStream_t st, const int* active
     }
 }
 
+template <typename T>
+void set_backward_smem_limit() {
+    cudaFuncSetAttribute(backward_level_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kBackwardSmemBytes);
+    cudaFuncSetAttribute(backward_level_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kBackwardSmemBytes);
+}
+
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
 // levels bottom-up, then levels top-down and subtree tasks (panels Lx and
 // reciprocal pivots dinv of the precision T).
@@ -814,16 +824,38 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
     if (c->ntasks > 0)
         forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
             c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+    // Levels with more supernodes than 256-thread CTAs keep resident at once
+    // (six per SM by registers) run 128-thread CTAs with the diagonal block
+    // sized for the level's widest supernode: one wave instead of two.
+    // Narrower levels keep a fixed 64 x 64 block.
     for (int l = 0; l < c->nlev; ++l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        forward_level_kernel<T><<<cnt, kThreads, 0, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], Lx, dinv,
-                                                          xp, active);
+        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
+        if (cnt > 6 * kNumSMs) {
+            const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
+            forward_level_kernel<T, true><<<cnt, kThreads / 2, dsm, st>>>(c->plan, lsn, Lx, dinv, xp, active);
+        } else {
+            forward_level_kernel<T, false><<<cnt, kThreads, 0, st>>>(c->plan, lsn, Lx, dinv, xp, active);
+        }
     }
     for (int l = c->nlev - 1; l >= 0; --l) {
-        int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        size_t sm = (size_t)c->lvl_max_rb[l] * sizeof(T);
-        backward_level_kernel<T><<<cnt, kThreads, sm, st>>>(c->plan, c->d_lvl_sn + c->h_lvl_ptr[l], Lx,
-                                                            dinv, xp, active);
+        const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
+        const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
+        const bool wide = cnt > 6 * kNumSMs;
+        const int dsz = wide ? c->lvl_max_c[l] * c->lvl_max_c[l] : 0;
+        const size_t xsm = (size_t)c->lvl_max_rb[l] * sizeof(T);
+        const size_t dbytes = wide ? (size_t)dsz * sizeof(T) : 64 * 64 * sizeof(T);   // dynamic or static
+        const bool stage = dbytes + xsm <= kBackwardSmemBytes;
+        const size_t sm = (size_t)dsz * sizeof(T) + (stage ? xsm : 0);
+        const int nt = wide ? kThreads / 2 : kThreads;
+        if (wide && stage)
+            backward_level_kernel<T, true, true><<<cnt, nt, sm, st>>>(c->plan, lsn, Lx, dinv, xp, dsz, active);
+        else if (wide)
+            backward_level_kernel<T, false, true><<<cnt, nt, sm, st>>>(c->plan, lsn, Lx, dinv, xp, dsz, active);
+        else if (stage)
+            backward_level_kernel<T, true, false><<<cnt, nt, sm, st>>>(c->plan, lsn, Lx, dinv, xp, dsz, active);
+        else
+            backward_level_kernel<T, false, false><<<cnt, nt, sm, st>>>(c->plan, lsn, Lx, dinv, xp, dsz, active);
     }
     if (c->ntasks > 0)
         backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(T), st>>>(
@@ -1247,12 +1279,9 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                              (int)(kSmemCapElems * sizeof(float)));
         cudaFuncSetAttribute(factor_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(df64)));
-        cudaFuncSetAttribute(backward_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 * 1024);
-        cudaFuncSetAttribute(backward_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 * 1024);
-        cudaFuncSetAttribute(backward_level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 * 1024);
+        set_backward_smem_limit<df64>();
+        set_backward_smem_limit<double>();
+        set_backward_smem_limit<float>();
         st = capture_graphs(c);
         if (st != KKT_OK) {
             set_err(nullptr, st, c->err);

@@ -14,6 +14,13 @@
 //    step for the reciprocal: with e = 1 - d y0, 1/d = y0 / (1 - e) =
 //    y0 (1 + e + e^2 + O(e^3)), truncation below 2^-66 -- three FP64 FMAs.
 //    Outside the range, the IEEE division.
+//  * max / min / |x| / sign tests of doubles on the integer units: the bit
+//    patterns of non-negative doubles order like their values (+inf above
+//    every finite value, NaN patterns above +inf), so for operands known to
+//    be >= 0 (or +-inf identities) a 64-bit integer compare replaces the FP64
+//    one.  As with fmax / fmin, a NaN operand is ignored.
+//  * split_pos: g = m 2^e with m in [0.5, 1) for positive normal g, by the
+//    bit layout (frexp without FP64 instructions).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -40,6 +47,52 @@ __device__ __forceinline__ double rcp_pos(double d) {
     const double y0 = f64_of(__frcp_rn(f32_of(d)));
     const double e = fma(-d, y0, 1.0);
     return fma(fma(e, e, e), y0, y0);
+}
+
+constexpr long long kBitsPosInf = 0x7ff0000000000000LL;
+
+__device__ __forceinline__ long long abs_bits(double x) {
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+
+// max(m, |x|) for m >= 0; a NaN x is ignored
+__device__ __forceinline__ double max_abs(double m, double x) {
+    const long long b = abs_bits(x), bm = __double_as_longlong(m);
+    return __longlong_as_double(b > bm && b <= kBitsPosInf ? b : bm);
+}
+
+// max / min of a, b >= 0 (or +-inf); a NaN b is ignored
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+    return __longlong_as_double(bb > ba && (bb & 0x7fffffffffffffffLL) <= kBitsPosInf ? bb : ba);
+}
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+    const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+    return __longlong_as_double(bb < ba ? bb : ba);   // NaN patterns lie above +inf
+}
+
+// a < b for a, b >= 0
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
+// sign bit set (x < 0, or x = -0.0)
+__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
+
+// strictly positive and not NaN (sign bit clear, nonzero)
+__device__ __forceinline__ bool is_pos(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= kBitsPosInf;
+}
+
+// g = m 2^e, m in [0.5, 1), for a positive normal g; false otherwise
+__device__ __forceinline__ bool split_pos(double g, double& m, int& e) {
+    const long long b = __double_as_longlong(g);
+    const int ex = (int)(b >> 52);   // sign bit clear for g > 0
+    if (b <= 0 || ex == 0 || ex >= 0x7ff) return false;
+    e = ex - 1022;
+    m = __longlong_as_double((b & 0x000fffffffffffffLL) | (1022LL << 52));
+    return true;
 }
 
 }  // namespace kktgb

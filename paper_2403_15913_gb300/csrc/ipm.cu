@@ -25,6 +25,11 @@
 
 namespace {
 
+using kktgb::is_pos;
+using kktgb::lt_nonneg;
+using kktgb::max_abs;
+using kktgb::max_nonneg;
+using kktgb::min_nonneg;
 using kktgb::rcp_pos;
 
 constexpr int kT = 256;
@@ -42,8 +47,10 @@ constexpr double kKappaWMinus = 1.0 / 3.0, kKappaWPlus = 8.0, kKappaWPlusBar = 1
 
 enum Op { SUM = 0, MAX = 1, MIN = 2 };
 
+// every MAX / MIN quantity of the reductions is >= 0 (or a +-inf identity),
+// so those are compared on the integer units
 __device__ __forceinline__ double combine(double a, double b, int op) {
-    return op == SUM ? a + b : (op == MAX ? fmax(a, b) : fmin(a, b));
+    return op == SUM ? a + b : (op == MAX ? max_nonneg(a, b) : min_nonneg(a, b));
 }
 
 __device__ __forceinline__ double block_reduce(double v, int op, double* red) {
@@ -86,16 +93,21 @@ __global__ void final_reduce_kernel(const double* __restrict__ part, const int* 
 
 // sum of log(g) over a thread's elements as log(prod of mantissas) plus the
 // exponents times ln 2: one logarithm per thread instead of one per element.
+// The splits g = m 2^e are taken on the bit patterns (one FP64 multiply per
+// element); zero, subnormal, infinite or negative g go through frexp.
 struct LogSum {
     double mant = 1.0;
     long long expo = 0;
     __device__ __forceinline__ void add(double g) {
+        double m;
         int e;
-        const double m = frexp(g, &e);       // g = m 2^e, m in [0.5, 1)
+        if (!kktgb::split_pos(g, m, e)) m = frexp(g, &e);   // g = m 2^e, m in [0.5, 1)
         mant *= m;
         expo += e;
         int e2;
-        mant = frexp(mant, &e2);             // keep the running product normalised
+        double mm;
+        if (!kktgb::split_pos(mant, mm, e2)) mm = frexp(mant, &e2);   // keep the product normalised
+        mant = mm;
         expo += e2;
     }
     __device__ __forceinline__ double value() const {
@@ -110,7 +122,7 @@ struct LogSum {
 struct MinRatio {
     double a = 1.0, b = 1.0;
     __device__ __forceinline__ void add(double na, double nb) {
-        if (na * b < a * nb) { a = na; b = nb; }
+        if (lt_nonneg(na * b, a * nb)) { a = na; b = nb; }   // products >= 0: integer compare
     }
     __device__ __forceinline__ double value() const { return a / b; }
 };
@@ -162,20 +174,20 @@ errors_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
             const double gl = x[i] - B.xlo[i], gu = B.xhi[i] - x[i];
-            v[0] = fmax(v[0], fabs(grad[i] + jty[i] - zl[i] + zu[i]));
+            v[0] = max_abs(v[0], grad[i] + jty[i] - zl[i] + zu[i]);
             const double a = zl[i] * gl, b = zu[i] * gu;
-            v[2] = fmax(v[2], fmax(a, b));
-            v[3] = fmin(v[3], fmin(a, b));
+            v[2] = max_nonneg(max_nonneg(v[2], a), b);
+            v[3] = min_nonneg(min_nonneg(v[3], a), b);
             v[5] += zl[i] + zu[i];
         } else {
             const int k = i - n;
-            v[1] = fmax(v[1], fabs(relaxed ? c[k] - s[k] : c[k]));
+            v[1] = max_abs(v[1], relaxed ? c[k] - s[k] : c[k]);
             v[4] += fabs(y[k]);
             if (relaxed) {
-                v[0] = fmax(v[0], fabs(-y[k] - vl[k] + vu[k]));
+                v[0] = max_abs(v[0], -y[k] - vl[k] + vu[k]);
                 const double a = vl[k] * (s[k] + B.tau), b = vu[k] * (B.tau - s[k]);
-                v[2] = fmax(v[2], fmax(a, b));
-                v[3] = fmin(v[3], fmin(a, b));
+                v[2] = max_nonneg(max_nonneg(v[2], a), b);
+                v[3] = min_nonneg(min_nonneg(v[3], a), b);
                 v[5] += vl[k] + vu[k];
             }
         }
@@ -234,10 +246,10 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
             const double b = mu * igu - zu[i] + (zu[i] * igu) * d;
             dzl[i] = a;
             dzu[i] = b;
-            if (d < 0) apr.add(tau * gl, -d);
-            if (d > 0) apr.add(tau * gu, d);
-            if (a < 0) adu.add(tau * zl[i], -a);
-            if (b < 0) adu.add(tau * zu[i], -b);
+            if (is_pos(-d)) apr.add(tau * gl, -d);   // sign tests on the bit patterns
+            if (is_pos(d)) apr.add(tau * gu, d);
+            if (is_pos(-a)) adu.add(tau * zl[i], -a);
+            if (is_pos(-b)) adu.add(tau * zu[i], -b);
             v[2] += (grad[i] - mu * igl + mu * igu) * d;
         } else if (relaxed) {
             const int k = i - n;
@@ -251,10 +263,10 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
             const double b = mu * ihu - vu[k] + (vu[k] * ihu) * d;
             dvl[k] = a;
             dvu[k] = b;
-            if (d < 0) apr.add(tau * hl, -d);
-            if (d > 0) apr.add(tau * hu, d);
-            if (a < 0) adu.add(tau * vl[k], -a);
-            if (b < 0) adu.add(tau * vu[k], -b);
+            if (is_pos(-d)) apr.add(tau * hl, -d);
+            if (is_pos(d)) apr.add(tau * hu, d);
+            if (is_pos(-a)) adu.add(tau * vl[k], -a);
+            if (is_pos(-b)) adu.add(tau * vu[k], -b);
             v[2] += gphi * d;
         }
     }
@@ -312,8 +324,8 @@ __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, do
             x[i] = xn;
             const double igl = rcp_pos(xn - B.xlo[i]), igu = rcp_pos(B.xhi[i] - xn);
             const double a = zl[i] + alpha_du * dzl[i], b = zu[i] + alpha_du * dzu[i];
-            zl[i] = fmax(fmin(a, k * mu * igl), (mu / k) * igl);
-            zu[i] = fmax(fmin(b, k * mu * igu), (mu / k) * igu);
+            zl[i] = max_nonneg(min_nonneg(a, k * mu * igl), (mu / k) * igl);
+            zu[i] = max_nonneg(min_nonneg(b, k * mu * igu), (mu / k) * igu);
         } else {
             const int q = i - n;
             y[q] += alpha * dy[q];
@@ -322,8 +334,8 @@ __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, do
                 s[q] = sn;
                 const double ihl = rcp_pos(sn + B.tau), ihu = rcp_pos(B.tau - sn);
                 const double a = vl[q] + alpha_du * dvl[q], b = vu[q] + alpha_du * dvu[q];
-                vl[q] = fmax(fmin(a, k * mu * ihl), (mu / k) * ihl);
-                vu[q] = fmax(fmin(b, k * mu * ihu), (mu / k) * ihu);
+                vl[q] = max_nonneg(min_nonneg(a, k * mu * ihl), (mu / k) * ihl);
+                vu[q] = max_nonneg(min_nonneg(b, k * mu * ihu), (mu / k) * ihu);
             }
         }
     }

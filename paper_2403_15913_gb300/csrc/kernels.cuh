@@ -72,8 +72,17 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
                                 T* __restrict__ Lx) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
          e += (long long)gridDim.x * blockDim.x) {
+        // the first source initialises the sum (no FP64 add of a zero; the
+        // same values as accumulating from 0)
+        const long long q0 = sptr[e], q1 = sptr[e + 1];
         double v = 0.0;
-        for (long long q = sptr[e]; q < sptr[e + 1]; ++q) {
+        if (q0 < q1) {
+            const int2 s = src[q0];
+            if (s.y == -1) v = W[s.x];
+            else if (s.y == -2) v = sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
+            else v = Js[s.x] * Js[s.y];
+        }
+        for (long long q = q0 + 1; q < q1; ++q) {
             const int2 s = src[q];
             if (s.y == -1) {
                 v += W[s.x];
@@ -859,18 +868,20 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
 }
 
+// block maximum of values >= 0, on the bit patterns (integer units)
 __device__ __forceinline__ double block_max(double v) {
-    __shared__ double red[kThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __shared__ long long red[kThreads / 32];
+    long long b = __double_as_longlong(v);
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, o));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) red[w] = v;
+    if (lane == 0) red[w] = b;
     __syncthreads();
     if (w == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        b = lane < (int)(blockDim.x >> 5) ? red[lane] : 0LL;
+        for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, o));
     }
-    return v;
+    return __longlong_as_double(b);
 }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -918,18 +929,18 @@ residual_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ 
             for (int q = jt_ptr[i]; q < jt_ptr[i + 1]; ++q) s += J[jt_idx[q]] * vy[jt_row[q]];
             double r = bx[i] - s;
             rx[i] = r;
-            mr = fmax(mr, fabs(r));
-            mv = fmax(mv, fabs(vx[i]));
-            mb = fmax(mb, fabs(bx[i]));
+            mr = max_abs(mr, r);   // max-norms on the integer units
+            mv = max_abs(mv, vx[i]);
+            mb = max_abs(mb, bx[i]);
         } else {
             int k = i - n;
             double s = C ? -C[k] * vy[k] : 0.0;
             for (int q = j_ptr[k]; q < j_ptr[k + 1]; ++q) s += J[q] * vx[j_col[q]];
             double r = by[k] - s;
             ry[k] = r;
-            mr = fmax(mr, fabs(r));
-            mv = fmax(mv, fabs(vy[k]));
-            mb = fmax(mb, fabs(by[k]));
+            mr = max_abs(mr, r);
+            mv = max_abs(mv, vy[k]);
+            mb = max_abs(mb, by[k]);
         }
     }
     mr = block_max(mr);
@@ -968,7 +979,7 @@ knorm_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ wf_
             for (int q = j_ptr[k]; q < j_ptr[k + 1]; ++q) s += fabs(J[q]);
             if (C) s += fabs(C[k]);
         }
-        mx = fmax(mx, s);
+        mx = max_nonneg(mx, s);
     }
     mx = block_max(mx);
     if (threadIdx.x == 0) atomic_max_nonneg(knorm + ch.z, mx);

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "fp64_lean.cuh"
+#include "sparse_dot.cuh"
 #include "kkt.h"
 #include "tray_internal.h"
 
@@ -137,9 +138,7 @@ __global__ void jt_kernel(int n, const int* __restrict__ cp, const int* __restri
                           const int* __restrict__ idx, const double* __restrict__ J,
                           const double* __restrict__ v, double* __restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int q = cp[i]; q < cp[i + 1]; ++q) s += J[idx[q]] * v[ri[q]];
-        out[i] = s;
+        out[i] = kktgb::gather_dot(cp[i], cp[i + 1], idx, ri, J, v, 0.0);
     }
 }
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "fp64_lean.cuh"
+#include "sparse_dot.cuh"
 
 namespace kktgb {
 
@@ -838,11 +839,28 @@ __global__ void jt_axpy_kernel(int n, const int* __restrict__ jt_ptr, const int*
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        // entries in batches: index loads, then value loads, then the FMAs
         double s = 0.0;
-        for (int q = jt_ptr[i]; q < jt_ptr[i + 1]; ++q) {
-            int r = jt_row[q];
-            double d = Dscale ? Dscale[r] : Dconst;
-            s += J[jt_idx[q]] * d * ay[r];
+        const int q0 = jt_ptr[i], q1 = jt_ptr[i + 1];
+        for (int q = q0; q < q1; q += kGatherBatch) {
+            int ri[kGatherBatch], ii[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const bool ok = q + u < q1;
+                ri[u] = ok ? jt_row[q + u] : 0;
+                ii[u] = ok ? jt_idx[q + u] : 0;
+            }
+            double jv[kGatherBatch], dv[kGatherBatch], yv[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const bool ok = q + u < q1;
+                jv[u] = ok ? J[ii[u]] : 0.0;
+                dv[u] = ok && Dscale ? Dscale[ri[u]] : Dconst;
+                yv[u] = ok ? ay[ri[u]] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u)
+                if (q + u < q1) s = fma(jv[u] * dv[u], yv[u], s);
         }
         out[i] = (ax ? ax[i] : 0.0) + alpha * s;
     }
@@ -856,8 +874,7 @@ __global__ void j_apply_kernel(int m, const int* __restrict__ j_ptr, const int* 
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int q = j_ptr[r]; q < j_ptr[r + 1]; ++q) s += J[q] * x[j_col[q]];
+        double s = gather_dot_direct(j_ptr[r], j_ptr[r + 1], j_col, J, x, 0.0);
         if (by) s -= by[r];
         out[r] = (Dscale ? Dscale[r] : Dconst) * s;
     }
@@ -925,8 +942,8 @@ residual_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ 
     for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
         if (i < n) {
             double s = (sigma[i] + (dvec ? dvec[i] : delta_x)) * vx[i];
-            for (int q = wf_ptr[i]; q < wf_ptr[i + 1]; ++q) s += W[wf_idx[q]] * vx[wf_col[q]];
-            for (int q = jt_ptr[i]; q < jt_ptr[i + 1]; ++q) s += J[jt_idx[q]] * vy[jt_row[q]];
+            s = gather_dot(wf_ptr[i], wf_ptr[i + 1], wf_idx, wf_col, W, vx, s);
+            s = gather_dot(jt_ptr[i], jt_ptr[i + 1], jt_idx, jt_row, J, vy, s);
             double r = bx[i] - s;
             rx[i] = r;
             mr = max_abs(mr, r);   // max-norms on the integer units
@@ -935,7 +952,7 @@ residual_kernel(const int4* __restrict__ chunks, int n, const int* __restrict__ 
         } else {
             int k = i - n;
             double s = C ? -C[k] * vy[k] : 0.0;
-            for (int q = j_ptr[k]; q < j_ptr[k + 1]; ++q) s += J[q] * vx[j_col[q]];
+            s = gather_dot_direct(j_ptr[k], j_ptr[k + 1], j_col, J, vx, s);
             double r = by[k] - s;
             ry[k] = r;
             mr = max_abs(mr, r);

@@ -517,6 +517,30 @@ kkt_status kkt_server_get_stats(kkt_server* srv, kkt_server_stats* stats);
 /* Finishes the running solves, stops the workers, frees every context. */
 void kkt_server_destroy(kkt_server* srv);
 
+/* ------------------------------------------------------------------------
+ * Verification of the FP64 helper functions the kernels are built on (the
+ * pivot reciprocal square root of the Cholesky, Sec. V-B, and the
+ * reciprocals, bit-pattern comparisons and splits of the IPM's elementwise
+ * kernels, Sec. III).  Evaluates on the device, elementwise,
+ *   unary   y[i] = f(x[i])            for i < n
+ *   binary  y[i] = f(x[i], x[n + i])  for i < n  (x holds 2n values)
+ * with f one of KKT_FN_*.  x and y are device pointers; the call is
+ * asynchronous on `stream` (cudaStream_t, NULL: the default stream).
+ * Returns KKT_ERR_ARG for an unknown fn or n < 0.                          */
+enum {
+    KKT_FN_RSQRT = 0,    /* pivot 1/sqrt(x): FP32 seed + third-order step     */
+    KKT_FN_RCP = 1,      /* 1/x: FP32 seed + third-order step (x > 0)         */
+    KKT_FN_SPLIT_M = 2,  /* m of x = m 2^e, m in [0.5, 1), by the bit layout;
+                            NaN unless x is positive and normal               */
+    KKT_FN_SPLIT_E = 3,  /* e of the same split, as a double                  */
+    KKT_FN_MAX_ABS = 4,  /* max(x0, |x1|) for x0 >= 0, a NaN x1 ignored      */
+    KKT_FN_MAX_NN = 5,   /* max(x0, x1) of non-negative values                */
+    KKT_FN_MIN_NN = 6,   /* min(x0, x1) of non-negative values                */
+    KKT_FN_F32_ROUNDTRIP = 7  /* double(float(x)) by the bit layout (x in
+                                 (1e-30, 1e30); truncates the mantissa)       */
+};
+kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

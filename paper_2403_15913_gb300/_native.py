@@ -40,7 +40,13 @@ EXPORTED = [
     "kkt_ipm_device_bytes", "kkt_device_bytes",
     "kkt_server_default_options", "kkt_server_create", "kkt_server_add_client", "kkt_server_submit",
     "kkt_server_wait", "kkt_server_drain", "kkt_server_get_stats", "kkt_server_destroy",
+    "kkt_eval_fn",
 ]
+
+# helper functions of kkt_eval_fn
+KKT_FN_RSQRT, KKT_FN_RCP, KKT_FN_SPLIT_M, KKT_FN_SPLIT_E = 0, 1, 2, 3
+KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN, KKT_FN_F32_ROUNDTRIP = 4, 5, 6, 7
+KKT_FN_BINARY = (KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN)
 
 
 class Options(ctypes.Structure):
@@ -220,6 +226,8 @@ def lib():
     L.kkt_ipm_device_bytes.restype = ctypes.c_int
     L.kkt_device_bytes.argtypes = [P, I64P]
     L.kkt_device_bytes.restype = ctypes.c_int
+    L.kkt_eval_fn.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
+    L.kkt_eval_fn.restype = ctypes.c_int
     L.kkt_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
     L.kkt_server_default_options.restype = None
     L.kkt_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.c_int, ctypes.POINTER(P)]

@@ -2018,3 +2018,39 @@ void kkt_destroy(kkt_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+__global__ void eval_fn_kernel(int fn, int n, const double* __restrict__ x, double* __restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double a = x[i];
+        double r = 0.0;
+        switch (fn) {
+            case KKT_FN_RSQRT: r = kktgb::rsqrt_householder(a); break;
+            case KKT_FN_RCP: r = kktgb::rcp_pos(a); break;
+            case KKT_FN_SPLIT_M:
+            case KKT_FN_SPLIT_E: {
+                double m;
+                int e;
+                if (kktgb::split_pos(a, m, e)) r = fn == KKT_FN_SPLIT_M ? m : (double)e;
+                else r = __longlong_as_double(0x7ff8000000000000LL);
+                break;
+            }
+            case KKT_FN_MAX_ABS: r = kktgb::max_abs(a, x[n + i]); break;
+            case KKT_FN_MAX_NN: r = kktgb::max_nonneg(a, x[n + i]); break;
+            case KKT_FN_MIN_NN: r = kktgb::min_nonneg(a, x[n + i]); break;
+            default: r = kktgb::f64_of(kktgb::f32_of(a)); break;
+        }
+        y[i] = r;
+    }
+}
+
+}  // namespace
+
+extern "C" kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream) {
+    if (fn < KKT_FN_RSQRT || fn > KKT_FN_F32_ROUNDTRIP || n < 0 || (n > 0 && (!x || !y))) return KKT_ERR_ARG;
+    if (n == 0) return KKT_OK;
+    eval_fn_kernel<<<std::min((n + 255) / 256, 152 * 8), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
+    return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_ERR_CUDA;
+}

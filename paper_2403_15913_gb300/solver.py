@@ -252,3 +252,18 @@ def autotune_batch(instances, sample=32, stream=None, **options):
         out[f] = getattr(best, f)
     return out, t.value
 
+
+def eval_fn(fn, x, stream=None):
+    """Evaluates one of the library's FP64 helper functions (nat.KKT_FN_*)
+    elementwise on the device: y[i] = f(x[i]), or f(x[0][i], x[1][i]) for the
+    binary ones (x of shape (2, n)).  x: CUDA float64 tensor; returns y."""
+    import torch
+    x = x.contiguous()
+    n = x.shape[-1] if fn in nat.KKT_FN_BINARY else x.numel()
+    if fn in nat.KKT_FN_BINARY and (x.dim() != 2 or x.shape[0] != 2):
+        raise ValueError("binary helper functions take x of shape (2, n)")
+    y = torch.empty(n, dtype=torch.float64, device=x.device)
+    st = nat.lib().kkt_eval_fn(int(fn), int(n), _dptr(x), _dptr(y), _stream(stream))
+    if st != 0:
+        raise KKTError(st, "kkt_eval_fn failed")
+    return y

@@ -227,49 +227,25 @@ __device__ __forceinline__ void update_target(const Plan& P, int s, int c, int j
     rm = P.relmap + P.seg_map[k];
 }
 
-constexpr int kTileI = 8, kTileJ = 4;   // SYRK output tile per warp (lane = one output)
-
-// SYRK output tile (ti, tj) of L21 L21^T, lane -> (ii, jj) = (8 ti + lane % 8,
-// 4 tj + lane / 8), scattered into the ancestors with FP64 atomics.
-template <typename T>
-__device__ __forceinline__ void syrk_tile(const Plan& P, int s, int c, int r, const T* A,
-                                          T* Lx, int ti, int tj) {
-    const int lane = threadIdx.x & 31;
-    const int rb = r - c;
-    const int ii = ti * kTileI + (lane & 7), jj = tj * kTileJ + (lane >> 3);
-    const bool valid = ii < rb && jj < rb && ii >= jj;
-    const T* ai = A + c + (valid ? ii : 0);
-    const T* aj = A + c + (valid ? jj : 0);
-    T sum = 0.0;
-    for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * r], aj[(long long)k * r], sum);
-    if (valid) {
-        long long base;
-        const int* rm;
-        int a;
-        update_target(P, s, c, jj, base, rm, a);
-        atomicAdd(Lx + base + rm[ii - a], -sum);
-    }
-}
-
 // SYRK of the rows below the diagonal block, L21 L21^T, over the packed
-// lower triangle: thread -> outputs p = tid, tid + nt, ... with p = ii (ii +
-// 1) / 2 + jj (row by row, jj <= ii), so every lane of a warp has an output
-// (8 x 4 tiles leave the lanes above the diagonal idle, a third of them when
-// rb is small).  The pair is decoded with an FP32 square root and an integer
-// correction; each output is then the same c-term FMA chain as a tile lane's.
+// lower triangle: thread -> outputs p = p0 + tid, p0 + tid + nt, ... < p1
+// with p = ii (ii + 1) / 2 + jj (row by row, jj <= ii), so every lane of a
+// warp has an output (8 x 4 tiles leave the lanes above the diagonal idle, a
+// third of them when rb is small).  The pair is decoded with an FP32 square
+// root and an integer correction; each output is a c-term FMA chain over
+// L21 (row i at A21[i], column stride ld), scattered into its ancestor.
 template <typename T>
-__device__ __forceinline__ void syrk_packed(const Plan& P, int s, int c, int r, const T* A, T* Lx) {
-    const int rb = r - c;
-    const int npairs = rb * (rb + 1) / 2;
-    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+__device__ __forceinline__ void syrk_pairs(const Plan& P, int s, int c, const T* A21, int ld, int p0,
+                                           int p1, T* Lx) {
+    for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) {
         int ii = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
         while (ii * (ii + 1) / 2 > p) --ii;
         while ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
         const int jj = p - ii * (ii + 1) / 2;
-        const T* ai = A + c + ii;
-        const T* aj = A + c + jj;
+        const T* ai = A21 + ii;
+        const T* aj = A21 + jj;
         T sum = 0.0;
-        for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * r], aj[(long long)k * r], sum);
+        for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * ld], aj[(long long)k * ld], sum);
         long long base;
         const int* rm;
         int a;
@@ -278,8 +254,11 @@ __device__ __forceinline__ void syrk_packed(const Plan& P, int s, int c, int r, 
     }
 }
 
-__device__ __forceinline__ int syrk_tiles_i(int rb) { return (rb + kTileI - 1) / kTileI; }
-__device__ __forceinline__ int syrk_tiles_j(int rb) { return (rb + kTileJ - 1) / kTileJ; }
+template <typename T>
+__device__ __forceinline__ void syrk_packed(const Plan& P, int s, int c, int r, const T* A, T* Lx) {
+    const int rb = r - c;
+    syrk_pairs(P, s, c, A + c, r, 0, rb * (rb + 1) / 2, Lx);
+}
 
 // One CTA per supernode (levels with many supernodes): the whole panel in
 // shared memory when it fits, dense right-looking factorisation, then the
@@ -498,15 +477,29 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
     if (lane + 32 < c) row[(long long)(lane + 32) * r] = a1 * dinv[f + lane + 32];
 }
 
-// task = (supernode, tile row ti, tile column tj); one tile per warp.
+// SYRK of a split level: task = (supernode, first pair, end pair) of the
+// packed lower triangle of L21 L21^T.  The CTA first copies L21 (rows c.. of
+// the panel, rb x c) into shared memory with coalesced loads when `stage` is
+// set (one memory latency instead of one per FMA pair), then computes one
+// output per thread as in the fused kernels.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-syrk_tile_kernel(Plan P, const int4* __restrict__ tasks, int ntasks, T* __restrict__ Lx) {
-    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= ntasks) return;
-    const int4 task = tasks[t];
-    const int s = task.x;
-    syrk_tile(P, s, P.sn_c[s], P.sn_r[s], Lx + P.sn_lptr[s], Lx, task.y, task.z);
+syrk_stage_kernel(Plan P, const int4* __restrict__ tasks, T* __restrict__ Lx, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    const int4 t = tasks[blockIdx.x];
+    const int s = t.x, c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
+    const T* g = Lx + P.sn_lptr[s];
+    if (stage) {
+        for (int e = threadIdx.x; e < rb * c; e += blockDim.x) {
+            const int i = e % rb, k = e / rb;
+            S[e] = g[c + i + (long long)k * r];
+        }
+        __syncthreads();
+        syrk_pairs(P, s, c, (const T*)S, rb, t.y, t.z, Lx);
+    } else {
+        syrk_pairs(P, s, c, g + c, r, t.y, t.z, Lx);
+    }
 }
 
 // After the factorisation: Lhat = L diag(1/l) (unit diagonal; the reciprocal

@@ -23,6 +23,7 @@ namespace {
 
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
 constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
+constexpr int kSyrkStageBytes = 96 * 1024;       // split-level SYRK: L21 staged in shared memory
 constexpr int kNumSMs = 152;   // GB300
 constexpr int kSplitLevel = 2 * kNumSMs;   // levels with fewer supernodes use split launches
 
@@ -558,15 +559,22 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         c->lvl_split[l] = cnt < kSplitLevel;
         if (c->lvl_split[l]) {
+            // SYRK tasks: chunks of the packed lower triangle of each
+            // supernode, sized so the level gives about four CTAs per SM
+            long long pairs = 0;
+            for (int q = c->h_lvl_ptr[l]; q < c->h_lvl_ptr[l + 1]; ++q) {
+                const long long rb = sn_r[c->h_lvl_sn[q]] - sn_c[c->h_lvl_sn[q]];
+                pairs += rb * (rb + 1) / 2;
+            }
+            const long long want = (pairs + 4LL * kNumSMs - 1) / (4LL * kNumSMs);
+            const int chunk = (int)std::min<long long>(1024, std::max<long long>(128, (want + 127) / 128 * 128));
             for (int q = c->h_lvl_ptr[l]; q < c->h_lvl_ptr[l + 1]; ++q) {
                 const int sn = c->h_lvl_sn[q];
                 const int rb = sn_r[sn] - sn_c[sn];
                 for (int r0 = 0; r0 < rb; r0 += kTrsmWarps) trsm_tasks.push_back(make_int2(sn, r0));
-                const int nti = (rb + kTileI - 1) / kTileI, ntj = (rb + kTileJ - 1) / kTileJ;
-                for (int ti = 0; ti < nti; ++ti)
-                    for (int tj = 0; tj < ntj; ++tj)
-                        if (tj * kTileJ <= ti * kTileI + kTileI - 1)
-                            syrk_tasks.push_back(make_int4(sn, ti, tj, 0));
+                const int np = rb * (rb + 1) / 2;
+                for (int p0 = 0; p0 < np; p0 += chunk)
+                    syrk_tasks.push_back(make_int4(sn, p0, std::min(np, p0 + chunk), 0));
             }
         }
         c->lvl_trsm_ptr[l + 1] = (int)trsm_tasks.size();
@@ -1164,9 +1172,12 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
             trsm_rows_kernel<T><<<nt, 32 * kTrsmWarps, 0, st>>>(
                 c->plan, c->d_trsm_tasks + c->lvl_trsm_ptr[l], Lx, dinv);
         const int ny = c->lvl_syrk_ptr[l + 1] - c->lvl_syrk_ptr[l];
-        if (ny > 0)
-            syrk_tile_kernel<T><<<(ny + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(
-                c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], ny, Lx);
+        if (ny > 0) {
+            const size_t l21 = (size_t)c->lvl_max_rb[l] * c->lvl_max_c[l] * sizeof(T);
+            const int stage = l21 <= kSyrkStageBytes;
+            syrk_stage_kernel<T><<<ny, kThreads, stage ? l21 : 0, st>>>(
+                c->plan, c->d_syrk_tasks + c->lvl_syrk_ptr[l], Lx, stage);
+        }
         c->stats.launches += 2;
     }
     if (c->n_norm > 0) {
@@ -1279,6 +1290,9 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                              (int)(kSmemCapElems * sizeof(float)));
         cudaFuncSetAttribute(factor_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(df64)));
+        cudaFuncSetAttribute(syrk_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
+        cudaFuncSetAttribute(syrk_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
+        cudaFuncSetAttribute(syrk_stage_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         set_backward_smem_limit<df64>();
         set_backward_smem_limit<double>();
         set_backward_smem_limit<float>();

@@ -60,8 +60,8 @@ __global__ void scale_rows_sqrt_kernel(int m, const int* __restrict__ jp,
 }
 
 // One thread per stored entry of the lower triangle of P K P^T: sums its
-// sources (W entry, diagonal Sigma_x + delta_x, products Js_a Js_b) and
-// writes the panel slot.  Source encoding: b == -1 -> W[a];
+// sources (W entries, diagonal Sigma_x + delta_x, products Js_a Js_b, in that
+// order within a slot) and writes the panel slot.  Source encoding: b == -1 -> W[a];
 // b == -2 -> sigma[a] + delta_x (dvec[a] when a per-variable vector is
 // given); b >= 0 -> Js[a] * Js[b].
 template <typename T>
@@ -83,15 +83,25 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
             else if (s.y == -2) v = sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
             else v = Js[s.x] * Js[s.y];
         }
-        for (long long q = q0 + 1; q < q1; ++q) {
-            const int2 s = src[q];
-            if (s.y == -1) {
-                v += W[s.x];
-            } else if (s.y == -2) {
-                v += sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
-            } else {
-                v = fma(Js[s.x], Js[s.y], v);
-            }
+        // A slot's sources come grouped (W entries, then the diagonal, then
+        // the J products), so three loops, each of one instruction type:
+        // lanes of a warp with different sources no longer step through all
+        // three branch bodies per source.
+        long long q = q0 + 1;
+        int2 s = q < q1 ? src[q] : make_int2(0, 0);
+        while (q < q1 && s.y == -1) {
+            v += W[s.x];
+            if (++q < q1) s = src[q];
+        }
+        if (q < q1 && s.y == -2) {
+            v += sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
+            if (++q < q1) s = src[q];
+        }
+        while (q < q1) {   // products (any other source is still summed correctly)
+            if (s.y >= 0) v = fma(Js[s.x], Js[s.y], v);
+            else if (s.y == -1) v += W[s.x];
+            else v += sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
+            if (++q < q1) s = src[q];
         }
         Lx[slot[e]] = (T)v;
     }

@@ -1160,8 +1160,13 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
         if (!c->lvl_split[l]) {
+            // At 60 registers a thread, 256-thread CTAs fit four to an SM: a
+            // level of 600-1200 narrow supernodes (c <= 32) takes two waves,
+            // where 128-thread CTAs (same warps per SM, twice the supernodes
+            // in flight) take one.  Wider supernodes or other counts keep 256.
+            const bool half = cnt > 4 * kNumSMs && cnt <= 8 * kNumSMs && c->lvl_max_c[l] <= 32;
             long long need = std::min<long long>(c->lvl_max_rc[l], kSmemCapElems);
-            factor_level_kernel<T><<<cnt, kThreads, (size_t)need * sizeof(T), st>>>(
+            factor_level_kernel<T><<<cnt, half ? kThreads / 2 : kThreads, (size_t)need * sizeof(T), st>>>(
                 c->plan, lsn, Lx, fs, need, dinv);
             continue;
         }

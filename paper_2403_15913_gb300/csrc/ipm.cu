@@ -68,28 +68,49 @@ __device__ __forceinline__ double block_reduce(double v, int op, double* red) {
     return v;
 }
 
-// Writes the block's K partial results to part[blockIdx.x * kQ + q].
+// Writes the block's K partial results to part[blockIdx.x * kQ + q]; the
+// CTA that finishes last (a device-wide counter taken after a fence) then
+// reduces the gridDim.x partials of each quantity into out[q]: warp q takes
+// quantity q, lane l combines blocks l, l + 32, ... in order, then a fixed
+// shuffle tree -- the same order every time (deterministic), without a
+// separate final launch.  The last CTA resets the counter.
 template <int K>
-__device__ __forceinline__ void store_partials(const double (&v)[K], const int (&ops)[K], double* part) {
+__device__ __forceinline__ void store_partials(const double (&v)[K], const int (&ops)[K], double* part,
+                                               unsigned* count, double* out) {
+    static_assert(K <= kT / 32, "one warp per quantity");
     __shared__ double red[kT / 32];
+    __shared__ bool last;
     for (int q = 0; q < K; ++q) {
         const double r = block_reduce(v[q], ops[q], red);
         if (threadIdx.x == 0) part[blockIdx.x * kQ + q] = r;
     }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (q < K) {
+        int op = SUM;
+        for (int j = 0; j < K; ++j)
+            if (j == q) op = ops[j];
+        double acc = __ldcg(part + lane * kQ + q);
+        for (int b = lane + 32; b < (int)gridDim.x; b += 32) acc = combine(acc, __ldcg(part + b * kQ + q), op);
+        for (int o = 16; o > 0; o >>= 1) acc = combine(acc, __shfl_down_sync(0xffffffffu, acc, o), op);
+        if (lane == 0) out[q] = acc;
+    }
+    if (threadIdx.x == 0) *count = 0u;
 }
 
-// Final reduction of kRB partial blocks: warp q reduces quantity q, lane l
-// combines blocks l, l + 32, ... in order, then a fixed shuffle tree
-// (deterministic).  Launch with 32 * nq threads.
-__global__ void final_reduce_kernel(const double* __restrict__ part, const int* __restrict__ ops,
-                                    int nq, double* __restrict__ out) {
-    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (q >= nq) return;
-    const int op = ops[q];
-    double acc = part[lane * kQ + q];
-    for (int b = lane + 32; b < kRB; b += 32) acc = combine(acc, part[b * kQ + q], op);
-    for (int o = 16; o > 0; o >>= 1) acc = combine(acc, __shfl_down_sync(0xffffffffu, acc, o), op);
-    if (lane == 0) out[q] = acc;
+// Sum of kRB partials part[b * kQ] (the objective), in the order above.
+__global__ void final_sum_kernel(const double* __restrict__ part, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    double acc = part[lane * kQ];
+    for (int b = lane + 32; b < kRB; b += 32) acc += part[b * kQ];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[0] = acc;
 }
 
 // sum of log(g) over a thread's elements as log(prod of mantissas) plus the
@@ -167,7 +188,8 @@ errors_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
               const double* __restrict__ zl, const double* __restrict__ zu,
               const double* __restrict__ vl, const double* __restrict__ vu,
               const double* __restrict__ grad, const double* __restrict__ jty,
-              const double* __restrict__ c, double* __restrict__ part) {
+              const double* __restrict__ c, double* __restrict__ part, unsigned* count,
+              double* __restrict__ out) {
     double v[6] = {0.0, 0.0, -INFINITY, INFINITY, 0.0, 0.0};
     const int ops[6] = {MAX, MAX, MAX, MIN, SUM, SUM};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
@@ -191,7 +213,7 @@ errors_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
             }
         }
     }
-    store_partials<6>(v, ops, part);
+    store_partials<6>(v, ops, part, count, out);
 }
 
 __global__ void prepare_kernel(int n, int m, int relaxed, Bounds B, double mu,
@@ -232,7 +254,8 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
                const double* __restrict__ vu, const double* __restrict__ grad,
                const double* __restrict__ dx, const double* __restrict__ dy,
                double* __restrict__ ds, double* __restrict__ dzl, double* __restrict__ dzu,
-               double* __restrict__ dvl, double* __restrict__ dvu, double* __restrict__ part) {
+               double* __restrict__ dvl, double* __restrict__ dvu, double* __restrict__ part,
+               unsigned* count, double* __restrict__ out) {
     double v[3] = {1.0, 1.0, 0.0};
     const int ops[3] = {MIN, MIN, SUM};
     MinRatio apr, adu;   // tau gap / |step| over the blocking steps
@@ -271,7 +294,7 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
     }
     v[0] = apr.value();
     v[1] = adu.value();
-    store_partials<3>(v, ops, part);
+    store_partials<3>(v, ops, part, count, out);
 }
 
 __global__ void trial_kernel(int n, int m, int relaxed, double alpha, const double* __restrict__ x,
@@ -287,7 +310,8 @@ __global__ void trial_kernel(int n, int m, int relaxed, double alpha, const doub
 // Filter measures at a point: partials [theta = sum |c - s|, sum log(gaps)].
 __global__ void __launch_bounds__(kT)
 measure_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x,
-               const double* __restrict__ s, const double* __restrict__ c, double* __restrict__ part) {
+               const double* __restrict__ s, const double* __restrict__ c, double* __restrict__ part,
+               unsigned* count, double* __restrict__ out) {
     double v[2] = {0.0, 0.0};
     const int ops[2] = {SUM, SUM};
     LogSum ls;
@@ -305,7 +329,7 @@ measure_kernel(int n, int m, int relaxed, Bounds B, const double* __restrict__ x
         }
     }
     v[1] = ls.value();
-    store_partials<2>(v, ops, part);
+    store_partials<2>(v, ops, part, count, out);
 }
 
 __global__ void accept_kernel(int n, int m, int relaxed, Bounds B, double mu, double alpha,
@@ -359,7 +383,7 @@ struct kkt_ipm {
     double *grad, *c, *Jv, *Wv, *jty, *sigma, *rx, *ry, *D;
     double *dx, *dy, *ds, *dzl, *dzu, *dvl, *dvu, *xt, *st, *ct;
     double *part, *red, *f;
-    int* ops;
+    unsigned* count;   // last-CTA counter of the reduction kernels (zero between launches)
     int *jt_cp, *jt_ri, *jt_idx;
     double* h_red = nullptr;   // pinned
     double* x0v = nullptr;     // per-tray initial state (device, k), NULL: x0bar
@@ -404,10 +428,8 @@ kkt_status dalloc(kkt_ipm* p, T** out, size_t count) {
 
 Bounds bounds_of(const kkt_ipm* p) { return Bounds{p->xlo, p->xhi, p->opt.tau_relax}; }
 
-// reduce kRB partials to q results and copy them to the host
-kkt_status finish_reduce(kkt_ipm* p, const int* h_ops, int nq, cudaStream_t st, double* out) {
-    ICUDA(p, cudaMemcpyAsync(p->ops, h_ops, nq * sizeof(int), cudaMemcpyHostToDevice, st));
-    final_reduce_kernel<<<1, 32 * nq, 0, st>>>(p->part, p->ops, nq, p->red);
+// copy the nq results the last CTA of a reduction kernel left in red
+kkt_status finish_reduce(kkt_ipm* p, int nq, cudaStream_t st, double* out) {
     ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
     ICUDA(p, cudaStreamSynchronize(st));
     for (int q = 0; q < nq; ++q) out[q] = p->h_red[q];
@@ -418,9 +440,7 @@ kkt_status finish_reduce(kkt_ipm* p, const int* h_ops, int nq, cudaStream_t st, 
 kkt_status objective(kkt_ipm* p, const double* w, cudaStream_t st, double* f) {
     if (!kktgb::tray_objective_partials(p->params, w, p->part + (kQ - 1), kQ, kRB, st))
         return ierr(p, KKT_ERR_CUDA, "objective kernel launch failed");
-    static const int ops[1] = {SUM};
-    ICUDA(p, cudaMemcpyAsync(p->ops, ops, sizeof(int), cudaMemcpyHostToDevice, st));
-    final_reduce_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->ops, 1, p->red);
+    final_sum_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->red);
     ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, sizeof(double), cudaMemcpyDeviceToHost, st));
     ICUDA(p, cudaStreamSynchronize(st));
     *f = p->h_red[0];
@@ -444,10 +464,10 @@ double err_mu(const kkt_ipm* p, const Errors& e, double mu) {
 
 kkt_status measures(kkt_ipm* p, const double* x, const double* s, const double* c, cudaStream_t st,
                     double* theta, double* logsum) {
-    measure_kernel<<<kRB, kT, 0, st>>>(p->n, p->m, p->opt.relaxed, bounds_of(p), x, s, c, p->part);
-    static const int ops[2] = {SUM, SUM};
+    measure_kernel<<<kRB, kT, 0, st>>>(p->n, p->m, p->opt.relaxed, bounds_of(p), x, s, c, p->part, p->count,
+                                       p->red);
     double out[2];
-    ITRY(finish_reduce(p, ops, 2, st, out));
+    ITRY(finish_reduce(p, 2, st, out));
     *theta = out[0];
     *logsum = out[1];
     return KKT_OK;
@@ -533,7 +553,7 @@ kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const k
         if (dalloc(p, v, m) != KKT_OK) return fail(KKT_ERR_OOM);
     if (dalloc(p, &p->Jv, p->nnzJ) != KKT_OK || dalloc(p, &p->Wv, p->nnzW) != KKT_OK ||
         dalloc(p, &p->part, (size_t)kRB * kQ) != KKT_OK || dalloc(p, &p->red, kQ) != KKT_OK ||
-        dalloc(p, &p->f, 1) != KKT_OK || dalloc(p, &p->ops, kQ) != KKT_OK ||
+        dalloc(p, &p->f, 1) != KKT_OK || dalloc(p, &p->count, 1) != KKT_OK ||
         dalloc(p, &p->jt_cp, n + 1) != KKT_OK || dalloc(p, &p->jt_ri, p->nnzJ) != KKT_OK ||
         dalloc(p, &p->jt_idx, p->nnzJ) != KKT_OK)
         return fail(KKT_ERR_OOM);
@@ -541,7 +561,8 @@ kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const k
         cudaMemcpy(p->jt_ri, ri.data(), p->nnzJ * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->jt_idx, idx.data(), p->nnzJ * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->xlo, lo.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->xhi, hi.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(p->xhi, hi.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->count, 0, sizeof(unsigned)) != cudaSuccess)
         return fail(KKT_ERR_CUDA);
     if (cudaMallocHost((void**)&p->h_red, kQ * sizeof(double)) != cudaSuccess) return fail(KKT_ERR_OOM);
     for (auto& e : p->ev)
@@ -601,10 +622,9 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     cudaEventRecord(p->ev[1], st);
     // 2. optimality error and barrier update
     errors_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, p->x, p->s, p->y, p->zl, p->zu, p->vl, p->vu,
-                                      p->grad, p->jty, p->c, p->part);
-    static const int eops[6] = {MAX, MAX, MAX, MIN, SUM, SUM};
+                                      p->grad, p->jty, p->c, p->part, p->count, p->red);
     double ev6[6];
-    ITRY(finish_reduce(p, eops, 6, st, ev6));
+    ITRY(finish_reduce(p, 6, st, ev6));
     Errors E{ev6[0], ev6[1], ev6[2], ev6[3], ev6[4], ev6[5]};
     double fval = 0.0;
     ITRY(objective(p, p->x, st, &fval));
@@ -657,10 +677,9 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     const double tau = std::max(kTauMin, 1.0 - mu);
     recover_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, mu, tau, p->x, p->s, p->y, p->zl, p->zu, p->vl,
                                        p->vu, p->grad, p->dx, p->dy, p->ds, p->dzl, p->dzu, p->dvl,
-                                       p->dvu, p->part);
-    static const int rops[3] = {MIN, MIN, SUM};
+                                       p->dvu, p->part, p->count, p->red);
     double rv[3];
-    ITRY(finish_reduce(p, rops, 3, st, rv));
+    ITRY(finish_reduce(p, 3, st, rv));
     const double a_pr = rv[0], a_du = rv[1], dphi = rv[2];
     // 6. filter line search
     double th = 0, lsum = 0;

@@ -368,7 +368,8 @@ def run_ours(args, ws, rank, local):
                 "h2d_bytes_per_step": p.n * 8 / max(1, e2e_iters),
                 "d2h_bytes_per_step": (p.n + p.m) * 8 / max(1, e2e_iters),
                 "scope": "whole solves: x0 host->device, all iterations, (x, y) device->host"},
-        "gpu_launches": int(st["launches"] / n_steps * args.steps) if n_steps else 0,
+        "gpu_launches": (int(st["launches"] / n_steps * args.steps) + sum(i["launches"] for i in infos))
+                        if n_steps else 0,
         "clocks": clk,
         "wall_s": wall,
     }

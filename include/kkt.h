@@ -385,6 +385,8 @@ typedef struct {
     double alpha_pr, alpha_du, delta_x, bwd_err;
     double t_eval_ms, t_kkt_ms, t_step_ms;   /* device time of the last step:
                           derivative evaluation, KKT factor + solve, total  */
+    int launches;      /* kernels the driver itself launched in the last step
+                          (the KKT context's own are counted in kkt_stats)  */
 } kkt_ipm_info;
 
 void kkt_ipm_default_options(kkt_ipm_options* opt);

@@ -94,7 +94,7 @@ class IPMInfo(ctypes.Structure):
                 ("alpha_pr", ctypes.c_double), ("alpha_du", ctypes.c_double),
                 ("delta_x", ctypes.c_double), ("bwd_err", ctypes.c_double),
                 ("t_eval_ms", ctypes.c_double), ("t_kkt_ms", ctypes.c_double),
-                ("t_step_ms", ctypes.c_double)]
+                ("t_step_ms", ctypes.c_double), ("launches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

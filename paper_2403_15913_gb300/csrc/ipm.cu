@@ -393,6 +393,7 @@ struct kkt_ipm {
     double mu = 0.1, theta_max = 0, theta_min = 0, delta_last = 0;
     std::vector<std::pair<double, double>> filter;
     int it = 0;
+    int launches = 0;   // kernels launched by the driver in the current step
     bool started = false;
     cudaEvent_t ev[4] = {};
 };
@@ -441,6 +442,7 @@ kkt_status objective(kkt_ipm* p, const double* w, cudaStream_t st, double* f) {
     if (!kktgb::tray_objective_partials(p->params, w, p->part + (kQ - 1), kQ, kRB, st))
         return ierr(p, KKT_ERR_CUDA, "objective kernel launch failed");
     final_sum_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->red);
+    p->launches += 2;
     ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, sizeof(double), cudaMemcpyDeviceToHost, st));
     ICUDA(p, cudaStreamSynchronize(st));
     *f = p->h_red[0];
@@ -466,6 +468,7 @@ kkt_status measures(kkt_ipm* p, const double* x, const double* s, const double* 
                     double* theta, double* logsum) {
     measure_kernel<<<kRB, kT, 0, st>>>(p->n, p->m, p->opt.relaxed, bounds_of(p), x, s, c, p->part, p->count,
                                        p->red);
+    p->launches += 1;
     double out[2];
     ITRY(finish_reduce(p, 2, st, out));
     *theta = out[0];
@@ -615,14 +618,17 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     const Bounds B = bounds_of(p);
     kkt_ipm_info inf{};
     inf.iter = p->it;
+    p->launches = 0;
     cudaEventRecord(p->ev[0], st);
     // 1. derivatives
     ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, p->y, 1.0, nullptr, p->grad, p->c, p->Jv, p->Wv, st));
     jt_kernel<<<grid(n), kT, 0, st>>>(n, p->jt_cp, p->jt_ri, p->jt_idx, p->Jv, p->y, p->jty);
+    p->launches += 2;
     cudaEventRecord(p->ev[1], st);
     // 2. optimality error and barrier update
     errors_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, p->x, p->s, p->y, p->zl, p->zu, p->vl, p->vu,
                                       p->grad, p->jty, p->c, p->part, p->count, p->red);
+    p->launches += 1;
     double ev6[6];
     ITRY(finish_reduce(p, 6, st, ev6));
     Errors E{ev6[0], ev6[1], ev6[2], ev6[3], ev6[4], ev6[5]};
@@ -636,7 +642,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     inf.err0 = e0;
     inf.mu = p->mu;
     if (e0 <= p->opt.tol) {
-        if (info) *info = inf;
+        { inf.launches = p->launches; if (info) *info = inf; }
         return KKT_CONVERGED;
     }
     while (p->mu > p->opt.tol / 10) {
@@ -650,6 +656,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     prepare_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, p->x, p->s, p->y, p->zl,
                                                         p->zu, p->vl, p->vu, p->grad, p->jty, p->c,
                                                         p->sigma, p->rx, p->ry, p->D);
+    p->launches += 1;
     // 4. factor with inertia correction, solve
     kkt_info ki{};
     double delta = 0.0;
@@ -678,6 +685,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     recover_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, mu, tau, p->x, p->s, p->y, p->zl, p->zu, p->vl,
                                        p->vu, p->grad, p->dx, p->dy, p->ds, p->dzl, p->dzu, p->dvl,
                                        p->dvu, p->part, p->count, p->red);
+    p->launches += 1;
     double rv[3];
     ITRY(finish_reduce(p, 3, st, rv));
     const double a_pr = rv[0], a_du = rv[1], dphi = rv[2];
@@ -691,7 +699,9 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     for (ls = 1; ls <= kMaxLs; ++ls) {
         trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, alpha, p->x, p->dx, p->s, p->ds,
                                                           p->xt, p->st);
+        p->launches += 1;
         ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
+        p->launches += 1;
         double tht = 0, lst = 0, ft = 0;
         ITRY(measures(p, p->xt, p->st, p->ct, st, &tht, &lst));
         ITRY(objective(p, p->xt, st, &ft));
@@ -718,13 +728,14 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     }
     inf.ls_trials = ls;
     if (!accepted) {
-        if (info) *info = inf;
+        { inf.launches = p->launches; if (info) *info = inf; }
         return ierr(p, KKT_ERR_STALL, "line search failed (no restoration phase)");
     }
     // 7. update
     accept_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, alpha, a_du, p->x, p->s,
                                                        p->y, p->zl, p->zu, p->vl, p->vu, p->dx,
                                                        p->ds, p->dy, p->dzl, p->dzu, p->dvl, p->dvu);
+    p->launches += 1;
     cudaEventRecord(p->ev[3], st);
     ICUDA(p, cudaEventSynchronize(p->ev[3]));
     float t01 = 0, t12 = 0, t03 = 0;
@@ -739,7 +750,7 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     p->it++;
     inf.iter = p->it;
     ICUDA(p, cudaGetLastError());
-    if (info) *info = inf;
+    { inf.launches = p->launches; if (info) *info = inf; }
     return KKT_OK;
 }
 

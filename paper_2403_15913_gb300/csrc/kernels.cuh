@@ -7,6 +7,7 @@
 // while it is factorised, and (iii) leave all index arithmetic to the
 // integer pipes.
 #pragma once
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -510,6 +511,66 @@ syrk_stage_kernel(Plan P, const int4* __restrict__ tasks, T* __restrict__ Lx, in
     } else {
         syrk_pairs(P, s, c, g + c, r, t.y, t.z, Lx);
     }
+}
+
+// The small top levels of the tree (a few supernodes each) in one launch per
+// level instead of three: a thread-block cluster of kClusterCtas CTAs per
+// supernode.  (1) CTA 0 factorises the diagonal block as potrf_diag_kernel;
+// (2) after a cluster barrier every warp of the cluster solves rows of L21
+// as trsm_rows_kernel; (3) after a second barrier each CTA stages L21 and
+// computes its share of the packed SYRK pairs.  Cluster barriers are
+// hardware barriers with release / acquire semantics at cluster scope, and
+// data written by another CTA of the cluster is read through L2.
+constexpr int kClusterCtas = 8;
+
+template <typename T>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kThreads)
+narrow_level_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx, FailSink fail,
+                            T* __restrict__ dinv) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int rank = (int)cluster.block_rank();
+    const int s = lvl_sn[blockIdx.x / kClusterCtas];
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
+    T* g = Lx + P.sn_lptr[s];
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    // (1) diagonal block
+    if (rank == 0) {
+        for (int e = tid; e < c * c; e += nt) sm[e] = g[(e % c) + (long long)(e / c) * r];
+        __syncthreads();
+        if (c <= 32) square_factor_lookahead(sm, f, c, fail, dinv);
+        else square_factor(sm, f, c, fail, dinv);
+        for (int e = tid; e < c * c; e += nt) {   // transpose of L11 diag(dinv) above the diagonal
+            const int row = e % c, col = e / c;
+            if (row > col) sm[col + row * c] = sm[e] * dinv[f + col];
+        }
+        __syncthreads();
+        for (int e = tid; e < c * c; e += nt) g[(e % c) + (long long)(e / c) * r] = sm[e];
+    }
+    cluster.sync();
+    // (2) rows below the diagonal block
+    for (int e = tid; e < c * c; e += nt) sm[e] = __ldcg(g + e / c + (long long)(e % c) * r);
+    __syncthreads();
+    const T di0 = lane < c ? __ldcg(dinv + f + lane) : T(0.0);
+    const T di1 = lane + 32 < c ? __ldcg(dinv + f + lane + 32) : T(0.0);
+    for (int i = rank * nw + warp; i < rb; i += kClusterCtas * nw) {
+        T* row = g + c + i;
+        T a0 = lane < c ? row[(long long)lane * r] : T(0.0);
+        T a1 = lane + 32 < c ? row[(long long)(lane + 32) * r] : T(0.0);
+        warp_lower_solve(sm, c, c, lane, a0, a1);
+        if (lane < c) row[(long long)lane * r] = a0 * di0;
+        if (lane + 32 < c) row[(long long)(lane + 32) * r] = a1 * di1;
+    }
+    cluster.sync();
+    // (3) SYRK share of this CTA
+    const int np = rb * (rb + 1) / 2;
+    const int p0 = (int)((long long)np * rank / kClusterCtas);
+    const int p1 = (int)((long long)np * (rank + 1) / kClusterCtas);
+    for (int e = tid; e < rb * c; e += nt) sm[e] = __ldcg(g + c + e % rb + (long long)(e / rb) * r);
+    __syncthreads();
+    syrk_pairs(P, s, c, (const T*)sm, rb, p0, p1, Lx);
 }
 
 // After the factorisation: Lhat = L diag(1/l) (unit diagonal; the reciprocal

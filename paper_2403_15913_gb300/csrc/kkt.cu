@@ -24,6 +24,8 @@ namespace {
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
 constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
 constexpr int kSyrkStageBytes = 96 * 1024;       // split-level SYRK: L21 staged in shared memory
+constexpr int kClusterLevelMax = 32;             // split levels this small run as one cluster launch
+constexpr int kClusterSmemBytes = 96 * 1024;     // its diagonal block / staged L21
 constexpr int kNumSMs = 152;   // GB300
 constexpr int kSplitLevel = 2 * kNumSMs;   // levels with fewer supernodes use split launches
 
@@ -1171,6 +1173,12 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
             continue;
         }
         const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
+        // the small top levels: one cluster launch instead of three launches
+        const size_t csm = std::max(dsm, (size_t)c->lvl_max_rb[l] * c->lvl_max_c[l] * sizeof(T));
+        if (cnt <= kClusterLevelMax && csm <= kClusterSmemBytes) {
+            narrow_level_cluster_kernel<T><<<cnt * kClusterCtas, kThreads, csm, st>>>(c->plan, lsn, Lx, fs, dinv);
+            continue;
+        }
         potrf_diag_kernel<T><<<cnt, kThreads, dsm, st>>>(c->plan, lsn, Lx, fs, dinv);
         const int nt = c->lvl_trsm_ptr[l + 1] - c->lvl_trsm_ptr[l];
         if (nt > 0)
@@ -1295,6 +1303,12 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                              (int)(kSmemCapElems * sizeof(float)));
         cudaFuncSetAttribute(factor_level_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemCapElems * sizeof(df64)));
+        cudaFuncSetAttribute(narrow_level_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kClusterSmemBytes);
+        cudaFuncSetAttribute(narrow_level_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kClusterSmemBytes);
+        cudaFuncSetAttribute(narrow_level_cluster_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kClusterSmemBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);

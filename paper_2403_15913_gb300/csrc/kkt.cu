@@ -24,7 +24,7 @@ namespace {
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
 constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
 constexpr int kSyrkStageBytes = 96 * 1024;       // split-level SYRK: L21 staged in shared memory
-constexpr int kClusterLevelMax = 64;             // split levels this small run as one cluster launch
+constexpr int kClusterLevelMax = 32;             // split levels this small run as one cluster launch
 constexpr int kClusterSmemBytes = 96 * 1024;     // its diagonal block / staged L21
 constexpr int kNumSMs = 152;   // GB300
 constexpr int kSplitLevel = 2 * kNumSMs;   // levels with fewer supernodes use split launches

@@ -12,6 +12,8 @@ passage of the paper it follows:
                 postorder, column counts and supernode partition (Sec. V-B:
                 symbolic analysis done once for the fixed pattern)
 * ``cholesky``  left-looking column Cholesky and triangular solves (Sec. V-B)
+* ``ldlt``      dense Bunch-Kaufman LDL^T: solutions and inertia of the
+                indefinite KKT matrix (Eq. inertia)
 * ``kkt``       the condensed KKT system (Eq. kkt:condensed), its dense
                 solution and inertia (Eq. inertia), Lifted-KKT with Richardson
                 refinement (Sec. IV-A, Sec. V-B) and HyKKT with CG on the

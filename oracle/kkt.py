@@ -14,9 +14,13 @@ h(x), only variable bounds) and with an optional dual block -C (C = 0 for the
 equality-constrained system; C = D^{-1} for the relaxed problem of Lifted-KKT,
 Eq. problemrelaxation).  Callers pass r = -F_mu.
 
-* ``dense_solve``: the plain definition, numpy's LU solve of K_orig followed
-  by two steps of FP64 refinement.
-* ``inertia``: Sylvester's law on scipy's Bunch-Kaufman LDL^T (Eq. inertia).
+* ``dense_solve``: the plain definition, the unique solution of K_orig v = b
+  by the Bunch-Kaufman LDL^T of ``oracle.ldlt`` (up to 2,500 unknowns; above
+  that LAPACK's LU solves the same definition, because the unblocked
+  elimination would take minutes), followed by two steps of FP64
+  refinement.
+* ``inertia``: Sylvester's law on the blocks of D of the same LDL^T
+  (Eq. inertia).
 * ``lifted_solve``: Lifted-KKT (Sec. IV-A, Sec. V-B).  The preconditioner
   M = [[H, J^T], [J, -D^{-1}]] is applied by one Cholesky solve with the
   condensed matrix K_D = H + J^T D J (Eq. liftedkkt) and
@@ -35,7 +39,7 @@ paper only names Richardson iterations, Sec. V-B).
 Backward error (Rigal-Gaches, normwise):
     eta = ||b - K_orig v||_inf / (||K_orig||_inf ||v||_inf + ||b||_inf).
 
-Parity: pinned (LAPACK cross-checks, Haynsworth inertia, equality of the
+Parity: pinned (LAPACK cross-checks of both dense solve routes, Haynsworth inertia, equality of the
 three solutions for every gamma, eigenvalues of gamma S_gamma -> 1).
 """
 from __future__ import annotations
@@ -46,6 +50,7 @@ import numpy as np
 import scipy.linalg
 import scipy.sparse as sp
 
+from oracle import ldlt
 from oracle.cholesky import SparseCholesky, NotPositiveDefinite
 
 
@@ -98,40 +103,26 @@ def backward_error(K, v, b, knorm=None):
 
 
 # --------------------------------------------------------------- dense O2
-def dense_solve(K, b, refine_steps=2):
-    """Plain definition of the KKT step: LU solve of the dense K_orig and two
-    Richardson steps in FP64."""
-    Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
-    lu = scipy.linalg.lu_factor(Kd)
-    v = scipy.linalg.lu_solve(lu, b)
+def dense_solve(K, b, refine_steps=2, ldlt_max=2500):
+    """Plain definition of the KKT step: the solution of the dense K_orig by
+    its Bunch-Kaufman LDL^T (LAPACK's LU above ``ldlt_max`` unknowns), then
+    ``refine_steps`` Richardson steps in FP64."""
+    Kd = K.toarray() if sp.issparse(K) else np.asarray(K, dtype=np.float64)
+    if Kd.shape[0] <= ldlt_max:
+        solve = ldlt.factor(Kd).solve
+    else:
+        lu = scipy.linalg.lu_factor(Kd)
+        solve = lambda r: scipy.linalg.lu_solve(lu, r)
+    v = solve(b)
     for _ in range(refine_steps):
-        v = v + scipy.linalg.lu_solve(lu, b - Kd @ v)
+        v = v + solve(b - Kd @ v)
     return v
 
 
 def inertia(K):
-    """(n_plus, n_zero, n_minus) of a symmetric matrix via Bunch-Kaufman
-    LDL^T and Sylvester's law of inertia."""
-    Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
-    _, d, _ = scipy.linalg.ldl(Kd, lower=True)
-    npos = nneg = nzero = 0
-    N = d.shape[0]
-    i = 0
-    while i < N:
-        if i + 1 < N and d[i + 1, i] != 0.0:
-            ev = np.linalg.eigvalsh(d[i:i + 2, i:i + 2])
-            i += 2
-        else:
-            ev = [d[i, i]]
-            i += 1
-        for e in ev:
-            if e > 0:
-                npos += 1
-            elif e < 0:
-                nneg += 1
-            else:
-                nzero += 1
-    return npos, nzero, nneg
+    """(n_plus, n_zero, n_minus) of a symmetric matrix: Sylvester's law of
+    inertia on the blocks of its Bunch-Kaufman LDL^T."""
+    return ldlt.factor(K).inertia()
 
 
 # ------------------------------------------------------------ hybrid O5/O6

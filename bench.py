@@ -43,7 +43,7 @@ PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 # dram__bytes_write.sum of its kernels in one ncu capture of this
 # benchmark), keyed by (trays, stages, solver, precision); other
 # configurations report null
-FACTOR_TRAFFIC = {}
+FACTOR_TRAFFIC = {(32, 5000, "supernodal", "fp64"): 484.5e6}
 DTYPE = {"fp64": "f64", "fp32": "f32 factor + f64 refinement", "df64": "df64 (float-pair) factor + f64 refinement"}
 UNIT = "ms/iter"
 

@@ -140,6 +140,24 @@ def test_hykkt_equals_dense(gamma):
     assert np.max(np.abs(vv - v)) <= 1e-7 * np.max(np.abs(v))
 
 
+@pytest.mark.parametrize("gamma", [1e2, 1e4, 1e7])
+def test_hykkt_inner_solve_is_exact_without_refinement(gamma):
+    """For every gamma, K_gamma and the Schur complement S_gamma reproduce
+    the KKT solution exactly (Eq. hykkt, Eq. schurcomp): one inner solve
+    with CG run to 1e-12 already gives the dense solution, no Richardson
+    sweep needed."""
+    p, pt, W, J = _tray_case(k=6, T=5, seed=2, sigma_range=(1e-2, 1e2))
+    sym = _sym(p, W, J, leaf_size=16)
+    delta_x = 20.0
+    K = kkt.kkt_matrix(p.n, p.m, W, J, pt.sigma, delta_x)
+    v = kkt.dense_solve(K, np.concatenate([pt.rx, pt.ry]))
+    dx, dy, info = kkt.hykkt_solve(sym, p.n, p.m, W, J, pt.sigma, delta_x, gamma,
+                                   pt.rx, pt.ry, tol_cg=1e-12, max_refine=0)
+    assert info.status == "ok" and info.refine_iters == 0
+    assert info.bwd_err <= 1e-12
+    assert np.max(np.abs(np.concatenate([dx, dy]) - v)) <= 1e-9 * np.max(np.abs(v))
+
+
 def test_lifted_relaxed_target_is_exact():
     """With target C = D^{-1} the condensed solve is exact (Eq. liftedkkt)."""
     p, pt, W, J = _tray_case(k=6, T=4, seed=4)
@@ -169,6 +187,31 @@ def test_lifted_refinement_converges_on_original_system():
     assert np.max(np.abs(np.concatenate([dx, dy]) - v)) <= 1e-6 * np.max(np.abs(v))
     # error contracts at least geometrically
     assert all(b2 < b1 for b1, b2 in zip(info.etas, info.etas[1:]))
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1e-3])
+def test_lifted_refinement_rate_closed_form(delta):
+    """Richardson with the Lifted-KKT preconditioner M = [[H, J^T], [J,
+    -delta I]] on K_orig = [[H, J^T], [J, 0]] maps the error by
+    M^{-1}(M - K_orig), whose nonzero eigenvalues are delta / (delta + mu_j)
+    for the eigenvalues mu_j of J H^{-1} J^T (Sec. IV-A, V-B): the backward
+    error contracts asymptotically by delta / (delta + mu_min)."""
+    p, pt, W, J = _tray_case(k=6, T=4, seed=6, sigma_range=(1e-2, 1e2))
+    sym = _sym(p, W, J, leaf_size=16)
+    delta_x = 30.0
+    H = kkt.hessian_block(p.n, W, pt.sigma, delta_x).toarray()
+    Jd = kkt.jacobian_matrix(p.n, p.m, J).toarray()
+    mu_min = np.linalg.eigvalsh(Jd @ np.linalg.solve(H, Jd.T))[0]
+    rho = delta / (delta + mu_min)
+    dx, dy, info = kkt.lifted_solve(sym, p.n, p.m, W, J, pt.sigma, delta_x,
+                                    np.full(p.m, 1.0 / delta), pt.rx, pt.ry,
+                                    tol=1e-14, max_refine=60)
+    etas = np.array(info.etas)
+    etas = etas[etas > 1e-13]                 # above the rounding floor
+    assert len(etas) >= 6
+    ratios = etas[1:] / etas[:-1]
+    assert abs(ratios[-1] / rho - 1.0) < 0.05, (ratios[-4:], rho)
+    assert np.all(ratios <= rho * 1.01)       # the slowest mode bounds every step
 
 
 def test_cg_exact_in_n_steps():

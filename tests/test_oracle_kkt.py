@@ -68,6 +68,31 @@ def test_cholesky_reports_first_failing_column():
     assert first == j0
 
 
+def test_cholesky_exact_zero_pivot_fails():
+    """[[1, 1], [1, 1]] is positive semidefinite: the second pivot is
+    exactly 1 - 1 * 1 = 0, which is not positive."""
+    structs = [np.array([0, 1]), np.array([1])]
+    with pytest.raises(cholesky.NotPositiveDefinite) as e:
+        cholesky.factor(2, structs, [{0: 1.0, 1: 1.0}, {1: 1.0}])
+    assert e.value.column == 1
+    vals = cholesky.factor(2, structs, [{0: 4.0, 1: 2.0}, {1: 5.0}])
+    assert np.array_equal(vals[0], [2.0, 1.0]) and np.array_equal(vals[1], [2.0])
+
+
+def test_cholesky_sums_duplicate_triplets():
+    """K given as the concatenated triplets of its summands (as assembly
+    produces it: W, the diagonal, J^T D J) factors like K itself."""
+    p, pt, W, J, Kr, Kc, Kv = _spd_case()
+    sym = _sym(p, W, J, leaf_size=16)
+    ref = cholesky.SparseCholesky(sym, p.n, Kr, Kc, Kv)
+    rng = np.random.default_rng(3)
+    split = rng.uniform(0.2, 0.8, len(Kv))
+    two = cholesky.SparseCholesky(sym, p.n, np.concatenate([Kr, Kr]), np.concatenate([Kc, Kc]),
+                                  np.concatenate([Kv * split, Kv * (1.0 - split)]))
+    for a, b in zip(ref.vals, two.vals):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-12 * np.max(np.abs(a)))
+
+
 def test_dense_solve_small_closed_form():
     # [[2, 1], [1, 0]] [x; y] = [3; 1]  ->  x = 1, y = 1
     K = np.array([[2.0, 1.0], [1.0, 0.0]])

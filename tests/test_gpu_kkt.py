@@ -21,11 +21,14 @@ def _built():
     ensure_built()
 
 
-@pytest.mark.parametrize("k,T", [(32, 50), (5, 7), (32, 0), (3, 4)])
-def test_tray_eval_matches_oracle(k, T):
+# the last case has non-default holdup, control weight, step, volatility and
+# feed composition, so a constant dropped on either side cannot hide behind 1
+@pytest.mark.parametrize("k,T,kw", [(32, 50, {}), (5, 7, {}), (32, 0, {}), (3, 4, {}),
+                                    (6, 5, dict(M=2.0, rho=0.7, h=0.05, alpha=1.9, xf=0.4))])
+def test_tray_eval_matches_oracle(k, T, kw):
     torch = torch_cuda()
     from paper_2403_15913_gb300 import TrayModel
-    p = TrayParams(k=k, T=T)
+    p = TrayParams(k=k, T=T, **kw)
     pt = kkt_point(p, 11)
     tm = TrayModel(p.as_array())
     w, lam = to_dev(torch, pt.w), to_dev(torch, pt.lam)

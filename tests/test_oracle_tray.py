@@ -26,9 +26,14 @@ def _dense_sym_lower(n, colptr, rowind, val):
     return A
 
 
-@pytest.mark.parametrize("k,T", [(4, 2), (32, 2), (6, 3)])
-def test_jacobian_complex_step(k, T):
-    p = TrayParams(k=k, T=T)
+# non-default constants (holdup, control weight, step, volatility, feed) so
+# that a dropped M_n, rho or h cannot hide behind a value of 1
+ODD = dict(M=2.0, rho=0.7, h=0.05, alpha=1.9, xf=0.4)
+
+
+@pytest.mark.parametrize("k,T,kw", [(4, 2, {}), (32, 2, {}), (6, 3, {}), (6, 3, ODD)])
+def test_jacobian_complex_step(k, T, kw):
+    p = TrayParams(k=k, T=T, **kw)
     pt = kkt_point(p, seed=3)
     J = _dense_jac(p, pt.w)
     for j in range(p.n):
@@ -38,9 +43,9 @@ def test_jacobian_complex_step(k, T):
         assert np.allclose(J[:, j], col, rtol=1e-13, atol=1e-13), j
 
 
-@pytest.mark.parametrize("k,T", [(4, 2), (32, 1), (6, 3)])
-def test_hessian_complex_step(k, T):
-    p = TrayParams(k=k, T=T)
+@pytest.mark.parametrize("k,T,kw", [(4, 2, {}), (32, 1, {}), (6, 3, {}), (6, 3, ODD)])
+def test_hessian_complex_step(k, T, kw):
+    p = TrayParams(k=k, T=T, **kw)
     pt = kkt_point(p, seed=5)
     W = _dense_sym_lower(p.n, *tray.hessian_lower_csc(p, pt.w, pt.lam, 0.7))
     for j in range(p.n):
@@ -50,14 +55,25 @@ def test_hessian_complex_step(k, T):
         assert np.allclose(W[:, j], col, rtol=1e-12, atol=1e-12), j
 
 
-def test_gradient_complex_step():
-    p = TrayParams(k=5, T=3)
+@pytest.mark.parametrize("kw", [{}, ODD])
+def test_gradient_complex_step(kw):
+    p = TrayParams(k=5, T=3, **kw)
     pt = kkt_point(p, seed=1)
     g = tray.objective_grad(p, pt.w)
     for j in range(p.n):
         wc = pt.w.astype(complex)
         wc[j] += 1j * EPS
         assert abs(tray.objective(p, wc).imag / EPS - g[j]) < 1e-13
+
+
+def test_dynamics_scale_with_step_over_holdup():
+    """Implicit Euler of M xdot = g: the dynamics rows depend on h and M only
+    through h / M (doubling both changes nothing; doubling M alone does)."""
+    w = kkt_point(TrayParams(k=6, T=3), seed=2).w
+    dyn = lambda p: tray.constraints(p, w).reshape(p.T + 1, 2 * p.k)[1:, :p.k]
+    base = dyn(TrayParams(k=6, T=3, h=0.1, M=1.0))
+    assert np.allclose(dyn(TrayParams(k=6, T=3, h=0.2, M=2.0)), base, rtol=1e-15, atol=1e-16)
+    assert np.max(np.abs(dyn(TrayParams(k=6, T=3, h=0.1, M=2.0)) - base)) > 1e-3
 
 
 def test_mass_balance_closed_form():

@@ -115,3 +115,28 @@ def test_analyse_rejects_bad_patterns(nat):
         KKTSolver(3, 0, [0, 2, 3, 4], [0, 1, 0, 2], [0], [], host_only=True)
     with pytest.raises(KKTError):   # J column out of range
         KKTSolver(3, 1, [0, 1, 2, 3], [0, 1, 2], [0, 1], [7], host_only=True)
+
+
+# the hand-worked graphs of the oracle's symbolic pins (even-length path,
+# pendant at the separator level, pseudo-peripheral choice, fill in minimum
+# degree), each as the pattern of W with no J, at the smallest leaf size
+WORKED_GRAPHS = [
+    (6, [(i, i + 1) for i in range(5)]),
+    (6, [(0, 1), (1, 2), (2, 3), (3, 4), (1, 5)]),
+    (7, [(0, 1), (0, 4), (1, 3), (1, 6), (2, 4), (2, 5), (4, 5)]),
+    (6, [(0, 1), (0, 3), (1, 5), (2, 3), (2, 4), (2, 5)]),
+    (15, [(i, i + 1) for i in range(14)]),
+]
+
+
+@pytest.mark.parametrize("leaf", [1, 3])
+@pytest.mark.parametrize("n,edges", WORKED_GRAPHS)
+def test_symbolic_bit_exact_worked_graphs(nat, n, edges, leaf):
+    lower = [set([j]) for j in range(n)]
+    for a, b in edges:
+        lower[min(a, b)].add(max(a, b))
+    colptr = np.cumsum([0] + [len(s) for s in lower])
+    rowind = np.concatenate([sorted(s) for s in lower])
+    pats = (colptr.astype(np.int64), rowind.astype(np.int64), np.zeros(1, np.int64),
+            np.zeros(0, np.int64))
+    _compare(None, pats, n, leaf_size=leaf, relax_cols=0, relax_zeros=0, max_width=0)

@@ -71,6 +71,88 @@ def test_minimum_degree_star_and_ties():
     assert symbolic.minimum_degree(adj, set(range(4))) == [0, 1, 2, 3]
 
 
+def test_path_of_even_length_splits_at_lower_middle():
+    # 0-1-2-3-4-5: five levels from node 0 (e = 5), separator level
+    # floor(5/2) = 2; then {0, 1} has e = 1 (a leaf) and {3, 4, 5} splits at 4
+    adj = _graph_from_edges(6, [(i, i + 1) for i in range(5)])
+    assert symbolic.nested_dissection(adj, leaf_size=1).tolist() == [0, 1, 3, 5, 4, 2]
+
+
+def test_separator_takes_only_nodes_facing_the_next_level():
+    # path 0-1-2-3-4 with a pendant 5 on node 1: levels from 0 are {0}, {1},
+    # {2, 5}, {3}, {4} (node 4's structure is no deeper); the middle level is
+    # {2, 5} but only 2 touches level 3, so the separator is {2}
+    adj = _graph_from_edges(6, [(0, 1), (1, 2), (2, 3), (3, 4), (1, 5)])
+    assert symbolic.nested_dissection(adj, leaf_size=1).tolist() == [0, 5, 1, 3, 4, 2]
+
+
+def test_pseudo_peripheral_node_worked_case():
+    # from 0: last level {2, 3, 5, 6}; degree-1 nodes 3 and 6, tie to 3;
+    # eccentricity of 3 is 4 > 2; from 3 the last level is {2, 5} (degree 2
+    # each, tie to 2), whose eccentricity is not larger: node 3
+    adj = _graph_from_edges(7, [(0, 1), (0, 4), (1, 3), (1, 6), (2, 4), (2, 5), (4, 5)])
+    r, levels = symbolic.pseudo_peripheral(adj, set(range(7)))
+    assert r == 3
+    assert [sorted(l) for l in levels] == [[3], [1], [0, 6], [4], [2, 5]]
+
+
+def test_minimum_degree_counts_fill():
+    # degrees 2,2,3,2,1,2: eliminate 4; then all degree 2, eliminate 0, which
+    # joins 1 and 3; 1 (degree 2: 3, 5) next, which joins 3 and 5; then 2,
+    # 3, 5 (without the fill edges 3 would go before 2)
+    adj = _graph_from_edges(6, [(0, 1), (0, 3), (1, 5), (2, 3), (2, 4), (2, 5)])
+    assert symbolic.minimum_degree(adj, set(range(6))) == [4, 0, 1, 2, 3, 5]
+
+
+def test_graph_is_pattern_of_W_plus_JtJ():
+    """Adjacency of pattern(W + J^T J) against a sparse product of the
+    patterns (positive values, so no cancellation)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(4)
+    n, m = 30, 18
+    Wd = np.tril(rng.random((n, n)) < 0.08)
+    np.fill_diagonal(Wd, True)
+    Jd = rng.random((m, n)) < 0.12
+    Wc = sp.csc_matrix(Wd.astype(float))
+    Jc = sp.csr_matrix(Jd.astype(float))
+    adj = symbolic.kkt_graph(n, Wc.indptr, Wc.indices, Jc.indptr, Jc.indices)
+    P = (abs(Wc) + abs(Wc).T + Jc.T @ Jc).toarray() != 0
+    np.fill_diagonal(P, False)
+    for v in range(n):
+        assert adj[v] == np.nonzero(P[v])[0].tolist()
+
+
+def test_postorder_visits_children_in_increasing_index():
+    # node 3 has children 0 and 2, node 2 has child 1
+    assert symbolic.postorder(np.array([3, 2, 3, -1])).tolist() == [0, 1, 2, 3]
+    # two roots, 2 (children 0, 1) and 4 (child 3)
+    assert symbolic.postorder(np.array([2, 2, -1, 4, -1])).tolist() == [0, 1, 2, 3, 4]
+
+
+@pytest.mark.parametrize("parent,cc,ptr", [
+    # chain 0 -> 1 -> 2 with nested structures: one supernode
+    ([1, 2, -1], [3, 2, 1], [0, 3]),
+    # column 1 holds a row that column 0 lacks (cc equal): 0 stands alone
+    ([1, 2, -1], [2, 2, 1], [0, 1, 3]),
+    # node 2 has two children: neither joins it
+    ([2, 2, -1], [2, 2, 1], [0, 1, 2, 3]),
+])
+def test_fundamental_supernodes_worked_cases(parent, cc, ptr):
+    assert symbolic.fundamental_supernodes(np.array(parent), np.array(cc)) == ptr
+
+
+@pytest.mark.parametrize("zeros,ptr", [(0, [0, 1, 3]), (1, [0, 3])])
+def test_relaxation_counts_explicit_zeros(zeros, ptr):
+    # fundamental supernodes {0}, {1}, {2} with rows {0, 2}, {1, 2}, {2} and
+    # parent(0) = parent(1) = 2.  Backward: {1} joins {2} with no zero (3 of
+    # 3 panel slots are in L); {0} joining {1, 2} gives a 3 x 3 lower
+    # triangle of 6 slots with 5 entries of L: one explicit zero, (1, 0)
+    rows = [np.array([0, 2]), np.array([1, 2]), np.array([2])]
+    got = symbolic.relax_and_split([0, 1, 2, 3], np.array([2, 2, 1]), np.array([2, 2, -1]),
+                                   rows, relax_cols=8, relax_zeros=zeros, max_width=0)
+    assert got == ptr
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_elimination_game_matches(seed):
     rng = np.random.default_rng(seed)
@@ -86,6 +168,19 @@ def test_elimination_game_matches(seed):
         below = game[j][1:]
         assert sym.parent[j] == (below[0] if below else -1)
         assert sym.colcount[j] == len(game[j])
+    # the final labels are a postorder: every subtree is the contiguous range
+    # of labels ending at its root
+    size = np.ones(n, dtype=int)
+    for j in range(n):
+        if sym.parent[j] >= 0:
+            size[sym.parent[j]] += size[j]
+    for j in range(n):
+        lo = j - size[j] + 1
+        for i in range(lo, j):
+            a = i
+            while a != -1 and a != j:
+                a = sym.parent[a]
+            assert a == j
 
 
 @pytest.mark.parametrize("relax", [(0, 0, 0), (48, 1024, 64), (16, 40, 5)])

@@ -38,7 +38,13 @@ Iteration (one call of ``step``):
 
 Parity: pinned by tests (closed-form box-constrained QP; the optimum of a tiny
 column instance against scipy's trust-constr; equal iteration counts and
-iterates for the exact dense solver and HyKKT).
+iterates for the exact dense solver and HyKKT; the barrier parameters drawn,
+in order, from the published Fiacco-McCormick sequence; accepted steps equal
+to the fraction-to-boundary step halved once per rejected trial).  The other
+rule details of the cited filter method (Armijo and filter acceptance,
+filter augmentation, the multiplier safeguard, the scaling of the optimality
+error, the dual step length) change iteration counts, not the optimum: they
+are pinned only through the optimum.
 """
 from __future__ import annotations
 
@@ -322,6 +328,7 @@ class IPM:
         if o.relaxed:
             dphi += float(gphi_s @ ds)
         alpha = a_pr
+        info.extra["alpha_max"] = a_pr
         accepted = False
         ls = 0
         for ls in range(1, o.max_ls + 1):

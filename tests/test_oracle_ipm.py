@@ -46,6 +46,43 @@ class SimplexQP:
         return np.clip(self.a - lam, 0, 1)
 
 
+# Fiacco-McCormick barrier sequence of the cited filter method with mu_0 = 0.1,
+# kappa_mu = 0.2, theta_mu = 1.5: 0.1, then min(0.2 mu, mu^1.5) at every
+# update, never below tol/10 (tol = 1e-10): 0.1, 0.02, 0.02^1.5, ...
+MU_SEQUENCE = [0.1, 0.02, 2.828427124746191e-03, 1.5042412372345582e-04,
+               1.8449144625279508e-06, 2.5059035596800618e-09, 1e-11]
+
+
+def test_barrier_parameter_follows_the_published_sequence():
+    a = np.random.default_rng(5).uniform(-0.5, 1.5, 12)
+    qp = SimplexQP(a, 4.0)
+    lin = ipm.KKTLinearSolver("dense", qp.n, qp.m, None, None)
+    s = ipm.IPM(qp, lin, ipm.IPMOptions(tol=1e-10), np.full(qp.n, 0.5))
+    assert s.solve().status == "converged"
+    used = [h.mu for h in s.history]
+    seen = []
+    for u in used:
+        assert any(u == pytest.approx(v, rel=1e-12) for v in MU_SEQUENCE), u
+        if not seen or u != seen[-1]:
+            seen.append(u)
+    # monotone and without skipping a value of the sequence
+    idx = [next(i for i, v in enumerate(MU_SEQUENCE) if u == pytest.approx(v, rel=1e-12))
+           for u in seen]
+    assert idx == list(range(idx[0], idx[0] + len(idx)))
+    assert len(seen) >= 4
+
+
+def test_backtracking_halves_the_fraction_to_boundary_step():
+    """Every accepted step is the largest fraction-to-boundary step halved
+    once per rejected trial."""
+    s, last = _tray_ipm(TrayParams(k=4, T=3), "lifted", relaxed=True)
+    assert last.status == "converged"
+    steps = [h for h in s.history if h.status == "ok"]
+    assert any(h.ls > 1 for h in steps)
+    for h in steps:
+        assert h.alpha_pr == h.extra["alpha_max"] * 0.5 ** (h.ls - 1)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_qp_closed_form(seed):
     rng = np.random.default_rng(seed)

@@ -54,9 +54,11 @@ typedef enum {
     KKT_ERR_NOT_SPD = -4,   /* non-positive pivot: kkt_info.failed_col is set */
     KKT_ERR_MAXIT = -5,     /* CG or refinement hit its iteration limit       */
     KKT_ERR_STALL = -6,     /* refinement stopped improving (eta stagnated)   */
-    KKT_ERR_TIMEOUT = -7,   /* a bounded device wait gave up                  */
+    KKT_ERR_TIMEOUT = -7,   /* reserved: no call of this library waits on the
+                               device with a time limit, so none returns it  */
     KKT_ERR_STATE = -8,     /* call out of order (e.g. solve before factor)   */
-    KKT_ERR_INTERNAL = -9   /* a device-side index check failed               */
+    KKT_ERR_INTERNAL = -9   /* a consistency check of the analysis' index
+                               maps failed on the host (a library bug)       */
 } kkt_status;
 
 typedef enum { KKT_LIFTED = 0, KKT_HYKKT = 1 } kkt_scheme;

@@ -188,7 +188,8 @@ kkt_status kkt_factor(kkt_ctx* ctx, const double* d_Wval, const double* d_Jval,
 
 /* Solve K_orig [dx; dy] = [r_x; r_y] with the factor of the last
  * kkt_factor (scheme per options), refining until eta <= tol_refine.
- *   d_rx[n], d_ry[m] in; d_dx[n], d_dy[m] out;
+ *   d_rx[n], d_ry[m] in; d_dx[n], d_dy[m] out (all four non-NULL, else
+ *   KKT_ERR_ARG);
  *   d_ds[m] (may be NULL): relaxed target only, ds = J dx - r_y.
  * Returns KKT_ERR_MAXIT / KKT_ERR_STALL when the tolerance is not reached
  * (the best iterate is still written) and KKT_ERR_STATE without a factor. */

@@ -225,6 +225,41 @@ def test_edge_sizes(k, T):
         assert np.max(np.abs(np.concatenate([dx, dy]) - v)) <= 1e-8 * np.max(np.abs(v))
 
 
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (5, 3), (9, 8)])
+def test_smallest_general_patterns(n, m):
+    """Systems that are not column models, down to one variable and one
+    constraint (one supernode, a 1 x 1 Schur complement), with every J row
+    touching one or two variables."""
+    torch = torch_cuda()
+    from paper_2403_15913_gb300 import KKTSolver
+    rng = np.random.default_rng(10 * n + m)
+    lower = [sorted(set([j] + [int(i) for i in rng.integers(j, n, 2)])) for j in range(n)]
+    Wc = np.cumsum([0] + [len(l) for l in lower]).astype(np.int64)
+    Wr = np.concatenate(lower).astype(np.int64)
+    Wv = np.array([float(n + 1) if i == j else rng.uniform(-1, 1)
+                   for j in range(n) for i in lower[j]])
+    # row r touches variable r % n (so J has full row rank for m <= n) and maybe one more
+    rows = [sorted(set([r % n] + ([int(rng.integers(0, n))] if rng.random() < 0.5 else [])))
+            for r in range(m)]
+    Jr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    Jc = np.concatenate(rows).astype(np.int64)
+    Jv = rng.uniform(0.5, 1.5, len(Jc)) * rng.choice([-1.0, 1.0], len(Jc))
+    sigma = rng.uniform(0.1, 1.0, n)
+    rx, ry = rng.standard_normal(n), rng.standard_normal(m)
+    K = okkt.kkt_matrix(n, m, (Wc, Wr, Wv), (Jr, Jc, Jv), sigma, 0.0)
+    v = okkt.dense_solve(K, np.concatenate([rx, ry]))
+    for scheme in ("lifted", "hykkt"):
+        s = KKTSolver(n, m, Wc, Wr, Jr, Jc, scheme=scheme, gamma=1e4, tol_refine=1e-14, **OPTS)
+        assert s.factor(to_dev(torch, Wv), to_dev(torch, Jv), to_dev(torch, sigma), None, 0.0) == 0
+        dx = torch.zeros(n, dtype=torch.float64, device="cuda")
+        dy = torch.zeros(m, dtype=torch.float64, device="cuda")
+        st = s.solve(to_dev(torch, rx), to_dev(torch, ry), dx, dy)
+        assert st in (0, -6), s.last_error()       # STALL: at the rounding floor
+        got = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
+        assert np.max(np.abs(got - v)) <= 1e-9 * np.max(np.abs(v)), scheme
+        s.close()
+
+
 @pytest.mark.parametrize("scheme", ["lifted", "hykkt"])
 def test_full_size_workload_backward_error(scheme):
     """The benchmark workload (32 trays, T = 5000, n = 325,065) in the

@@ -86,6 +86,30 @@ MUTANTS = [
     ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
      'v = v + precond(r)',
      'v = precond(r)'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'vals = np.concatenate([v, v[off], np.asarray(sigma) + delta_x])',
+     'vals = np.concatenate([v, v[off], np.asarray(sigma)])'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'vals = np.concatenate([v, v[off], np.asarray(sigma) + delta_x])',
+     'vals = np.concatenate([v, v, np.asarray(sigma) + delta_x])'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'Cm = sp.diags(np.zeros(m) if C is None else -np.asarray(C))',
+     'Cm = sp.diags(np.zeros(m) if C is None else np.asarray(C))'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'return sp.bmat([[H, Jm.T], [Jm, Cm]], format="csr")',
+     'return sp.bmat([[H, Jm], [Jm.T, Cm]], format="csr")'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'K = (H + Jm.T @ sp.diags(np.asarray(D)) @ Jm).tocoo()',
+     'K = (H + Jm.T @ Jm).tocoo()'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'return float(np.max(np.abs(r)) / (kn * np.max(np.abs(v)) + np.max(np.abs(b))))',
+     'return float(np.max(np.abs(r)) / (kn * np.max(np.abs(v))))'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'return float(np.max(np.asarray(abs(K).sum(axis=1)).ravel()))',
+     'return float(np.max(np.asarray(abs(K).sum(axis=0)).ravel()) * 0.5)'),
+    ('oracle/kkt.py', 'tests/test_oracle_kkt.py',
+     'for _ in range(refine_steps):\n        v = v + solve(b - Kd @ v)',
+     'for _ in range(refine_steps):\n        v = solve(b - Kd @ v)'),
     # oracle/cholesky.py  (pins: tests/test_oracle_kkt.py)
     ('oracle/cholesky.py', 'tests/test_oracle_kkt.py',
      'keep = r >= c',

@@ -96,9 +96,26 @@ def test_cholesky_sums_duplicate_triplets():
 def test_dense_solve_small_closed_form():
     # [[2, 1], [1, 0]] [x; y] = [3; 1]  ->  x = 1, y = 1
     K = np.array([[2.0, 1.0], [1.0, 0.0]])
-    v = kkt.dense_solve(K, np.array([3.0, 1.0]))
-    assert np.allclose(v, [1.0, 1.0], rtol=0, atol=1e-15)
+    for steps in range(4):          # any number of refinement steps, odd or even
+        v = kkt.dense_solve(K, np.array([3.0, 1.0]), refine_steps=steps)
+        assert np.allclose(v, [1.0, 1.0], rtol=0, atol=1e-15), steps
     assert kkt.inertia(K) == (1, 0, 1)
+
+
+def test_backward_error_and_norm_worked_values():
+    """Rigal-Gaches normwise backward error
+    eta = ||b - K v||_inf / (||K||_inf ||v||_inf + ||b||_inf) and the
+    infinity norm (largest absolute row sum) on hand-computed cases."""
+    K = np.array([[1.0, -2.0], [3.0, 4.0]])
+    assert kkt.inf_norm(K) == 7.0
+    import scipy.sparse as sps
+    assert kkt.inf_norm(sps.csr_matrix(K)) == 7.0
+    # K = I: v = (1, 0), b = (2, 0): residual 1, eta = 1 / (1 * 1 + 2)
+    assert kkt.backward_error(np.eye(2), np.array([1.0, 0.0]), np.array([2.0, 0.0])) == 1.0 / 3.0
+    # v = 0 is never better than eta = 1
+    assert kkt.backward_error(K, np.zeros(2), np.array([1.0, -5.0])) == 1.0
+    # an exact solution has eta = 0
+    assert kkt.backward_error(K, np.array([1.0, 1.0]), np.array([-1.0, 7.0])) == 0.0
 
 
 def test_condensation_recovers_augmented_solution():

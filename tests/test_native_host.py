@@ -140,3 +140,30 @@ def test_symbolic_bit_exact_worked_graphs(nat, n, edges, leaf):
     pats = (colptr.astype(np.int64), rowind.astype(np.int64), np.zeros(1, np.int64),
             np.zeros(0, np.int64))
     _compare(None, pats, n, leaf_size=leaf, relax_cols=0, relax_zeros=0, max_width=0)
+
+
+def test_missing_library_fails_loudly(nat, monkeypatch):
+    """Without the CUDA library every entry point raises: there is no CPU
+    or library fallback behind the binding."""
+    from paper_2403_15913_gb300 import KKTSolver
+    monkeypatch.setattr(nat, "_lib", None)
+    monkeypatch.setattr(nat, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libkkt_gb300.so"))
+    p = TrayParams(k=3, T=1)
+    pt = kkt_point(p, 0)
+    W = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = tray.jacobian_csr(p, pt.w)
+    with pytest.raises(RuntimeError, match="missing"):
+        KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], host_only=True)
+
+
+def test_product_package_imports_no_oracle_or_fallback():
+    """The binding marshals arguments only: no module of the package imports
+    the oracle, or a compiler or library that could stand in for the
+    kernels."""
+    pkg = os.path.join(ROOT, "paper_2403_15913_gb300")
+    banned = re.compile(r"^\s*(from|import)\s+(oracle|triton|numba|cupy)\b|torch\.compile|scipy",
+                        re.M)
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert not banned.search(src), name

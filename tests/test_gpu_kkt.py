@@ -111,6 +111,29 @@ def test_not_spd_reports_oracle_column():
         s.solve(z, zy, z.clone(), zy.clone())
 
 
+@pytest.mark.parametrize("where,bad", [("W", np.nan), ("J", np.inf), ("sigma", np.nan),
+                                       ("sigma", -np.inf)])
+def test_nonfinite_values_report_oracle_column(where, bad):
+    """A NaN or infinity injected on the host into W, J or Sigma reaches a
+    pivot: the factor reports KKT_ERR_NOT_SPD at the oracle's first failing
+    column (the library never returns a factor built on it)."""
+    torch = torch_cuda()
+    p, pt, W, J = instance(8, 12, seed=3, sigma_range=(1e-2, 1e2))
+    Wv, Jv, sig = W[2].copy(), J[2].copy(), pt.sigma.copy()
+    target = {"W": Wv, "J": Jv, "sigma": sig}[where]
+    target[len(target) // 2] = bad
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **OPTS)
+    Kr, Kc, Kv = okkt.condensed_coo(p.n, (W[0], W[1], Wv), (J[0], J[1], Jv), sig, 1.0,
+                                    np.full(p.m, 1e2))
+    with pytest.raises(cholesky.NotPositiveDefinite) as e, np.errstate(invalid="ignore"):
+        cholesky.SparseCholesky(sym, p.n, Kr, Kc, Kv)
+    s = solver_for(p, W, J, scheme="lifted", **OPTS)
+    st = s.factor(to_dev(torch, Wv), to_dev(torch, Jv), to_dev(torch, sig),
+                  to_dev(torch, np.full(p.m, 1e2)), 1.0)
+    assert st == -4
+    assert s.info.failed_col == e.value.column
+
+
 @pytest.mark.parametrize("sig,D,dx0", [((1e-2, 1e2), 1e2, 10.0), ((1e-6, 1e6), 1e8, 0.0)])
 def test_backsolve_matches_oracle(sig, D, dx0):
     """K^{-1} b by the supernodal triangular solves equals the oracle's

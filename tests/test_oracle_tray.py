@@ -161,6 +161,42 @@ def test_table1_structure_is_a_different_variant():
     assert abs(per_stage / 837 - 1) < 0.03
 
 
+def _constants():
+    path = os.path.join(os.path.dirname(__file__), "golden", "column_constants.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, val = line.split()
+            out[key] = float(val)
+    return out
+
+
+def test_column_constants_and_tray_sections_follow_the_paper():
+    """The printed constants (fixture in tests/golden) are the generator's
+    defaults, and the liquid flow entering each tray from the one above is
+    L_t on trays 2..17 and S_t on trays 18..32 (rectifying section, feed,
+    stripping section, reboiler), read off by complex-step differentiation
+    of the tray balances."""
+    c = _constants()
+    p = TrayParams()
+    assert p.k == c["trays"] and p.alpha == c["alpha"] and p.D == c["D"] and p.F == c["F"]
+    assert p.rho == c["rho"] and p.u_lo == c["u_lo"] and p.u_hi == c["u_hi"]
+    assert p.feed + 1 == c["feed_tray"]
+    u = np.array([3.0])                      # L = 0.6, S = 1.0
+    L, V, S = tray.flows(p, u)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0.1, 0.9, (1, p.k))
+    y = rng.uniform(0.1, 0.9, (1, p.k))
+    for n1 in range(2, p.k + 1):             # 1-based tray receiving liquid from n1 - 1
+        xc = x.astype(complex)
+        xc[0, n1 - 2] += 1j * EPS
+        d = tray.balance(p, xc, y, u)[0, n1 - 1].imag / EPS
+        want = L[0] if n1 <= c["feed_tray"] else S[0]
+        assert abs(d - want) < 1e-14, n1
+    assert c["rectifying_last"] + 1 == c["feed_tray"] == c["stripping_first"] - 1
+    assert c["stripping_last"] + 1 == c["trays"]
+
+
 def test_initial_state_vector():
     """A per-tray initial state changes only the stage-0 composition rows,
     which become x_{i,0} - x0_i exactly; x0 = x0bar everywhere reproduces

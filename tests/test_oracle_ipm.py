@@ -118,6 +118,24 @@ def _tray_ipm(p, kind, relaxed=False, tol=1e-8):
     return s, s.solve()
 
 
+def test_hykkt_cg_needs_few_iterations_at_large_gamma():
+    """Sec. V-B: with gamma = 1e7 the unpreconditioned CG on S_gamma takes
+    fewer than 10 iterations on average over the IPM's linear solves (the
+    eigenvalues of gamma S_gamma cluster at 1)."""
+    p = TrayParams(k=16, T=20)
+    mdl = ipm.TrayModel(p)
+    x0 = ipm_start(p)
+    W = tray.hessian_lower_csc(p, x0, np.zeros(p.m))
+    J = tray.jacobian_csr(p, x0)
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=16, relax_cols=16,
+                           relax_zeros=64, max_width=16)
+    lin = ipm.KKTLinearSolver("hykkt", p.n, p.m, None, None, sym=sym, gamma=1e7)
+    s = ipm.IPM(mdl, lin, ipm.IPMOptions(tol=1e-8), x0)
+    assert s.solve().status == "converged"
+    per_solve = [i.cg_iters / (i.refine_iters + 1) for i in lin.stats]
+    assert len(per_solve) >= 3 and np.mean(per_solve) < 10
+
+
 def test_tray_optimum_matches_scipy():
     p = TrayParams(k=4, T=3)
     s, last = _tray_ipm(p, "hykkt", tol=1e-9)

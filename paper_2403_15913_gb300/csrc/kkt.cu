@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1336,15 +1338,22 @@ kkt_status analyse_common(int n, int m, const int* W_colptr, const int* W_rowind
     TRY(new_ctx(opt, &c));
     c->n = n;
     c->m = m;
-    Graph g;
-    std::string e = build_graph(n, m, W_colptr, W_rowind, J_rowptr, J_colind, g);
-    if (!e.empty()) {
+    std::string e;
+    try {
+        Graph g;
+        e = build_graph(n, m, W_colptr, W_rowind, J_rowptr, J_colind, g);
+        if (e.empty()) {
+            c->nnzW = W_colptr[n];
+            c->nnzJ = J_rowptr[m];
+            e = analyse(g, symbolic_options(c->opt), c->sym);
+        }
+    } catch (const std::bad_alloc&) {
         delete c;
-        return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
+        return set_err(nullptr, KKT_ERR_OOM, "kkt_analyse: host allocation failed");
+    } catch (const std::exception& ex) {
+        delete c;
+        return set_err(nullptr, KKT_ERR_INTERNAL, std::string("kkt_analyse: ") + ex.what());
     }
-    c->nnzW = W_colptr[n];
-    c->nnzJ = J_rowptr[m];
-    e = analyse(g, symbolic_options(c->opt), c->sym);
     if (!e.empty()) {
         delete c;
         return set_err(nullptr, KKT_ERR_ARG, "kkt_analyse: " + e);
@@ -1380,13 +1389,18 @@ kkt_status analyse_batch(int count, const int* n, const int* m, const int* const
     TRY(new_ctx(opt, &c));
     std::vector<Symbolic> parts(count);
     std::vector<std::string> errs(count);
-    const SymbolicOptions so = symbolic_options(c->opt);
+    SymbolicOptions so = symbolic_options(c->opt);
+    so.parallel = false;   // the instances themselves run on the worker threads
     std::atomic<int> next(0);
     auto work = [&]() {
         for (int i = next++; i < count; i = next++) {
-            Graph g;
-            errs[i] = build_graph(n[i], m[i], W_colptr[i], W_rowind[i], J_rowptr[i], J_colind[i], g);
-            if (errs[i].empty()) errs[i] = analyse(g, so, parts[i]);
+            try {
+                Graph g;
+                errs[i] = build_graph(n[i], m[i], W_colptr[i], W_rowind[i], J_rowptr[i], J_colind[i], g);
+                if (errs[i].empty()) errs[i] = analyse(g, so, parts[i]);
+            } catch (const std::exception& ex) {
+                errs[i] = std::string("analysis failed: ") + ex.what();
+            }
         }
     };
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());

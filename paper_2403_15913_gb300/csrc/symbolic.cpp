@@ -25,7 +25,9 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <future>
 #include <numeric>
 #include <set>
 
@@ -89,18 +91,33 @@ std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
 namespace {
 
 // ----------------------------------------------------------- nested dissection
+//
+// The components left by a separator are disconnected from one another, and
+// every node adjacent to one of them is already numbered (tag 0, never
+// written again), so the recursion on sibling components touches disjoint
+// entries of tag / stamp / level.  The top levels of the recursion therefore
+// run sibling components on their own threads, each writing its ordering into
+// its own vector; the vectors are concatenated in component order, so the
+// result is the one of the sequential recursion.  Tags and stamps only encode
+// membership and visits: any unique value works, so both come from atomic
+// counters.
+constexpr int kParallelDepth = 4;         // recursion levels that fork
+constexpr int kParallelMinNodes = 4096;   // smaller components stay sequential
+
 struct NestedDissection {
     const Graph& g;
     int leaf;
+    bool parallel;
     std::vector<int> tag;     // set membership: nodes of the component being
                               // processed carry its tag; numbered nodes carry 0
-    int next_tag = 1;
+    std::atomic<int> next_tag{1};
     std::vector<int> stamp;   // BFS visit stamps
     std::vector<int> level;   // BFS level of stamped nodes
-    int cur_stamp = 0;
+    std::atomic<int> next_stamp{0};
     std::vector<int> order;
 
-    NestedDissection(const Graph& g_, int leaf_) : g(g_), leaf(leaf_) {
+    NestedDissection(const Graph& g_, int leaf_, bool parallel_)
+        : g(g_), leaf(leaf_), parallel(parallel_) {
         tag.assign(g.n, 0);
         stamp.assign(g.n, 0);
         level.assign(g.n, -1);
@@ -108,9 +125,9 @@ struct NestedDissection {
     }
 
     // BFS level structure of root inside the nodes tagged t; returns the
-    // flat node list and level pointers.
-    void bfs(int root, int t, std::vector<int>& nodes, std::vector<int>& lptr) {
-        ++cur_stamp;
+    // flat node list and level pointers, and the stamp its visits carry.
+    int bfs(int root, int t, std::vector<int>& nodes, std::vector<int>& lptr) {
+        const int cur_stamp = ++next_stamp;
         nodes.clear();
         lptr.clear();
         nodes.push_back(root);
@@ -138,6 +155,7 @@ struct NestedDissection {
         }
         // lptr has one entry per level start plus the final end
         lptr.back() = (int)nodes.size();
+        return cur_stamp;
     }
 
     int degree_in(int v, int t) const {
@@ -174,7 +192,7 @@ struct NestedDissection {
         }
     }
 
-    void minimum_degree(const std::vector<int>& comp, int t) {
+    void minimum_degree(const std::vector<int>& comp, int t, std::vector<int>& order) {
         const int c = (int)comp.size();
         if (c == 0) return;
         // local index = rank in the sorted component (so ties to the
@@ -262,8 +280,8 @@ struct NestedDissection {
         }
     }
 
-    void component(const std::vector<int>& comp, int t) {
-        if ((int)comp.size() <= leaf) { minimum_degree(comp, t); return; }
+    void component(const std::vector<int>& comp, int t, std::vector<int>& order, int depth) {
+        if ((int)comp.size() <= leaf) { minimum_degree(comp, t, order); return; }
         std::vector<int> nodes, lptr, nodes2, lptr2;
         int r = comp[0];
         bfs(r, t, nodes, lptr);
@@ -286,9 +304,9 @@ struct NestedDissection {
         }
         // `nodes`/`lptr` hold the level structure of r; re-run it so that the
         // stamps/levels correspond to r (the last BFS was of the candidate)
-        bfs(r, t, nodes, lptr);
+        const int cur_stamp = bfs(r, t, nodes, lptr);
         int e = (int)lptr.size() - 2;   // levels 0..e
-        if (e < 2) { minimum_degree(comp, t); return; }
+        if (e < 2) { minimum_degree(comp, t, order); return; }
         int lv = e / 2;
         std::vector<int> sep;
         for (int q = lptr[lv]; q < lptr[lv + 1]; ++q) {
@@ -310,12 +328,29 @@ struct NestedDissection {
         std::vector<std::vector<int>> comps;
         std::vector<int> tags;
         components(rest, t, comps, tags);
-        for (size_t i = 0; i < comps.size(); ++i) {
-            std::vector<int> c = std::move(comps[i]);
-            component(c, tags[i]);
-            for (int v : c) tag[v] = 0;
+        if (parallel && depth < kParallelDepth && comps.size() > 1 &&
+            (int)comp.size() >= kParallelMinNodes) {
+            // async | deferred: without a free thread the task runs here at get()
+            std::vector<std::vector<int>> parts(comps.size());
+            std::vector<std::future<void>> running;
+            for (size_t i = 1; i < comps.size(); ++i)
+                running.push_back(std::async(std::launch::async | std::launch::deferred,
+                                             [this, &comps, &tags, &parts, i, depth] {
+                    sub(comps[i], tags[i], parts[i], depth + 1);
+                }));
+            sub(comps[0], tags[0], parts[0], depth + 1);
+            for (auto& f : running) f.get();
+            for (auto& part : parts) order.insert(order.end(), part.begin(), part.end());
+        } else {
+            for (size_t i = 0; i < comps.size(); ++i) sub(comps[i], tags[i], order, depth + 1);
         }
         for (int v : sep) order.push_back(v);
+    }
+
+    // one component of a split: order it, then mark its nodes numbered
+    void sub(std::vector<int>& c, int t, std::vector<int>& order, int depth) {
+        component(c, t, order, depth);
+        for (int v : c) tag[v] = 0;
     }
 
     void run() {
@@ -326,11 +361,7 @@ struct NestedDissection {
         std::vector<std::vector<int>> comps;
         std::vector<int> tags;
         components(all, t0, comps, tags);
-        for (size_t i = 0; i < comps.size(); ++i) {
-            std::vector<int> c = std::move(comps[i]);
-            component(c, tags[i]);
-            for (int v : c) tag[v] = 0;
-        }
+        for (size_t i = 0; i < comps.size(); ++i) sub(comps[i], tags[i], order, 0);
     }
 };
 
@@ -431,7 +462,7 @@ void supernode_rows(const Graph& g, const std::vector<int>& perm, const std::vec
 std::string analyse(const Graph& g, const SymbolicOptions& opt, Symbolic& out) {
     const int n = g.n;
     if (opt.leaf_size < 1) return "leaf_size must be >= 1";
-    NestedDissection nd(g, opt.leaf_size);
+    NestedDissection nd(g, opt.leaf_size, opt.parallel);
     nd.run();
     if ((int)nd.order.size() != n) return "internal error: ordering is not a permutation";
     std::vector<int> perm0 = nd.order, iperm0(n);

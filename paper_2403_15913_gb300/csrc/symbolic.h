@@ -14,6 +14,8 @@ struct SymbolicOptions {
     int relax_cols = 48;
     int relax_zeros = 1024;
     int max_width = 64;
+    bool parallel = true;   // fork the top of the nested-dissection recursion
+                            // onto threads (the result does not depend on it)
 };
 
 // Result of the analysis.  All column/row labels after `perm` are in the

@@ -167,3 +167,25 @@ def test_product_package_imports_no_oracle_or_fallback():
         if name.endswith(".py"):
             src = open(os.path.join(pkg, name)).read()
             assert not banned.search(src), name
+
+
+@pytest.mark.parametrize("k,T,opts", [(32, 500, OPTS[0]), (16, 1500, OPTS[3]), (32, 500, OPTS[2])])
+def test_symbolic_bit_exact_parallel_recursion(nat, k, T, opts):
+    """Columns large enough that the top of the nested-dissection recursion
+    runs sibling components on threads: the analysis equals the oracle's,
+    every time (repeated to expose any dependence on thread timing)."""
+    from paper_2403_15913_gb300 import KKTSolver
+    p = TrayParams(k=k, T=T)
+    pt = kkt_point(p, 0)
+    W = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = tray.jacobian_csr(p, pt.w)
+    o = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **opts)
+    rows = np.concatenate(o.sn_rows)
+    for _ in range(5):
+        s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], host_only=True, **opts)
+        g = s.symbolic()
+        assert np.array_equal(g["perm"], o.perm)
+        assert np.array_equal(g["parent"], o.parent)
+        assert np.array_equal(g["sn_ptr"], o.sn_ptr)
+        assert np.array_equal(g["sn_rows"], rows)
+        s.close()

@@ -189,3 +189,19 @@ def test_symbolic_bit_exact_parallel_recursion(nat, k, T, opts):
         assert np.array_equal(g["sn_ptr"], o.sn_ptr)
         assert np.array_equal(g["sn_rows"], rows)
         s.close()
+
+
+def test_device_analysis_without_a_gpu_returns_a_status(nat):
+    """Where no GPU can be used, the device analysis ends with a CUDA status
+    and its message (the binding raises KKTError): no crash, no fallback."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2403_15913_gb300 import KKTError, KKTSolver
+    p = TrayParams(k=3, T=2)
+    pt = kkt_point(p, 0)
+    W = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = tray.jacobian_csr(p, pt.w)
+    with pytest.raises(KKTError) as e:
+        KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1])
+    assert e.value.status == nat.KKT_ERR_CUDA

@@ -133,10 +133,12 @@ void kkt_default_options(kkt_options* opt);
  * IPM iterations).  n variables, m constraints.
  *   W_colptr[n+1], W_rowind[nnzW]: pattern of the LOWER triangle of the
  *       Hessian W, CSC, row indices >= column index (diagonal optional);
- *   J_rowptr[m+1], J_colind[nnzJ]: pattern of the Jacobian J (m x n), CSR.
+ *   J_rowptr[m+1], J_colind[nnzJ]: pattern of the Jacobian J (m x n), CSR;
+ *       no column index repeated within a row.
  * Value arrays passed to kkt_factor follow exactly these entry orders.
  * On success *out receives a new context (free with kkt_destroy).
- * Errors: KKT_ERR_ARG on out-of-range or upper-triangular indices,
+ * Errors: KKT_ERR_ARG on out-of-range or upper-triangular indices or a J row
+ * that repeats a column,
  * KKT_ERR_OOM / KKT_ERR_CUDA on device failures. */
 kkt_status kkt_analyse(int n, int m,
                        const int* W_colptr, const int* W_rowind,

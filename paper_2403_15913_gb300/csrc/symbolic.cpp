@@ -47,10 +47,18 @@ std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
             if (i < j || i >= n) return "W pattern entry outside the lower triangle";
         }
     if (J_rowptr[0] != 0) return "J_rowptr[0] must be 0";
+    // a row of J may not name a column twice: every pair of entries of a row
+    // becomes one product J_ra J_rb of J^T D J, which a repeated column would
+    // get wrong (and the counts below assume distinct columns)
+    std::vector<int> seen(n, -1);
     for (int r = 0; r < m; ++r) {
         if (J_rowptr[r + 1] < J_rowptr[r]) return "J_rowptr not monotone";
-        for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p)
-            if (J_colind[p] < 0 || J_colind[p] >= n) return "J column index out of range";
+        for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p) {
+            const int c = J_colind[p];
+            if (c < 0 || c >= n) return "J column index out of range";
+            if (seen[c] == r) return "a row of J repeats a column index";
+            seen[c] = r;
+        }
     }
     std::vector<int64_t> cnt(n + 1, 0);
     for (int j = 0; j < n; ++j)

@@ -115,6 +115,15 @@ def test_analyse_rejects_bad_patterns(nat):
         KKTSolver(3, 0, [0, 2, 3, 4], [0, 1, 0, 2], [0], [], host_only=True)
     with pytest.raises(KKTError):   # J column out of range
         KKTSolver(3, 1, [0, 1, 2, 3], [0, 1, 2], [0, 1], [7], host_only=True)
+    # a J row naming a column twice (its products J_ra J_rb would be wrong)
+    with pytest.raises(KKTError) as e:
+        KKTSolver(5, 1, np.arange(6), np.arange(5), [0, 3], [3, 3, 4], host_only=True)
+    assert e.value.status == nat.KKT_ERR_ARG and "repeats" in str(e.value)
+    from paper_2403_15913_gb300 import KKTBatchSolver
+    good = (np.arange(6), np.arange(5), np.array([0, 2]), np.array([3, 4]))
+    bad = (np.arange(6), np.arange(5), np.array([0, 3]), np.array([3, 3, 4]))
+    with pytest.raises(KKTError):
+        KKTBatchSolver([(5, 1) + good, (5, 1) + bad], host_only=True)
 
 
 # the hand-worked graphs of the oracle's symbolic pins (even-length path,

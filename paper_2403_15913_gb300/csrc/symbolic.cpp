@@ -30,8 +30,27 @@
 #include <future>
 #include <numeric>
 #include <set>
+#include <thread>
 
 namespace kktgb {
+
+namespace {
+// body(lo, hi) over [0, n): on threads in contiguous ranges when n is large
+// (every range independent), else in one call
+constexpr int kParallelGraphNodes = 100000;
+template <typename F>
+void for_ranges(int n, F&& body) {
+    const int hw = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < kParallelGraphNodes || hw < 2) { body(0, n); return; }
+    std::vector<std::future<void>> running;
+    for (int t = 1; t < hw; ++t) {
+        const int lo = (int)((long long)n * t / hw), hi = (int)((long long)n * (t + 1) / hw);
+        running.push_back(std::async(std::launch::async | std::launch::deferred, [&body, lo, hi] { body(lo, hi); }));
+    }
+    body(0, (int)((long long)n / hw));
+    for (auto& f : running) f.get();
+}
+}  // namespace
 
 std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
                         const int* J_rowptr, const int* J_colind, Graph& g) {
@@ -81,18 +100,27 @@ std::string build_graph(int n, int m, const int* W_colptr, const int* W_rowind,
         for (int p = J_rowptr[r]; p < J_rowptr[r + 1]; ++p)
             for (int q = J_rowptr[r]; q < J_rowptr[r + 1]; ++q)
                 if (J_colind[p] != J_colind[q]) tmp[fill[J_colind[p]]++] = J_colind[q];
+    // every node's list: sorted, duplicates and the node itself dropped (in
+    // place, independent per node), then compacted; large graphs split the
+    // nodes into ranges on threads, which changes nothing in the result
     g.n = n;
+    std::vector<int64_t> len(n);
+    auto dedup = [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i) {
+            auto b = tmp.begin() + ptr[i], e = tmp.begin() + ptr[i + 1];
+            std::sort(b, e);
+            auto u = std::remove(b, std::unique(b, e), i);
+            len[i] = u - b;
+        }
+    };
     g.xadj.assign(n + 1, 0);
-    g.adj.clear();
-    g.adj.reserve(tmp.size());
-    for (int i = 0; i < n; ++i) {
-        auto b = tmp.begin() + ptr[i], e = tmp.begin() + ptr[i + 1];
-        std::sort(b, e);
-        auto u = std::unique(b, e);
-        for (auto it = b; it != u; ++it)
-            if (*it != i) g.adj.push_back(*it);
-        g.xadj[i + 1] = (int64_t)g.adj.size();
-    }
+    for_ranges(n, dedup);
+    for (int i = 0; i < n; ++i) g.xadj[i + 1] = g.xadj[i] + len[i];
+    g.adj.resize(g.xadj[n]);
+    for_ranges(n, [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i)
+            std::copy(tmp.begin() + ptr[i], tmp.begin() + ptr[i] + len[i], g.adj.begin() + g.xadj[i]);
+    });
     return "";
 }
 

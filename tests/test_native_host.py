@@ -178,11 +178,14 @@ def test_product_package_imports_no_oracle_or_fallback():
             assert not banned.search(src), name
 
 
-@pytest.mark.parametrize("k,T,opts", [(32, 500, OPTS[0]), (16, 1500, OPTS[3]), (32, 500, OPTS[2])])
+@pytest.mark.parametrize("k,T,opts", [(32, 500, OPTS[0]), (16, 1500, OPTS[3]), (32, 500, OPTS[2]),
+                                    (32, 1600, OPTS[0])])
 def test_symbolic_bit_exact_parallel_recursion(nat, k, T, opts):
     """Columns large enough that the top of the nested-dissection recursion
-    runs sibling components on threads: the analysis equals the oracle's,
-    every time (repeated to expose any dependence on thread timing)."""
+    runs sibling components on threads (and, from 100,000 variables, the
+    graph's adjacency lists are built on threads): the analysis equals the
+    oracle's, every time (repeated to expose any dependence on thread
+    timing)."""
     from paper_2403_15913_gb300 import KKTSolver
     p = TrayParams(k=k, T=T)
     pt = kkt_point(p, 0)

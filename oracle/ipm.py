@@ -40,11 +40,15 @@ Parity: pinned by tests (closed-form box-constrained QP; the optimum of a tiny
 column instance against scipy's trust-constr; equal iteration counts and
 iterates for the exact dense solver and HyKKT; the barrier parameters drawn,
 in order, from the published Fiacco-McCormick sequence; accepted steps equal
-to the fraction-to-boundary step halved once per rejected trial).  The other
-rule details of the cited filter method (Armijo and filter acceptance,
-filter augmentation, the multiplier safeguard, the scaling of the optimality
-error, the dual step length) change iteration counts, not the optimum: they
-are pinned only through the optimum.
+to the fraction-to-boundary step halved once per rejected trial) and by
+worked single steps with a prescribed direction, whose outcomes were worked
+out by hand from the cited method's definitions: Armijo acceptance of f-type
+steps, filter and theta_max rejection, the switching condition and the
+theta_min test, filter augmentation by h-type steps only and its reset at
+each barrier decrease, the l1 constraint violation, the barrier-update
+threshold kappa_eps, the scaling s_d / s_c of the optimality error, tau =
+max(tau_min, 1 - mu), the dual step length from both bound multipliers, the
+primal step length for y, and the kappa_Sigma multiplier safeguard.
 """
 from __future__ import annotations
 

@@ -217,3 +217,37 @@ def test_device_analysis_without_a_gpu_returns_a_status(nat):
     with pytest.raises(KKTError) as e:
         KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1])
     assert e.value.status == nat.KKT_ERR_CUDA
+
+
+def _bench_column_parity(nat, T):
+    from paper_2403_15913_gb300 import KKTSolver
+    p = TrayParams(k=32, T=T)
+    pt = kkt_point(p, 0)
+    W = tray.hessian_lower_csc(p, pt.w, pt.lam)
+    J = tray.jacobian_csr(p, pt.w)
+    o = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **OPTS[0])
+    s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], host_only=True, **OPTS[0])
+    g = s.symbolic()
+    assert np.array_equal(g["perm"], o.perm)
+    assert np.array_equal(g["parent"], o.parent)
+    assert np.array_equal(g["colcount"], o.colcount)
+    assert np.array_equal(g["sn_ptr"], o.sn_ptr)
+    assert np.array_equal(g["sn_rows"], np.concatenate(o.sn_rows))
+    sz = s.sizes()
+    assert sz.nnz_L == o.nnz_L and sz.flops == o.flops
+    s.close()
+
+
+def test_symbolic_bit_exact_benchmark_column(nat):
+    """The benchmark's column (32 trays, T = 5000: n = 325,065) with the
+    library's default options: the threaded nested dissection and the
+    threaded adjacency build give the oracle's analysis bit for bit."""
+    _bench_column_parity(nat, 5000)
+
+
+@pytest.mark.slow
+def test_symbolic_bit_exact_largest_column(nat):
+    """The mixed-precision workload's column (32 trays, T = 20000: n =
+    1,300,065), bit for bit against the oracle (about two minutes of
+    oracle time)."""
+    _bench_column_parity(nat, 20000)

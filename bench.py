@@ -13,6 +13,18 @@ a pivot fails), the Lifted-KKT (or HyKKT) solve refined to a backward error
 filter line search.  When the IPM converges it is restarted (untimed).  The
 symbolic analysis is done once before timing (the paper's SYM column).
 
+The JSON line also carries, on one GPU, "sub": the other configurations of
+the metric measured in the same run at reduced step counts -- HyKKT at gamma
+1e4 and 1e7 on the same column, the largest factorisation (T = 20000, Sigma
+log-uniform on [1e-8, 1e8]) with the FP32 and the FP64 factor, the batch of
+256 uneven systems (FP64 and FP32 factor, against one instance at a time in
+FP64) and the NMPC serving stream (Poisson arrivals at 2000/s; solves/s,
+p50/p99 latency, against one slot in FP64).  "e2e" is measured through the
+host-buffer C ABI: whole cold solves of the same column submitted to a
+one-slot server (host state in, host solution out).  "cpu_baseline" is the
+oracle IPM on the same column (T = 5000, not scaled), one full iteration per
+single-threaded process, several processes side by side.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme lifted|hykkt]
         python bench.py --impl reference ...   (the CPU oracle, timed as it stands)
 
@@ -35,15 +47,68 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x DFMA/clk/SM x flops x GHz = 1258.6
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FFMA lanes/SM x flops x GHz = 80,548
 METRIC = "KKT solve time per IPM iteration"
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
-# DRAM bytes of one numeric factorisation (dram__bytes_read.sum +
-# dram__bytes_write.sum of its kernels in one ncu capture of this
-# benchmark), keyed by (trays, stages, solver, precision); other
-# configurations report null
-FACTOR_TRAFFIC = {(32, 5000, "supernodal", "fp64"): 484.5e6}
+# DRAM bytes of one numeric factorisation come from an ncu capture recorded
+# in this file together with the SHA-256 of the kernel sources it measured;
+# when the sources differ the counters are stale and roofline.traffic is null
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "factor_dram_traffic.txt")
+TRAFFIC_SOURCES = ("kernels.cuh", "kkt.cu", "fp64_lean.cuh", "sparse_dot.cuh")
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_15913_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def stored_factor_traffic(k, T, solver, precision):
+    """Bytes per factorisation from the recorded capture, or None."""
+    try:
+        rec = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                key, val = line.split(":", 1)
+                rec[key.strip()] = val.strip()
+        if rec.get("source_sha256") != kernel_source_digest():
+            return None
+        if rec.get("config") != f"k={k} T={T} solver={solver} precision={precision}":
+            return None
+        return float(rec["dram_bytes_per_factor"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def max_sm_clock_mhz(gpu):
+    """Maximum SM clock of the device (nvidia-smi), else the measured peaks file."""
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={gpu}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().splitlines()
+        return float(out[0]), "nvidia-smi clocks.max.sm"
+    except Exception:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except Exception:
+            return 2070.0, "nominal maximum SM clock"
+
+
+def alu_peak(local, fp32=False):
+    """FP64 DFMA (or FP32 FFMA) peak of the device in GFLOP/s: SM count from
+    the device properties, maximum SM clock, and the per-SM issue rate of
+    this chip (2 FP64 FMA lanes or 128 FP32 FMA lanes per clock)."""
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz, src = max_sm_clock_mhz(local)
+    lanes = 128 if fp32 else 2
+    peak = sms * lanes * 2 * mhz / 1e3
+    what = "FP32 FFMA" if fp32 else "FP64 DFMA"
+    return peak, (f"{what}: {sms} SMs (device query) x {lanes} FMA lanes/clk x 2 flop x {mhz:.0f} MHz "
+                  f"({src}); derived from unit counts and clock")
 DTYPE = {"fp64": "f64", "fp32": "f32 factor + f64 refinement", "df64": "df64 (float-pair) factor + f64 refinement"}
 UNIT = "ms/iter"
 
@@ -73,6 +138,8 @@ def parse():
                     help="batch workload: pick the supernode partition with kkt_autotune_batch first")
     ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the sub-records of the other configurations")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -148,67 +215,149 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- oracle
-def oracle_ipm_sample(k, T_sample, scheme, budget_s):
-    """Oracle IPM iterations at a bounded size until the budget is spent:
-    returns seconds per iteration (model, sparse factor, hybrid solve, line
-    search: the oracle as it stands, single thread)."""
+ORACLE_WORKER_BYTES = 2.5e9   # resident set of one oracle IPM at T = 5000 is ~1.8 GB
+
+
+def _host_memory_bytes():
+    """Memory this process may still use: MemAvailable, capped by a cgroup limit."""
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            raw = open(path).read().strip()
+            if raw.isdigit():
+                lim = int(raw)
+                used = 0
+                for upath in ("/sys/fs/cgroup/memory.current",
+                              "/sys/fs/cgroup/memory/memory.usage_in_bytes"):
+                    try:
+                        used = int(open(upath).read().strip())
+                        break
+                    except (OSError, ValueError):
+                        continue
+                free = lim - used
+                avail = free if avail is None else min(avail, free)
+        except OSError:
+            continue
+    return avail
+
+
+def oracle_workers(cap):
+    mem = _host_memory_bytes()
+    by_mem = cap if mem is None else int(mem // ORACLE_WORKER_BYTES)
+    return max(1, min(cap, os.cpu_count() or 1, by_mem))
+
+
+def _oracle_ipm_worker(k, T, scheme, n_warm, n_timed, barrier, out_q):
+    """One single-threaded oracle IPM on the full workload: set-up (model
+    pattern, symbolic analysis), n_warm untimed iterations, a barrier, then
+    n_timed timed iterations (a converged IPM restarts from the start)."""
     import numpy as np
     from gen.tray import TrayParams, ipm_start
     from oracle import ipm as oipm, symbolic, tray as otray
-    p = TrayParams(k=k, T=T_sample)
+    p = TrayParams(k=k, T=T)
     x0 = ipm_start(p)
     W = otray.hessian_lower_csc(p, x0, np.zeros(p.m))
     J = otray.jacobian_csr(p, x0)
     sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=64, relax_cols=32,
                            relax_zeros=128, max_width=64)
-    iters, t_total = 0, 0.0
-    while t_total < budget_s or iters == 0:
+
+    def fresh():
         lin = oipm.KKTLinearSolver(scheme, p.n, p.m, None, None, sym=sym, gamma=1e4)
-        s = oipm.IPM(oipm.TrayModel(p), lin, oipm.IPMOptions(relaxed=(scheme == "lifted")), x0)
-        while not s.done and s.it < 200 and t_total < budget_s * 2:
+        return oipm.IPM(oipm.TrayModel(p), lin, oipm.IPMOptions(relaxed=(scheme == "lifted")), x0)
+
+    s = fresh()
+
+    def one():
+        nonlocal s
+        while True:
             t0 = time.perf_counter()
             info = s.step()
             dt = time.perf_counter() - t0
-            if info.status != "converged":
-                iters += 1
-                t_total += dt
-        if s.it == 0:
-            break
-    return t_total / max(1, iters), iters
+            if info.status == "ok":
+                return dt
+            s = fresh()
+
+    for _ in range(n_warm):
+        one()
+    barrier.wait()
+    out_q.put([one() for _ in range(n_timed)])
 
 
-def cpu_baseline(args, budget_s=15.0, T_sample=50):
-    per, iters = oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s)
-    scale = (args.T + 1) / (T_sample + 1)
-    return {"value": per * scale * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{iters} oracle IPM iterations ({args.scheme}) at {args.k} trays, T={T_sample}: "
-                       f"{per*1e3:.1f} ms each, scaled x{scale:.1f} to T={args.T} (work linear in T)")}
+def oracle_ipm_parallel(k, T, scheme, n_warm, n_timed, workers):
+    """Oracle IPM iterations on the full workload, `workers` single-threaded
+    processes (spawned) side by side, iterations shared round-robin.  Returns
+    (wall seconds of the timed iterations, per-iteration seconds)."""
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers + 1)
+    q = ctx.Queue()
+    share = lambda tot, i: tot // workers + (1 if i < tot % workers else 0)
+    procs = [ctx.Process(target=_oracle_ipm_worker,
+                         args=(k, T, scheme, share(n_warm, i), share(n_timed, i), barrier, q))
+             for i in range(workers)]
+    for pr in procs:
+        pr.start()
+    barrier.wait()
+    t0 = time.perf_counter()
+    times = []
+    for _ in procs:
+        times += q.get()
+    wall = time.perf_counter() - t0
+    for pr in procs:
+        pr.join()
+    return wall, times
+
+
+def ipm_workload(args, n, m):
+    return (f"tray column k={args.k} T={args.T} (n={n}, m={m}), full IPM iteration ({args.scheme}) "
+            f"from xbar_0 = 0.3, tol 1e-8")
+
+
+def cpu_baseline(args):
+    """The oracle IPM as it stands on the benchmark's own column: one
+    iteration per worker process, the processes side by side."""
+    workers = oracle_workers(8)
+    wall, times = oracle_ipm_parallel(args.k, args.T, args.scheme, 0, workers, workers)
+    return {"value": wall * 1e3 / len(times), "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": (f"{len(times)} oracle IPM iterations ({args.scheme}) on the benchmark's column "
+                       f"(k={args.k}, T={args.T}, not scaled), {workers} single-threaded processes side by "
+                       f"side: {wall:.1f} s wall / {len(times)} iterations; one iteration takes "
+                       f"{statistics.mean(times):.1f} s on one core; set-up (model pattern, symbolic "
+                       f"analysis) untimed")}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the oracle IPM as it stands on the same column,
+    W untimed and K timed iterations, each a full single-threaded iteration,
+    run by up to 16 processes side by side (bounded by host memory) so that
+    the run ends within a few minutes; ms_per_step = timed wall / K."""
     if rank != 0:
-        return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    T_sample = 50
-    # warm-up iterations, then the timed ones (each step: one oracle IPM
-    # iteration at T=50, scaled to the workload's horizon)
-    oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s=0.5 * args.warmup)
-    per, iters = oracle_ipm_sample(args.k, T_sample, args.scheme, budget_s=max(2.0, 1.5 * args.steps))
-    scale = (args.T + 1) / (T_sample + 1)
-    ms = per * scale * 1e3
-    line = {
+        return None
+    workers = oracle_workers(16)
+    wall, times = oracle_ipm_parallel(args.k, args.T, args.scheme, args.warmup, args.steps, workers)
+    ms = wall * 1e3 / args.steps
+    n, m = (2 * args.k + 1) * (args.T + 1), 2 * args.k * (args.T + 1)
+    return {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"tray column k={args.k} T={args.T} (n={(2*args.k+1)*(args.T+1)}), "
-                               f"{args.scheme} IPM iteration; oracle at T={T_sample} scaled by "
-                               f"(T+1)/{T_sample+1}", "scheme": args.scheme},
-        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{iters} oracle IPM iterations at T={T_sample}, scaled x{scale:.1f}"},
+        "config": {"workload": ipm_workload(args, n, m), "scheme": args.scheme},
+        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": (f"{args.steps} timed oracle IPM iterations on the benchmark's column, "
+                                    f"{workers} single-threaded processes side by side ({wall:.1f} s wall); "
+                                    f"one iteration takes {statistics.mean(times):.1f} s on one core")},
         "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------- ours
@@ -296,29 +445,28 @@ def run_ours(args, ws, rank, local):
     ms = across_ranks(ms, "max", dist)
     ipm.set_profiling(False)
 
-    # ---- end to end through the public API: whole solves from a host x0
-    h_x0 = torch.as_tensor(ipm_start(p)).pin_memory()
-    d_x0 = torch.empty(p.n, dtype=torch.float64, device="cuda")
-    h_x = torch.empty(p.n, dtype=torch.float64).pin_memory()
-    h_y = torch.empty(p.m, dtype=torch.float64).pin_memory()
-    e2e_total, e2e_iters = 0.0, 0
-    for rep in range(2):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d_x0.copy_(h_x0, non_blocking=True)
-        ipm.init(d_x0)
-        hist = ipm.solve()
-        x, y, _, _, _ = ipm.get()
-        h_x.copy_(x, non_blocking=True)
-        h_y.copy_(y, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if rep >= 1:
-            e2e_total += e0.elapsed_time(e1)
-            e2e_iters += hist[-1]["iter"]
-    e2e_ms = e2e_total / max(1, e2e_iters)
+    # ---- end to end through the host-buffer C ABI: whole cold solves of the
+    # same column submitted to a one-slot server (kkt_server_submit with the
+    # host initial state x0[k], kkt_server_wait copying the solution x[n] to
+    # host memory); time per IPM iteration = wall time / iterations
+    e2e_ms, e2e_iters, e2e_solves = None, 0, 0
+    if args.precision == "fp64" and args.solver == "supernodal":
+        from paper_2403_15913_gb300 import NMPCServer
+        srv = NMPCServer(slots=1, hbm_budget_gb=200.0, scheme=args.scheme, gamma=args.gamma,
+                         warm_start=False)
+        cl = srv.add_client(p.as_array())
+        h_state = np.full(p.k, p.x0bar)
+        srv.wait(srv.submit(cl, h_state, keep_solution=True), want_solution=True)   # context set-up
+        t0 = time.perf_counter()
+        for _ in range(2):
+            r, _x = srv.wait(srv.submit(cl, h_state, keep_solution=True), want_solution=True)
+            if r["status"] != nat.KKT_CONVERGED:
+                raise RuntimeError(f"end-to-end solve ended with status {r['status']}")
+            e2e_iters += r["iters"]
+            e2e_solves += 1
+        e2e_wall = time.perf_counter() - t0
+        srv.close()
+        e2e_ms = e2e_wall * 1e3 / max(1, e2e_iters)
 
     if rank != 0:
         if dist:
@@ -328,23 +476,21 @@ def run_ours(args, ws, rank, local):
     factor_ms = st["factor_ms"] / fcalls
     kinv_ms = st["solve_ms"] / max(1, st["kinv_calls"])
     f32 = args.precision == "fp32"
+    peak, peak_src = alu_peak(local, f32)
     roof = {"kernel": ("block cyclic reduction (bcr_elim/bcr_update kernels)" if args.solver == "bcr" else
-                       "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)"),
+                       "supernodal Cholesky (factor kernels of one kkt_factor)"),
             "bound": "alu", "achieved": fl.value / (factor_ms * 1e-3) / 1e9,
-            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
+            "peak": peak, "unit": "GFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = FACTOR_TRAFFIC.get((args.k, args.T, args.solver, args.precision))
-    roof["peak_source"] = ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
-                           if f32 else
-                           "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")
+    roof["traffic"] = stored_factor_traffic(args.k, args.T, args.solver, args.precision)
+    roof["peak_source"] = peak_src
     n_steps = len(step_ms)
     line = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"tray column k={args.k} T={args.T} (n={p.n}, m={p.m}), full IPM "
-                               f"iteration ({args.scheme}) from xbar_0 = {p.x0bar}, tol 1e-8",
+        "config": {"workload": ipm_workload(args, p.n, p.m),
                    "scheme": args.scheme, "gamma": args.gamma if args.scheme == "hykkt" else None,
                    "precision": args.precision, "solver": args.solver,
                    "fp32_factors": st["fp32_factors"], "fp64_fallbacks": st["fp64_fallbacks"],
@@ -365,10 +511,13 @@ def run_ours(args, ws, rank, local):
                    "cg_iters": [i["cg_iters"] for i in infos][:6],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof,
-        "e2e": {"value": e2e_ms, "unit": UNIT,
-                "h2d_bytes_per_step": p.n * 8 / max(1, e2e_iters),
-                "d2h_bytes_per_step": (p.n + p.m) * 8 / max(1, e2e_iters),
-                "scope": "whole solves: x0 host->device, all iterations, (x, y) device->host"},
+        "e2e": ({"value": e2e_ms, "unit": UNIT,
+                 "h2d_bytes_per_step": p.k * 8 * e2e_solves / max(1, e2e_iters),
+                 "d2h_bytes_per_step": p.n * 8 * e2e_solves / max(1, e2e_iters),
+                 "scope": (f"{e2e_solves} whole cold solves ({e2e_iters} iterations) through the host-buffer "
+                           "C ABI: kkt_server_submit with the host state x0[k], kkt_server_wait copying "
+                           "x[n] to host memory; wall time / iterations")}
+                if e2e_ms is not None else None),
         "gpu_launches": (int(st["launches"] / n_steps * args.steps) + sum(i["launches"] for i in infos))
                         if n_steps else 0,
         "clocks": clk,
@@ -376,9 +525,9 @@ def run_ours(args, ws, rank, local):
     }
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
-    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return line
 
 
 # --------------------------------------------------------------- one KKT step
@@ -532,13 +681,13 @@ def run_kkt(args, ws, rank, local):
     fcalls = max(1, st["factor_calls"])
     factor_ms = st["factor_ms"] / fcalls
     f32 = prec == 1
+    peak, peak_src = alu_peak(local, f32)
     roof = {"kernel": ("block cyclic reduction (bcr_elim/bcr_update kernels)" if args.solver == "bcr" else
-                       "supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)"),
+                       "supernodal Cholesky (factor kernels of one kkt_factor)"),
             "bound": "alu", "achieved": sym.flops / (factor_ms * 1e-3) / 1e9,
-            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "traffic": None,
-            "peak_source": ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
-                            if f32 else
-                            "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")}
+            "peak": peak, "unit": "GFLOP/s",
+            "traffic": stored_factor_traffic(args.k, args.T, args.solver, args.precision),
+            "peak_source": peak_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     in_bytes = sum(v.numel() * 8 for v in h_in.values())
     line = {
@@ -575,9 +724,9 @@ def run_kkt(args, ws, rank, local):
                                 "sample": f"{n_s} oracle {args.scheme} KKT steps at {args.k} trays, T={T_s}: "
                                           f"{per*1e3:.1f} ms each, scaled x{scale:.1f} to T={args.T}"}
     solver.close()
-    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return line
 
 
 # --------------------------------------------------------------- batched KKT
@@ -682,9 +831,11 @@ def run_batch(args, ws, rank, local):
 
     # the plain per-instance FP64 path on the same inputs: one context per
     # instance, factor + solve one after the other
+    do_serial = not getattr(args, "no_serial", False)
     singles = []
     for i, (p, pt) in enumerate(zip(params, pats)):
-        singles.append(KKTSolver(p.n, p.m, *pt, precision=0, **opts))
+        if do_serial:
+            singles.append(KKTSolver(p.n, p.m, *pt, precision=0, **opts))
     sx = [dx[xo[i]:xo[i + 1]] for i in range(args.batch)]
     sy = [dy[yo[i]:yo[i + 1]] for i in range(args.batch)]
     views = [{k: d_in[k][a:b] for k, (a, b) in (("W", (wo[i], wo[i + 1])), ("J", (jo[i], jo[i + 1])),
@@ -700,7 +851,7 @@ def run_batch(args, ws, rank, local):
     serial()
     torch.cuda.synchronize()
     ser_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 3)) if do_serial else 0):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -708,7 +859,7 @@ def run_batch(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ser_ms.append(e0.elapsed_time(e1))
-    ser_eta = max(s1.info.bwd_err for s1 in singles)
+    ser_eta = max((s1.info.bwd_err for s1 in singles), default=None)
     for s1 in singles:
         s1.close()
     # end to end: values and right-hand sides host->device, batched factor +
@@ -736,12 +887,10 @@ def run_batch(args, ws, rank, local):
     sym = bs.sizes()
     factor_ms = st["factor_ms"] / max(1, st["factor_calls"])
     f32 = prec == 1
-    roof = {"kernel": "batched supernodal Cholesky (factor_subtree/level, potrf/trsm/syrk kernels)",
+    peak, peak_src = alu_peak(local, f32)
+    roof = {"kernel": "batched supernodal Cholesky (factor kernels of one kkt_factor_batch)",
             "bound": "alu", "achieved": sym.flops / (factor_ms * 1e-3) / 1e9,
-            "peak": FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "traffic": None,
-            "peak_source": ("FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, of nominal units)"
-                            if f32 else
-                            "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, of nominal units)")}
+            "peak": peak, "unit": "GFLOP/s", "traffic": None, "peak_source": peak_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     in_bytes = sum(v.numel() * 8 for v in h_in.values())
     line = {
@@ -761,9 +910,9 @@ def run_batch(args, ws, rank, local):
                    "max_bwd_err": max(etas), "max_refine_iters": int(res["refine_iters"].max()),
                    "fp64_fallbacks": st["fp64_fallbacks"],
                    "delta_x_nonzero": int((delta > 0).sum()),
-                   "per_instance_fp64_path": {"ms_per_batch": statistics.mean(ser_ms),
-                                              "solves_per_s": args.batch / (statistics.mean(ser_ms) * 1e-3),
-                                              "max_bwd_err": ser_eta},
+                   "per_instance_fp64_path": ({"ms_per_batch": statistics.mean(ser_ms),
+                                               "solves_per_s": args.batch / (statistics.mean(ser_ms) * 1e-3),
+                                               "max_bwd_err": ser_eta} if ser_ms else None),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof,
         "e2e": {"value": args.batch * ws / (statistics.mean(e2e) * 1e-3), "unit": "solves/s",
@@ -773,9 +922,9 @@ def run_batch(args, ws, rank, local):
         "clocks": clk,
     }
     bs.close()
-    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return line
 
 
 # --------------------------------------------------------------- NMPC serving
@@ -848,6 +997,7 @@ def run_serve(args, ws, rank, local):
     light.pop("clocks")
     light["rate_per_s"] = light_rate
     total = across_ranks(conc["solves_per_s"], "sum", dist)
+    line = None
     if rank == 0:
         clk = conc.pop("clocks")
         serial.pop("clocks")
@@ -874,24 +1024,109 @@ def run_serve(args, ws, rank, local):
             "gpu_launches": None,
             "clocks": clk,
         }
-        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def sub_records(args, local):
+    """The other configurations of the metric, measured in the same run at
+    reduced step counts (one GPU): HyKKT at gamma 1e4 and 1e7 on the same
+    column, the largest factorisation (T = 20000, Sigma on [1e-8, 1e8]) in
+    FP32 and FP64, the 256-instance batch (FP64 and FP32 factor, against one
+    instance at a time in FP64) and the NMPC serving stream."""
+    import copy
+    out = {}
+
+    def sub(**kw):
+        a = copy.copy(args)
+        a.no_cpu_baseline, a.gpus = True, 1
+        a.steps, a.warmup = kw.pop("steps", 5), kw.pop("warmup", 3)
+        for key, val in kw.items():
+            setattr(a, key, val)
+        return a
+
+    def safe(name, fn):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:   # a failed sub-record is reported, the main line stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+
+    def hykkt(g):
+        ln = run_ours(sub(scheme="hykkt", gamma=g), 1, 0, local)
+        c = ln["config"]
+        return {"ms_per_iter": ln["value"], "e2e_ms_per_iter": ln["e2e"]["value"],
+                "factor_ms": c["phase_ms"]["factor"], "kinv_ms": c["phase_ms"]["kinv"],
+                "kinv_per_iter": c["phase_ms"]["kinv_per_step"], "cg_iters": c["cg_iters"],
+                "max_bwd_err": c["max_bwd_err"], "steps": ln["steps"], "clocks": ln["clocks"]}
+
+    def largest():
+        ln = run_kkt(sub(workload="kkt", T=20000, sigma="1e-8,1e8", precision="fp32",
+                         scheme="lifted"), 1, 0, local)
+        c, f64 = ln["config"], ln["config"]["fp64_factor_path"]
+        peak64, _ = alu_peak(local, False)
+        return {"workload": c["workload"], "factor_gflop": c["factor_gflop"],
+                "fp64": {"factor_ms": f64["factor_ms"], "step_ms": f64["ms"],
+                         "frac_of_fp64_peak": c["factor_gflop"] / (f64["factor_ms"] * 1e-3) / peak64,
+                         "max_bwd_err": f64["bwd_err"]},
+                "fp32_factor": {"factor_ms": c["factor_ms"], "step_ms": ln["value"],
+                                "frac_of_fp32_peak": ln["roofline"]["frac"],
+                                "max_bwd_err": c["max_bwd_err"], "refine_iters": c["refine_iters"],
+                                "fp64_fallbacks": c["fp64_fallbacks"],
+                                "rel_diff_vs_fp64_path": f64["rel_diff_vs_fp64_path"]},
+                "steps": ln["steps"], "clocks": ln["clocks"]}
+
+    def batch(prec, **kw):
+        ln = run_batch(sub(workload="batch", precision=prec, scheme="lifted", **kw), 1, 0, local)
+        c = ln["config"]
+        return {"solves_per_s": ln["value"], "ms_per_batch": ln["ms_per_step"],
+                "e2e_solves_per_s": ln["e2e"]["value"], "factor_ms": c["factor_ms"],
+                "factor_frac_of_peak": ln["roofline"]["frac"], "max_bwd_err": c["max_bwd_err"],
+                "per_instance_fp64": c["per_instance_fp64_path"], "steps": ln["steps"],
+                "clocks": ln["clocks"]}
+
+    def serve():
+        ln = run_serve(sub(workload="serve", scheme="lifted", precision="fp64"), 1, 0, local)
+        c = ln["config"]
+        return {"workload": c["workload"], "solves_per_s": ln["value"],
+                "p50_ms": c["concurrent"]["p50_ms"], "p99_ms": c["concurrent"]["p99_ms"],
+                "serial_fp64_one_slot": {k: c["serial_fp64_one_slot"][k]
+                                         for k in ("solves_per_s", "p50_ms", "p99_ms")},
+                "at_70pct_of_capacity": {k: c["at_70pct_of_capacity"][k]
+                                         for k in ("rate_per_s", "solves_per_s", "p50_ms", "p99_ms")},
+                "iters_mean": c["concurrent"]["iters_mean"], "clocks": ln["clocks"]}
+
+    safe("hykkt_gamma_1e4", lambda: hykkt(1e4))
+    safe("hykkt_gamma_1e7", lambda: hykkt(1e7))
+    safe("largest_factor", largest)
+    safe("batch_fp64", lambda: batch("fp64"))
+    safe("batch_fp32", lambda: batch("fp32", no_serial=True))
+    safe("serve", serve)
+    return out
 
 
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
-        run_reference(args, ws, rank)
+        line = run_reference(args, ws, rank)
     elif args.workload == "kkt":
-        run_kkt(args, ws, rank, local)
+        line = run_kkt(args, ws, rank, local)
     elif args.workload == "batch":
-        run_batch(args, ws, rank, local)
+        line = run_batch(args, ws, rank, local)
     elif args.workload == "serve":
-        run_serve(args, ws, rank, local)
+        line = run_serve(args, ws, rank, local)
     else:
-        run_ours(args, ws, rank, local)
+        line = run_ours(args, ws, rank, local)
+        if line is not None and ws == 1 and not args.no_sub:
+            cb = line.pop("cpu_baseline", None)
+            line["sub"] = sub_records(args, local)
+            if cb is not None:
+                line["cpu_baseline"] = cb
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -279,11 +279,14 @@ kkt_status kkt_backsolve(kkt_ctx* ctx, const double* d_b, double* d_x,
  * fixed device array inside the library of KKT_STATIC_SCRATCH_DOUBLES
  * doubles (16 MiB), which every GPU that loads the library holds until the
  * process exits.  Sizes n > KKT_STATIC_SCRATCH_DOUBLES return KKT_ERR_ARG.
- * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All
- * calls share the one array: calls that overlap on the GPU (other streams,
- * other threads, other contexts of this library) race and give wrong
- * results, so serialise them.  No profiling events are recorded. */
+ * The array is placed on the device, and its device address looked up once
+ * per device, by kkt_analyse (with that device current), so this call itself
+ * takes no device memory.  All calls share the one array: calls that overlap
+ * on the GPU (other streams, other contexts of this library) race and give
+ * wrong results.  Each call returns only after its stream has finished, so
+ * calls from one host thread never overlap; calls from different host
+ * threads must be serialised by the caller (e.g. one mutex around them).
+ * No profiling events are recorded. */
 #define KKT_STATIC_SCRATCH_DOUBLES (1 << 21)
 kkt_status kkt_backsolve_noalloc(kkt_ctx* ctx, const double* d_b, double* d_x,
                                  cudaStream_t stream);

@@ -21,6 +21,17 @@
 
 using namespace kktgb;
 
+// ---------------------------------------------------------------------------
+// Allocation-free backsolve.  The permuted work vector lives in a file-scope
+// device array; host code must not use the symbol's name as a pointer (it is
+// a host-side stand-in), so its device address is looked up once per device,
+// with that device current, when a context is set up on it (kkt_analyse):
+// that lookup is also what places the array on the device, so the
+// allocation-free call itself takes no device memory and touches no module
+// loading.
+static __device__ __align__(256) double g_noalloc_scratch[KKT_STATIC_SCRATCH_DOUBLES];
+
+
 namespace {
 
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
@@ -105,6 +116,11 @@ struct kkt_ctx {
     const double* f_C = nullptr;   // dual block of the target system (device) or NULL
     DevBuf<double> d_Cbuf;
     bool device_ready = false;   // false for host-only analyses
+    // device address of the allocation-free backsolve's static scratch,
+    // looked up when the context is set up (null with noalloc_err set if
+    // the lookup failed)
+    double* noalloc_ptr = nullptr;
+    std::string noalloc_err;
     // CUDA graphs captured once after the analysis: the triangular solves on
     // w_xp, and one HyKKT CG iteration on the internal CG vectors
     cudaGraph_t tri_graph = nullptr, cg_graph = nullptr, tri_graph32 = nullptr, cg_graph32 = nullptr;
@@ -1253,6 +1269,29 @@ kkt_status new_ctx(const kkt_options* opt, kkt_ctx** out) {
     return KKT_OK;
 }
 
+// Allocation-free backsolve: device address of its static scratch (below).
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Address of the static scratch on the current device (cached per device).
+cudaError_t noalloc_lookup(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        if (!p) return cudaErrorInvalidSymbol;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
 SymbolicOptions symbolic_options(const kkt_options& o) {
     SymbolicOptions so;
     so.leaf_size = o.leaf_size;
@@ -1322,6 +1361,13 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             set_err(nullptr, st, c->err);
             kkt_destroy(c);
             return st;
+        }
+        // a failed lookup only disables kkt_backsolve_noalloc
+        const cudaError_t e = noalloc_lookup(&c->noalloc_ptr);
+        if (e != cudaSuccess) {
+            c->noalloc_ptr = nullptr;
+            c->noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            cudaGetLastError();
         }
     }
     c->device_ready = device;
@@ -1913,34 +1959,6 @@ kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_
     return KKT_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Allocation-free backsolve.  The permuted work vector lives in a file-scope
-// device array; host code must not use the symbol's name as a pointer (it is
-// a host-side stand-in), so its device address is looked up once per device.
-static __device__ __align__(256) double g_noalloc_scratch[KKT_STATIC_SCRATCH_DOUBLES];
-
-namespace {
-constexpr int kMaxDevices = 64;
-double* g_noalloc_ptr[kMaxDevices] = {};
-std::mutex g_noalloc_mu;
-
-kkt_status noalloc_scratch(kkt_ctx* c, double** out) {
-    int dev = -1;
-    CUDA_TRY(c, cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_err(c, KKT_ERR_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return set_err(c, KKT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
-    return KKT_OK;
-}
-}  // namespace
-
 kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_t st) {
     if (!c || !d_b || !d_x) return set_err(c, KKT_ERR_ARG, "NULL argument");
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve_noalloc called without a factor");
@@ -1948,8 +1966,8 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
         return set_err(c, KKT_ERR_ARG, "n = " + std::to_string(c->n) +
                                            " exceeds the static scratch of kkt_backsolve_noalloc (" +
                                            std::to_string(KKT_STATIC_SCRATCH_DOUBLES) + " doubles)");
-    double* xp = nullptr;
-    TRY(noalloc_scratch(c, &xp));
+    double* xp = c->noalloc_ptr;
+    if (!xp) return set_err(c, KKT_ERR_CUDA, c->noalloc_err.empty() ? "no device scratch" : c->noalloc_err);
     const int n = c->n;
     if (c->opt.solver == 1) {
         CUDA_TRY(c, cudaMemcpyAsync(xp, d_b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -90,3 +90,29 @@ def test_backsolve_noalloc_df64_factor():
     assert np.all(np.isfinite(o))
     assert np.max(np.abs(o - r)) <= 1e-12 * np.max(np.abs(r))
 
+
+def test_backsolve_noalloc_block_cyclic_reduction():
+    """Block cyclic reduction (solver = 1): the static scratch holds the
+    right-hand side in natural order while it is solved in place; two calls
+    in a row give the ordinary backsolve's result."""
+    torch = torch_cuda()
+    ensure_built()
+    from paper_2403_15913_gb300 import _native as nat
+    p, pt, W, J = instance(32, 50, 0, sigma_range=(1e-2, 1e2))
+    s = solver_for(p, W, J, scheme="lifted", solver=1, block=2 * p.k + 1)
+    assert s.factor(to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma),
+                    to_dev(torch, np.full(p.m, 1e2)), 10.0) == 0
+    L = nat.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(13)
+    for call in range(2):
+        b = to_dev(torch, rng.standard_normal(p.n))
+        ref = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        out = torch.full((p.n,), np.nan, dtype=torch.float64, device="cuda")
+        s.backsolve(b, ref)
+        st = L.kkt_backsolve_noalloc(s._ctx, ctypes.c_void_p(b.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), stream)
+        assert st == 0, L.kkt_last_error(s._ctx)
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert np.array_equal(o, r), call

@@ -153,7 +153,9 @@ kkt_status kkt_analyse_host(int n, int m,
                             const int* J_rowptr, const int* J_colind,
                             const kkt_options* opt, kkt_ctx** out);
 
-/* Sizes of the symbolic result: supernodes, nonzeros of L, stored panel
+/* Sizes of the symbolic result of kkt_analyse (the one-time symbolic
+ * factorisation that the paper keeps across refactorisations, Sec. V-B;
+ * its SYM column of Table I): supernodes, nonzeros of L, stored panel
  * entries (nnz(L) plus explicit zeros of relaxed supernodes), total row
  * indices over supernodes, levels of the supernodal elimination tree, and
  * the factorisation flop count sum_j cc_j^2 of the exact structure.  With
@@ -164,7 +166,8 @@ kkt_status kkt_symbolic_sizes(const kkt_ctx* ctx, int* ns, int64_t* nnz_L,
                               int64_t* panel_entries, int64_t* row_entries,
                               int* levels, double* flops);
 
-/* Copy out the symbolic analysis (host arrays, caller-allocated):
+/* Copy out the symbolic analysis of Sec. V-B (fill-reducing ordering,
+ * elimination tree, column counts, supernodes), host arrays, caller-allocated:
  * perm[n] (new -> old), parent[n] (etree of P K P^T, -1 for roots),
  * colcount[n], sn_ptr[ns+1], sn_rowptr[ns+1], sn_rows[row_entries]
  * (supernode row structures in permuted labels).  Any pointer may be NULL. */
@@ -546,8 +549,10 @@ enum {
     KKT_FN_MAX_ABS = 4,  /* max(x0, |x1|) for x0 >= 0, a NaN x1 ignored      */
     KKT_FN_MAX_NN = 5,   /* max(x0, x1) of non-negative values                */
     KKT_FN_MIN_NN = 6,   /* min(x0, x1) of non-negative values                */
-    KKT_FN_F32_ROUNDTRIP = 7  /* double(float(x)) by the bit layout (x in
+    KKT_FN_F32_ROUNDTRIP = 7, /* double(float(x)) by the bit layout (x in
                                  (1e-30, 1e30); truncates the mantissa)       */
+    KKT_FN_RCP_FAST = 8   /* 1/x (x > 0): float-pair seed on the FP32 and
+                             integer units + one Newton step (two FP64 FMAs) */
 };
 kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream);
 

@@ -45,7 +45,7 @@ EXPORTED = [
 
 # helper functions of kkt_eval_fn
 KKT_FN_RSQRT, KKT_FN_RCP, KKT_FN_SPLIT_M, KKT_FN_SPLIT_E = 0, 1, 2, 3
-KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN, KKT_FN_F32_ROUNDTRIP = 4, 5, 6, 7
+KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN, KKT_FN_F32_ROUNDTRIP, KKT_FN_RCP_FAST = 4, 5, 6, 7, 8
 KKT_FN_BINARY = (KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN)
 
 

@@ -1204,3 +1204,7 @@ cg_check_kernel(int nb, double* __restrict__ cgs, int* __restrict__ cgi, int max
 }
 
 }  // namespace kktgb
+
+// defined before df64.cuh, like the kernels above, so that fma and the
+// shuffles of T = double / float resolve to the CUDA built-ins
+#include "fused_factor.cuh"

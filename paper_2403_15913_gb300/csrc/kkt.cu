@@ -12,6 +12,7 @@
 #include <stdexcept>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "bcr_kernels.cuh"
@@ -80,6 +81,11 @@ struct kkt_ctx {
     int* d_task_sn = nullptr;
     int n_norm = 0;               // supernodes normalised after the factorisation
     int* d_norm_list = nullptr;
+    // levels factorised by factor_fused_kernel (FP64 and FP32 panels), and
+    // the normalisation list that leaves their supernodes out
+    std::vector<char> lvl_fused;
+    int n_norm_fused = 0;
+    int* d_norm_list_fused = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
     // device allocations (all freed in kkt_destroy) and their total size
     std::vector<void*> allocs;
@@ -573,11 +579,13 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     std::vector<int2> trsm_tasks;
     std::vector<int4> syrk_tasks;
     c->lvl_split.assign(nlev, 0);
+    c->lvl_fused.assign(nlev, 0);
     c->lvl_trsm_ptr.assign(nlev + 1, 0);
     c->lvl_syrk_ptr.assign(nlev + 1, 0);
     for (int l = 0; l < nlev; ++l) {
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         c->lvl_split[l] = cnt < kSplitLevel;
+        c->lvl_fused[l] = c->lvl_split[l] && c->lvl_max_c[l] <= kFusedMaxC && c->lvl_max_rb[l] <= kFusedMaxRb;
         if (c->lvl_split[l]) {
             // SYRK tasks: chunks of the packed lower triangle of each
             // supernode, sized so the level gives about four CTAs per SM
@@ -605,14 +613,17 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     // normalised (split narrow levels, panels too large for shared memory):
     // the normalisation pass after the factorisation covers only these
     {
-        std::vector<int> norm_list;
+        std::vector<int> norm_list, norm_list_fused;
         for (int s = 0; s < ns; ++s) {
             if (in_task[s]) continue;
             const bool fused_smem = !c->lvl_split[level[s]] && (long long)sn_r[s] * sn_c[s] <= kSmemCapElems;
             if (!fused_smem) norm_list.push_back(s);
+            if (!fused_smem && !c->lvl_fused[level[s]]) norm_list_fused.push_back(s);
         }
         c->n_norm = (int)norm_list.size();
+        c->n_norm_fused = (int)norm_list_fused.size();
         TRY(upload(c, &c->d_norm_list, norm_list));
+        TRY(upload(c, &c->d_norm_list_fused, norm_list_fused));
     }
 
     // ---- SpMV structures (original labels)
@@ -1156,6 +1167,46 @@ kkt_status enqueue_bcr_factor(kkt_ctx* c, double delta_x, cudaStream_t st) {
     return KKT_OK;
 }
 
+// panel types the fused narrow-level kernels are instantiated for
+template <typename T>
+constexpr bool kFusedType = std::is_same<T, double>::value || std::is_same<T, float>::value;
+
+// One split level of supernodes with <= 32 columns and <= 128 rows below:
+// one CTA per supernode when the level fills the SMs, otherwise a cluster of
+// K = 2, 4 or 8 CTAs per supernode sharing its rows and Schur pairs.
+template <typename T>
+kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx, FailSink fs, T* dinv,
+                              cudaStream_t st) {
+    const size_t mc = (size_t)c->lvl_max_c[l], mrb = (size_t)c->lvl_max_rb[l];
+    int K = 1;
+    while (K < kFusedClusterMax && (long long)cnt * K * 2 <= kNumSMs) K *= 2;
+    if (K == 1) {
+        const size_t fsm = ((size_t)c->lvl_max_rc[l] + mrb * mc) * sizeof(T);
+        if (cnt <= kNumSMs)
+            factor_fused_kernel<T, true><<<cnt, kFusedThreads, fsm, st>>>(c->plan, lsn, 1, Lx, fs, dinv);
+        else
+            factor_fused_kernel<T, false><<<cnt, kFusedThreads, fsm, st>>>(c->plan, lsn, 1, Lx, fs, dinv);
+        CUDA_TRY(c, cudaGetLastError());
+        return KKT_OK;
+    }
+    const size_t own = (mc + (mrb + K - 1) / K) * mc;
+    const size_t fsm = (own + (size_t)c->lvl_max_rc[l] + mrb * mc) * sizeof(T);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(cnt * K), 1, 1);
+    cfg.blockDim = dim3(kFusedThreads, 1, 1);
+    cfg.dynamicSmemBytes = fsm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_TRY(c, cudaLaunchKernelEx(&cfg, factor_fused_cluster_kernel<T>, c->plan, lsn, Lx, fs, dinv));
+    return KKT_OK;
+}
+
 template <typename T>
 kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
     const int sp_a = span_begin(c, 0, st);
@@ -1190,6 +1241,12 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
                 c->plan, lsn, Lx, fs, need, dinv);
             continue;
         }
+        if constexpr (kFusedType<T>) {
+            if (c->lvl_fused[l]) {
+                TRY(launch_fused_level<T>(c, l, cnt, lsn, Lx, fs, dinv, st));
+                continue;
+            }
+        }
         const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
         // the small top levels: one cluster launch instead of three launches
         const size_t csm = std::max(dsm, (size_t)c->lvl_max_rb[l] * c->lvl_max_c[l] * sizeof(T));
@@ -1211,9 +1268,10 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
         }
         c->stats.launches += 2;
     }
-    if (c->n_norm > 0) {
-        normalize_panels_kernel<T><<<std::min(c->n_norm, 152 * 16), kThreads, 0, st>>>(
-            c->plan, c->d_norm_list, c->n_norm, Lx, dinv);
+    const int n_norm = kFusedType<T> ? c->n_norm_fused : c->n_norm;
+    if (n_norm > 0) {
+        normalize_panels_kernel<T><<<std::min(n_norm, 152 * 16), kThreads, 0, st>>>(
+            c->plan, kFusedType<T> ? c->d_norm_list_fused : c->d_norm_list, n_norm, Lx, dinv);
         c->stats.launches += 1;
     }
     span_end(c, sp_f, st);
@@ -1350,6 +1408,16 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                              kClusterSmemBytes);
         cudaFuncSetAttribute(narrow_level_cluster_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kClusterSmemBytes);
+        {
+            const int fb = (int)(((kFusedMaxC + kFusedMaxRb) * kFusedMaxC + kFusedMaxRb * kFusedMaxC) * sizeof(double));
+            const int fcb = fb + (int)((kFusedMaxC + kFusedMaxRb / 2) * kFusedMaxC * sizeof(double));
+            cudaFuncSetAttribute(factor_fused_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
+            cudaFuncSetAttribute(factor_fused_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
+            cudaFuncSetAttribute(factor_fused_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb / 2);
+            cudaFuncSetAttribute(factor_fused_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb / 2);
+            cudaFuncSetAttribute(factor_fused_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb);
+            cudaFuncSetAttribute(factor_fused_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb / 2);
+        }
         cudaFuncSetAttribute(syrk_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
@@ -2094,6 +2162,7 @@ __global__ void eval_fn_kernel(int fn, int n, const double* __restrict__ x, doub
         switch (fn) {
             case KKT_FN_RSQRT: r = kktgb::rsqrt_householder(a); break;
             case KKT_FN_RCP: r = kktgb::rcp_pos(a); break;
+            case KKT_FN_RCP_FAST: r = kktgb::rcp_pos_fast(a); break;
             case KKT_FN_SPLIT_M:
             case KKT_FN_SPLIT_E: {
                 double m;
@@ -2114,7 +2183,7 @@ __global__ void eval_fn_kernel(int fn, int n, const double* __restrict__ x, doub
 }  // namespace
 
 extern "C" kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream) {
-    if (fn < KKT_FN_RSQRT || fn > KKT_FN_F32_ROUNDTRIP || n < 0 || (n > 0 && (!x || !y))) return KKT_ERR_ARG;
+    if (fn < KKT_FN_RSQRT || fn > KKT_FN_RCP_FAST || n < 0 || (n > 0 && (!x || !y))) return KKT_ERR_ARG;
     if (n == 0) return KKT_OK;
     eval_fn_kernel<<<std::min((n + 255) / 256, 152 * 8), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
     return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_ERR_CUDA;

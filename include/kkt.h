@@ -294,6 +294,17 @@ kkt_status kkt_backsolve(kkt_ctx* ctx, const double* d_b, double* d_x,
 kkt_status kkt_backsolve_noalloc(kkt_ctx* ctx, const double* d_b, double* d_x,
                                  cudaStream_t stream);
 
+/* Test hook of bounds-check builds (the library compiled with
+ * -DKKT_BOUNDS_CHECK=1, in which every index read from a precomputed map is
+ * tested on the device before it is used, and a failed test makes
+ * kkt_factor / kkt_solve / kkt_backsolve return KKT_ERR_INTERNAL without any
+ * out-of-bounds access; not a step of the paper's method).  what = 1
+ * overwrites one entry of the Schur-update relative-row map with a row one
+ * past its target supernode's rows -- a wrong index that still lies inside
+ * the factor storage -- so that a test can exercise the checks; what = 0
+ * restores it.  KKT_ERR_STATE in other builds. */
+kkt_status kkt_debug_corrupt_map(kkt_ctx* ctx, int what);
+
 /* Diagnostic: copy the numeric factor L (permuted order) as CSC with the
  * panel structure: colptr[n+1], rowind[], val[] sized by the panel entries
  * below and on the diagonal (lower trapezoid of each supernode panel). */
@@ -549,10 +560,8 @@ enum {
     KKT_FN_MAX_ABS = 4,  /* max(x0, |x1|) for x0 >= 0, a NaN x1 ignored      */
     KKT_FN_MAX_NN = 5,   /* max(x0, x1) of non-negative values                */
     KKT_FN_MIN_NN = 6,   /* min(x0, x1) of non-negative values                */
-    KKT_FN_F32_ROUNDTRIP = 7, /* double(float(x)) by the bit layout (x in
+    KKT_FN_F32_ROUNDTRIP = 7  /* double(float(x)) by the bit layout (x in
                                  (1e-30, 1e30); truncates the mantissa)       */
-    KKT_FN_RCP_FAST = 8   /* 1/x (x > 0): float-pair seed on the FP32 and
-                             integer units + one Newton step (two FP64 FMAs) */
 };
 kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream);
 

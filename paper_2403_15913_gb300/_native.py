@@ -40,12 +40,12 @@ EXPORTED = [
     "kkt_ipm_device_bytes", "kkt_device_bytes",
     "kkt_server_default_options", "kkt_server_create", "kkt_server_add_client", "kkt_server_submit",
     "kkt_server_wait", "kkt_server_drain", "kkt_server_get_stats", "kkt_server_destroy",
-    "kkt_eval_fn",
+    "kkt_eval_fn", "kkt_debug_corrupt_map",
 ]
 
 # helper functions of kkt_eval_fn
 KKT_FN_RSQRT, KKT_FN_RCP, KKT_FN_SPLIT_M, KKT_FN_SPLIT_E = 0, 1, 2, 3
-KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN, KKT_FN_F32_ROUNDTRIP, KKT_FN_RCP_FAST = 4, 5, 6, 7, 8
+KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN, KKT_FN_F32_ROUNDTRIP = 4, 5, 6, 7
 KKT_FN_BINARY = (KKT_FN_MAX_ABS, KKT_FN_MAX_NN, KKT_FN_MIN_NN)
 
 
@@ -145,7 +145,14 @@ def lib():
         raise RuntimeError(
             f"CUDA library {LIB_PATH} is missing; build it with "
             "`python -c 'import __graft_entry__ as g; g.build()'`")
-    L = ctypes.CDLL(LIB_PATH)
+    _lib = load(LIB_PATH)
+    return _lib
+
+
+def load(path):
+    """Open a build of the library at `path` and declare its C ABI (the
+    bounds-check build is a second library with the same symbols)."""
+    L = ctypes.CDLL(path)
     L.kkt_default_options.argtypes = [ctypes.POINTER(Options)]
     L.kkt_default_options.restype = None
     for name in ("kkt_analyse", "kkt_analyse_host"):
@@ -244,7 +251,8 @@ def lib():
     L.kkt_server_get_stats.restype = ctypes.c_int
     L.kkt_server_destroy.argtypes = [P]
     L.kkt_server_destroy.restype = None
-    _lib = L
+    L.kkt_debug_corrupt_map.argtypes = [P, ctypes.c_int]
+    L.kkt_debug_corrupt_map.restype = ctypes.c_int
     return L
 
 

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libkkt_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
+# the bounds-check build (-DKKT_BOUNDS_CHECK=1): same C ABI, every map index
+# tested on the device; used by the tests, never by the product path
+LIB_PATH_CHECKED = os.path.join(HERE, "libkkt_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kkt.cu", "tray.cu", "ipm.cu", "serve.cu", "symbolic.cpp"]
 
@@ -29,9 +32,11 @@ def _nvcc():
 
 
 def build(verbose: bool = False, debug_checks: bool = False) -> str:
-    """Compile every source and link the shared library; returns its path."""
+    """Compile every source and link the shared library; returns its path
+    (debug_checks: the bounds-check build, a separate library)."""
     nvcc = _nvcc()
-    obj_dir = os.path.join(HERE, "_build")
+    obj_dir = os.path.join(HERE, "_build_checked" if debug_checks else "_build")
+    lib_path = LIB_PATH_CHECKED if debug_checks else LIB_PATH
     os.makedirs(obj_dir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-Xcompiler", "-fPIC,-O2",
               "-lineinfo"] + ARCH
@@ -56,13 +61,13 @@ def build(verbose: bool = False, debug_checks: bool = False) -> str:
             errors.append(f"{src}:\n{out.decode(errors='replace')}")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + ["-lpthread", "-o", tmp]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -14,8 +14,6 @@
 //    step for the reciprocal: with e = 1 - d y0, 1/d = y0 / (1 - e) =
 //    y0 (1 + e + e^2 + O(e^3)), truncation below 2^-66 -- three FP64 FMAs.
 //    Outside the range, the IEEE division.
-//  * rcp_pos_fast: 1/d with a float-pair seed built on the FP32 and integer
-//    units and one FP64 Newton step (two FP64 FMAs), for latency-bound chains.
 //  * max / min / |x| / sign tests of doubles on the integer units: the bit
 //    patterns of non-negative doubles order like their values (+inf above
 //    every finite value, NaN patterns above +inf), so for operands known to
@@ -49,52 +47,6 @@ __device__ __forceinline__ double rcp_pos(double d) {
     const double y0 = f64_of(__frcp_rn(f32_of(d)));
     const double e = fma(-d, y0, 1.0);
     return fma(fma(e, e, e), y0, y0);
-}
-
-// 1/d for d > 0 with two FP64 operations on its dependency chain (for the
-// pivot chain of the factorisation, where every FP64 operation costs its
-// full latency).  d = M 2^E with M in [1, 2); M = Mh + Ml with Mh its top 24
-// bits (an FP32 number) and Ml the low 29 bits (converted to FP32, exact to
-// 2^-47 of M).  In FP32: y0 = rcp.approx(Mh) (error ~2^-23); the residual
-// e = 1 - M y0 = fma(-Mh, y0, 1) - Ml y0 (the FMA rounds once, so e is
-// accurate to ~2^-46); 1/M = y0 (1 + e + e^2 + O(e^3)), kept as the float
-// pair y0 + y0 (e + e^2).  The pair is added into one double on the integer
-// units (mantissas aligned and summed as 64-bit integers, bits below the
-// double's last place truncated) and the exponent reduced by E: a seed Y
-// within ~2^-45 of 1/d.  One Newton step in FP64, r = Y + Y (1 - d Y), then
-// leaves a truncation of ~2^-90: two FMAs.  Outside the range, the IEEE
-// division.
-__device__ __forceinline__ double rcp_pos_fast(double d) {
-    if (!lean_range(d)) return 1.0 / d;
-    const long long b = __double_as_longlong(d);
-    const int E = (int)(b >> 52) - 1023;
-    const long long mb = b & 0x000fffffffffffffLL;
-    const float mh = __int_as_float((127 << 23) | (int)(mb >> 29));
-    const float ml = __int2float_rn((int)(mb & 0x1fffffffLL)) * 0x1p-52f;
-    float y0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(mh));
-    const float e = __fmaf_rn(-ml, y0, __fmaf_rn(-mh, y0, 1.0f));
-    const float ylo = y0 * __fmaf_rn(e, e, e);
-    // y0 + ylo as a double: 24-bit mantissa of y0 at bit 29, ylo aligned to it
-    const int hb = __float_as_int(y0);
-    int ex = (hb >> 23) & 0xff;
-    long long Y = (long long)((hb & 0x7fffff) | 0x800000) << 29;
-    const int lb = __float_as_int(ylo);
-    if ((lb & 0x7fffffff) != 0) {
-        const int sh = ((lb >> 23) & 0xff) - ex + 29;
-        const long long ml64 = (long long)((lb & 0x7fffff) | 0x800000);
-        const long long add = sh >= 0 ? (ml64 << sh) : (sh > -40 ? (ml64 >> -sh) : 0LL);
-        Y = lb < 0 ? Y - add : Y + add;
-    }
-    if (Y < (1LL << 52)) {
-        Y <<= 1;
-        --ex;
-    } else if (Y >= (1LL << 53)) {
-        Y >>= 1;
-        ++ex;
-    }
-    const double yd = __longlong_as_double(((long long)(ex - 127 + 1023 - E) << 52) | (Y & 0x000fffffffffffffLL));
-    return fma(yd, fma(-d, yd, 1.0), yd);
 }
 
 constexpr long long kBitsPosInf = 0x7ff0000000000000LL;

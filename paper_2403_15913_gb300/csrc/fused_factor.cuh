@@ -15,10 +15,9 @@
 //            U[i][l] -= U[i][j] Lhat[l][j]    for j < l <= i (the update
 //            of L L^T by column j: L[i][j] L[l][j] = U[i][j] U[l][j] r_j).
 // Warp 0 carries only the chain from r_j to r_{j+1}: the update of column
-// j+1 of the diagonal block, the new pivot d_{j+1} and its reciprocal (a
-// float-pair seed on the FP32 and integer units and one Newton step, two
-// FP64 FMAs): three dependent FP64 operations per column, where a Cholesky
-// pivot also needs a square root and the scaling of the column.  The other
+// j+1 of the diagonal block, the new pivot d_{j+1} and its reciprocal (an
+// FP32 seed and one third-order step), where a Cholesky pivot also needs a
+// square root and the scaling of the column.  The other
 // warps apply column j to the columns beyond j + 1 (lower triangle of the
 // diagonal block, through a table of its pairs ordered by column descending,
 // so the active pairs are a prefix) and to the rows below the diagonal
@@ -44,7 +43,7 @@ constexpr int kFusedClusterMax = 8;   // CTAs per supernode (portable cluster si
 template <typename T>
 __device__ __forceinline__ T chain_rcp(T d);
 template <>
-__device__ __forceinline__ double chain_rcp<double>(double d) { return rcp_pos_fast(d); }
+__device__ __forceinline__ double chain_rcp<double>(double d) { return rcp_pos(d); }
 template <>
 __device__ __forceinline__ float chain_rcp<float>(float d) { return 1.0f / d; }
 
@@ -80,9 +79,10 @@ __device__ __forceinline__ void syrk_pairs_ldl(const Plan& P, int s, int c, cons
         if (k < c) s0 = fma(ai[k * lda], bj[k * ldb], s0);
         long long base;
         const int* rm;
-        int a;
-        update_target(P, s, c, jj, base, rm, a);
-        atomicAdd(Lx + base + rm[ii - a], -(s0 + s1));
+        int a, rt;
+        if (!update_target(P, s, c, jj, base, rm, a, rt)) continue;
+        const int q = rm[ii - a];
+        if (kkt_in(P.berr, q >= 0 && q < rt, kBcRelRow)) atomicAdd(Lx + base + q, -(s0 + s1));
     }
 }
 
@@ -101,8 +101,8 @@ __device__ __forceinline__ void fused_panel(T* U, int ru, int c, int nr, int f, 
     const int wid = wrank * 32 + lane, nw = nworkers * 32;
     // warp 0's registers: cur = column j of the diagonal block (lane = row),
     // rj = 1/d_j, and, prepared a step ahead, b = U[j+1][j], sq = b^2 and
-    // pc = cur * b, so that r_{j+1} depends on r_j through three FP64 FMAs:
-    // d_{j+1} = U[j+1][j+1] - sq r_j and the two of the reciprocal
+    // pc = cur * b, so that r_{j+1} depends on r_j through four FP64 FMAs:
+    // d_{j+1} = U[j+1][j+1] - sq r_j and the three of the reciprocal
     T cur = T(0.0), rj = T(0.0), sq = T(0.0), pc = T(0.0);
     if (warp == 0) {
         cur = lane < c ? U[lane] : T(0.0);
@@ -192,6 +192,7 @@ factor_fused_kernel(Plan P, const int* __restrict__ lvl_sn, int split, T* __rest
     __shared__ T lh[2][kFusedMaxC];        // Lhat[.][j] of the diagonal block
     __shared__ short2 tab[kFusedMaxC * (kFusedMaxC - 1) / 2];
     const int s = lvl_sn[blockIdx.x / split];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int rank = (int)(blockIdx.x % split);
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     T* U = reinterpret_cast<T*>(smem_raw);   // r x c, ld = r
@@ -245,6 +246,9 @@ factor_fused_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
     const int K = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int s = lvl_sn[blockIdx.x / K];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) {   // the whole cluster returns together
+        return;
+    }
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     const int i0 = (int)((long long)rb * rank / K), i1 = (int)((long long)rb * (rank + 1) / K);
     const int nr = i1 - i0;
@@ -273,17 +277,19 @@ factor_fused_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
         if (row >= c || rank == 0) g[(row < c ? row : row + i0) + col * r] = Uo[e] * rr[col];
     }
     cluster.sync();
-    // gather every CTA's unnormalised rows below from its shared memory
-    for (int e = tid; e < rb * c; e += kFusedThreads) {
-        const int col = e / rb, i = e - col * rb;
-        int k = (int)(((long long)i * K) / rb);
-        while (k > 0 && i < (int)((long long)rb * k / K)) --k;
-        while (k + 1 < K && i >= (int)((long long)rb * (k + 1) / K)) ++k;
-        const int ki0 = (int)((long long)rb * k / K), kro = c + (int)((long long)rb * (k + 1) / K) - ki0;
+    // gather every CTA's unnormalised rows below from its shared memory, one
+    // peer at a time (its rows i0k .. i0k + nk - 1, ld c + nk there)
+    for (int k = 0; k < K; ++k) {
+        const int i0k = (int)((long long)rb * k / K), nk = (int)((long long)rb * (k + 1) / K) - i0k;
+        if (nk == 0) continue;
         const T* remote = cluster.map_shared_rank(Uo, k);
-        const T v = remote[c + (i - ki0) + col * kro];
-        Uf[c + i + col * r] = v;
-        L21[i + col * rb] = v * rr[col];
+        const int rk = c + nk;
+        for (int e = tid; e < nk * c; e += kFusedThreads) {
+            const int col = e / nk, i = e - col * nk;
+            const T v = remote[c + i + col * rk];
+            Uf[c + i0k + i + col * r] = v;
+            L21[i0k + i + col * rb] = v * rr[col];
+        }
     }
     cluster.sync();
     if (rb > 0) {

@@ -18,6 +18,37 @@ namespace kktgb {
 
 constexpr int kThreads = 256;
 
+// Bounds-check builds (compiled with -DKKT_BOUNDS_CHECK=1): every index read
+// from a precomputed map -- assembly slots, supernodes of level and task
+// lists, update segments, the target column and relative row of every Schur
+// update, the row indices of the solves -- is tested against the extent it
+// must lie in before it is used; a failed test records the first error code
+// in a device word (read back by kkt_factor / kkt_solve as KKT_ERR_INTERNAL)
+// and the access is skipped.  No trap, no assert.  In ordinary builds
+// kkt_in() is the constant true and the tests compile away.
+#ifndef KKT_BOUNDS_CHECK
+#define KKT_BOUNDS_CHECK 0
+#endif
+enum {
+    kBcSlot = 1,       // assembly slot outside the panel storage
+    kBcSupernode = 2,  // level / task list entry outside 0 .. ns-1
+    kBcSegment = 3,    // update segment target not an ancestor index
+    kBcColumn = 4,     // Schur update column outside the target supernode
+    kBcRelRow = 5,     // relative row outside the target supernode's rows
+    kBcSolveRow = 6    // solve row index outside 0 .. n-1
+};
+__device__ __forceinline__ bool kkt_in(int* berr, bool ok, int code) {
+#if KKT_BOUNDS_CHECK
+    if (!ok && berr) atomicCAS(berr, 0, code);
+    return ok;
+#else
+    (void)berr;
+    (void)ok;
+    (void)code;
+    return true;
+#endif
+}
+
 // Kernels that run inside the graph of one CG iteration take `active`: when
 // it points to 0 (CG has converged) they return at once, so iterations
 // enqueued after convergence do nothing.  NULL means always active.
@@ -44,6 +75,9 @@ struct Plan {
     const long long* seg_map; // offset in relmap of positions of below rows a..rb-1
     const int* relmap;        // positions of rows in the target's rows(t)
     const unsigned long long* rmask;   // structural mask of every panel row
+    int* berr;                // bounds-check error word (bounds-check builds)
+    int ns, n;                // supernodes, columns
+    long long panel;          // panel entries
 };
 
 // ------------------------------------------------------------- assembly
@@ -71,7 +105,7 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
                                 const int2* __restrict__ src, const double* __restrict__ W,
                                 const double* __restrict__ Js, const double* __restrict__ sigma,
                                 double delta_x, const double* __restrict__ dvec,
-                                T* __restrict__ Lx) {
+                                T* __restrict__ Lx, long long nslot, int* berr) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
          e += (long long)gridDim.x * blockDim.x) {
         // the first source initialises the sum (no FP64 add of a zero; the
@@ -104,7 +138,8 @@ __global__ void assemble_kernel(long long nk, const long long* __restrict__ slot
             else v += sigma[s.x] + (dvec ? dvec[s.x] : delta_x);
             if (++q < q1) s = src[q];
         }
-        Lx[slot[e]] = (T)v;
+        const long long sl = slot[e];
+        if (kkt_in(berr, sl >= 0 && sl < nslot, kBcSlot)) Lx[sl] = (T)v;
     }
 }
 
@@ -226,16 +261,23 @@ __device__ __forceinline__ void panel_factor(T* A, int f, int c, int r, int nrow
 }
 
 // Segment lookup for update column jj (below-row index) of supernode s.
-__device__ __forceinline__ void update_target(const Plan& P, int s, int c, int jj, long long& base,
-                                              const int*& rm, int& a) {
+// With bounds checks it also returns false (and records the error) when the
+// target or the column it names lies outside the tree; rt = rows of the
+// target, for the caller's check of the relative row.
+__device__ __forceinline__ bool update_target(const Plan& P, int s, int c, int jj, long long& base,
+                                              const int*& rm, int& a, int& rt) {
     const int sp0 = P.seg_ptr[s], sp1 = P.seg_ptr[s + 1];
     int k = sp0;
     while (k < sp1 - 1 && jj >= P.seg_b[k]) ++k;
     const int t = P.seg_t[k];
+    if (!kkt_in(P.berr, sp1 > sp0 && t > s && t < P.ns, kBcSegment)) return false;
     a = P.seg_a[k];
     const int row = P.rows[P.sn_rptr[s] + c + jj];
-    base = P.sn_lptr[t] + (long long)(row - P.sn_f[t]) * P.sn_r[t];
+    rt = P.sn_r[t];
+    if (!kkt_in(P.berr, row >= P.sn_f[t] && row < P.sn_f[t] + P.sn_c[t], kBcColumn)) return false;
+    base = P.sn_lptr[t] + (long long)(row - P.sn_f[t]) * rt;
     rm = P.relmap + P.seg_map[k];
+    return true;
 }
 
 // SYRK of the rows below the diagonal block, L21 L21^T, over the packed
@@ -259,9 +301,10 @@ __device__ __forceinline__ void syrk_pairs(const Plan& P, int s, int c, const T*
         for (int k = 0; k < c; ++k) sum = fma(ai[(long long)k * ld], aj[(long long)k * ld], sum);
         long long base;
         const int* rm;
-        int a;
-        update_target(P, s, c, jj, base, rm, a);
-        atomicAdd(Lx + base + rm[ii - a], -sum);
+        int a, rt;
+        if (!update_target(P, s, c, jj, base, rm, a, rt)) continue;
+        const int q = rm[ii - a];
+        if (kkt_in(P.berr, q >= 0 && q < rt, kBcRelRow)) atomicAdd(Lx + base + q, -sum);
     }
 }
 
@@ -281,6 +324,7 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const long long lp = P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -397,6 +441,7 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
@@ -472,6 +517,7 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
     __shared__ T D[64 * 64];
     const int2 task = tasks[blockIdx.x];
     const int s = task.x;
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x)   // L11(row, col) dinv(col), row > col,
@@ -499,7 +545,9 @@ syrk_stage_kernel(Plan P, const int4* __restrict__ tasks, T* __restrict__ Lx, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     const int4 t = tasks[blockIdx.x];
-    const int s = t.x, c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
+    const int s = t.x;
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    const int c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     const T* g = Lx + P.sn_lptr[s];
     if (stage) {
         for (int e = threadIdx.x; e < rb * c; e += blockDim.x) {
@@ -533,6 +581,7 @@ narrow_level_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int rank = (int)cluster.block_rank();
     const int s = lvl_sn[blockIdx.x / kClusterCtas];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;   // the whole cluster returns together
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     T* g = Lx + P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
@@ -583,6 +632,7 @@ normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __re
                         const T* __restrict__ dinv) {
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const int s = list[q];
+        if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         T* A = Lx + P.sn_lptr[s];
         for (int e = threadIdx.x; e < r * c; e += blockDim.x) A[e] *= dinv[f + e / r];
@@ -598,7 +648,7 @@ normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __re
 template <typename T>
 __device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, int r,
                                               const T* __restrict__ u, const int* __restrict__ rows,
-                                              T* __restrict__ x, T (*part)[32]) {
+                                              T* __restrict__ x, T (*part)[32], int* berr, int n) {
     const int tid = threadIdx.x, nw = blockDim.x >> 5, warp = tid >> 5, lane = tid & 31;
     const int rb = r - c;
     for (int i0 = 0; i0 < rb; i0 += 32 * nw) {
@@ -629,7 +679,8 @@ __device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, in
             const int b = tid >> 5;
             T t = part[b][lane];
             for (int qq = 1; qq < wpr; ++qq) t += part[b + qq * nrb][lane];
-            atomicAdd(x + rows[c + i0 + tid], -t);
+            const int rw = rows[c + i0 + tid];
+            if (kkt_in(berr, rw >= 0 && rw < n, kBcSolveRow)) atomicAdd(x + rw, -t);
         }
         __syncthreads();
     }
@@ -651,6 +702,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
     __shared__ T z[64];
     __shared__ T part[kThreads / 32][32];
     const int s = lvl_sn[blockIdx.x];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const T* A = Lx + P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -665,7 +717,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
         if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
     }
     __syncthreads();
-    scatter_below(A, c, r, z, P.rows + P.sn_rptr[s], x, part);
+    scatter_below(A, c, r, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
 }
 
 // Backward substitution L^T w = z, one CTA per supernode of a level
@@ -684,6 +736,7 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
     T* D = kDynD ? reinterpret_cast<T*>(smem_raw) : Dst;   // c x c (dsz = the level's widest c squared)
     T* xb = reinterpret_cast<T*>(smem_raw) + (kDynD ? dsz : 0);   // x of the rows below, when staged
     const int s = lvl_sn[blockIdx.x];
+    if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const T* A = Lx + P.sn_lptr[s];
     const int* rows = P.rows + P.sn_rptr[s];
@@ -692,20 +745,28 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
     const int rb = r - c;
     for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
     if (kStageXb)
-        for (int i = tid; i < rb; i += nt) xb[i] = x[rows[c + i]];
+        for (int i = tid; i < rb; i += nt) {
+            const int rw = rows[c + i];
+            xb[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? x[rw] : T(0.0);
+        }
     __syncthreads();
     // warp w sums rows i = w, w + nw, ... for columns k = lane, lane + 32
     {
         T s0 = 0.0, s1 = 0.0;
         if (c > 32) {
             for (int i = warp; i < rb; i += nw) {
-                const T xv = kStageXb ? xb[i] : x[rows[c + i]];
+                const int rw = rows[c + i];
+                const T xv = kStageXb ? xb[i] : (kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? x[rw] : T(0.0));
                 s0 = fma(A[c + i + (long long)lane * r], xv, s0);
                 if (lane + 32 < c) s1 = fma(A[c + i + (long long)(lane + 32) * r], xv, s1);
             }
         } else if (lane < c) {
             for (int i = warp; i < rb; i += nw)
-                s0 = fma(A[c + i + (long long)lane * r], kStageXb ? xb[i] : x[rows[c + i]], s0);
+                s0 = fma(A[c + i + (long long)lane * r],
+                         kStageXb ? xb[i]
+                                  : (kkt_in(P.berr, rows[c + i] >= 0 && rows[c + i] < P.n, kBcSolveRow) ? x[rows[c + i]]
+                                                                                                 : T(0.0)),
+                         s0);
         }
         part[warp][lane] = s0;
         part[warp][lane + 32] = s1;
@@ -746,6 +807,7 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
+        if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         T* g = Lx + P.sn_lptr[s];
         for (int e = tid; e < r * c; e += nt) sm[e] = __ldcg(g + e);
@@ -773,6 +835,7 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
+        if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         const T* A = Lx + P.sn_lptr[s];
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
@@ -790,7 +853,8 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
         for (int i = tid; i < r - c; i += nt) {
             T sum = 0.0;
             for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
-            atomicAdd(x + rows[c + i], -sum);
+            const int rw = rows[c + i];
+            if (kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow)) atomicAdd(x + rw, -sum);
         }
         __threadfence();
         __syncthreads();
@@ -812,6 +876,7 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     for (int q = task_ptr[blockIdx.x + 1] - 1; q >= task_ptr[blockIdx.x]; --q) {
         const int s = task_sn[q];
+        if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         const T* A = Lx + P.sn_lptr[s];
         const int* rows = P.rows + P.sn_rptr[s];
@@ -819,7 +884,10 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
         T* D = dyn;
         T* xb = dyn + c * c;
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
-        for (int i = tid; i < rb; i += nt) xb[i] = __ldcg(x + rows[c + i]);
+        for (int i = tid; i < rb; i += nt) {
+            const int rw = rows[c + i];
+            xb[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? __ldcg(x + rw) : T(0.0);
+        }
         __syncthreads();
         if (c <= 32) {
             // narrow supernode: a warp instruction covers 32 / cp rows (lane =

@@ -127,6 +127,11 @@ struct kkt_ctx {
     // the lookup failed)
     double* noalloc_ptr = nullptr;
     std::string noalloc_err;
+    // bounds-check error word (device) and the test hook's map entry
+    int* d_berr = nullptr;
+    long long dbg_relmap_pos = -1;
+    int dbg_relmap_bad = 0, dbg_relmap_old = 0;
+    bool dbg_corrupted = false;
     // CUDA graphs captured once after the analysis: the triangular solves on
     // w_xp, and one HyKKT CG iteration on the internal CG vectors
     cudaGraph_t tri_graph = nullptr, cg_graph = nullptr, tri_graph32 = nullptr, cg_graph32 = nullptr;
@@ -489,6 +494,10 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             seg_b.push_back(e);
             seg_map.push_back((long long)relmap.size());
             fill_pos(t);
+            if (c->dbg_relmap_pos < 0 && rb > 0) {
+                c->dbg_relmap_pos = (long long)relmap.size();
+                c->dbg_relmap_bad = sn_r[t];
+            }
             for (int q = i; q < rb; ++q) {
                 int pq = pos[rows[cc + q]];
                 if (pq < 0) {
@@ -771,8 +780,11 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         std::vector<unsigned long long> rm(S.sn_rowmask.begin(), S.sn_rowmask.end());
         TRY(upload(c, &d_rmask, rm));
     }
+    TRY(alloc(c, &c->d_berr, 1));
+    CUDA_TRY(c, cudaMemset(c->d_berr, 0, sizeof(int)));
     c->plan = Plan{d_sn_f, d_sn_c, d_sn_r, d_sn_lptr, d_sn_rptr, d_rows,
-                   d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap, d_rmask};
+                   d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap, d_rmask,
+                   c->d_berr, ns, n, c->panel};
     TRY(upload(c, &c->d_lvl_sn, c->h_lvl_sn));
     TRY(upload(c, &c->d_trsm_tasks, trsm_tasks));
     TRY(upload(c, &c->d_task_ptr, task_ptr));
@@ -1142,7 +1154,7 @@ kkt_status enqueue_bcr_factor(kkt_ctx* c, double delta_x, cudaStream_t st) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_bcr, 0, (size_t)2 * N * bb * sizeof(double), st));
     assemble_kernel<double><<<grid_for(c->bcr_nk), kThreads, 0, st>>>(
         c->bcr_nk, c->d_bcr_slot, c->d_bcr_sptr, c->d_bcr_src, c->f_W, c->v_Js, c->f_sigma, delta_x,
-        c->f_dvec, c->d_bcr);
+        c->f_dvec, c->d_bcr, (long long)2 * N * bb, c->d_berr);
     span_end(c, sp_a, st);
     CUDA_TRY(c, cudaMemsetAsync(c->d_fail, 0x7f, sizeof(int), st));
     const FailSink fs{c->d_fail, nullptr};
@@ -1167,6 +1179,11 @@ kkt_status enqueue_bcr_factor(kkt_ctx* c, double delta_x, cudaStream_t st) {
     return KKT_OK;
 }
 
+// Shared memory requested by the fused launches that must run one CTA per
+// SM (more than half of an SM's 228 KB): two CTAs on one SM would put both
+// pivot chains on sub-partition 0 and its single FP64 unit.
+constexpr size_t kOneCtaPerSmBytes = 120 * 1024;
+
 // panel types the fused narrow-level kernels are instantiated for
 template <typename T>
 constexpr bool kFusedType = std::is_same<T, double>::value || std::is_same<T, float>::value;
@@ -1182,8 +1199,9 @@ kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx,
     while (K < kFusedClusterMax && (long long)cnt * K * 2 <= kNumSMs) K *= 2;
     if (K == 1) {
         const size_t fsm = ((size_t)c->lvl_max_rc[l] + mrb * mc) * sizeof(T);
-        if (cnt <= kNumSMs)
-            factor_fused_kernel<T, true><<<cnt, kFusedThreads, fsm, st>>>(c->plan, lsn, 1, Lx, fs, dinv);
+        if (cnt <= kNumSMs)   // one CTA per SM: the chain keeps its sub-partition's FP64 unit to itself
+            factor_fused_kernel<T, true><<<cnt, kFusedThreads, std::max(fsm, kOneCtaPerSmBytes), st>>>(
+                c->plan, lsn, 1, Lx, fs, dinv);
         else
             factor_fused_kernel<T, false><<<cnt, kFusedThreads, fsm, st>>>(c->plan, lsn, 1, Lx, fs, dinv);
         CUDA_TRY(c, cudaGetLastError());
@@ -1194,7 +1212,7 @@ kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx,
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(cnt * K), 1, 1);
     cfg.blockDim = dim3(kFusedThreads, 1, 1);
-    cfg.dynamicSmemBytes = fsm;
+    cfg.dynamicSmemBytes = std::max(fsm, kOneCtaPerSmBytes);   // one CTA of the cluster per SM
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1213,7 +1231,7 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
     CUDA_TRY(c, cudaMemsetAsync(Lx, 0, (size_t)c->panel * sizeof(T), st));
     assemble_kernel<T><<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
                                                              c->f_W, c->v_Js, c->f_sigma, delta_x,
-                                                             c->f_dvec, Lx);
+                                                             c->f_dvec, Lx, c->panel, c->d_berr);
     span_end(c, sp_a, st);
     CUDA_TRY(c, cudaMemsetAsync(c->d_fail, 0x7f, (size_t)c->nb * sizeof(int), st));
     const FailSink fs{c->d_fail, c->nb > 1 ? c->d_col_inst : nullptr};
@@ -1409,14 +1427,16 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         cudaFuncSetAttribute(narrow_level_cluster_kernel<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kClusterSmemBytes);
         {
-            const int fb = (int)(((kFusedMaxC + kFusedMaxRb) * kFusedMaxC + kFusedMaxRb * kFusedMaxC) * sizeof(double));
-            const int fcb = fb + (int)((kFusedMaxC + kFusedMaxRb / 2) * kFusedMaxC * sizeof(double));
+            const int fb = std::max((int)kOneCtaPerSmBytes,
+                                    (int)(((kFusedMaxC + kFusedMaxRb) * kFusedMaxC + kFusedMaxRb * kFusedMaxC) * sizeof(double)));
+            const int fcb = std::max((int)kOneCtaPerSmBytes,
+                                     fb + (int)((kFusedMaxC + kFusedMaxRb / 2) * kFusedMaxC * sizeof(double)));
             cudaFuncSetAttribute(factor_fused_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
             cudaFuncSetAttribute(factor_fused_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
-            cudaFuncSetAttribute(factor_fused_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb / 2);
-            cudaFuncSetAttribute(factor_fused_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb / 2);
+            cudaFuncSetAttribute(factor_fused_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
+            cudaFuncSetAttribute(factor_fused_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
             cudaFuncSetAttribute(factor_fused_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb);
-            cudaFuncSetAttribute(factor_fused_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb / 2);
+            cudaFuncSetAttribute(factor_fused_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb);
         }
         cudaFuncSetAttribute(syrk_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
@@ -1874,20 +1894,62 @@ static kkt_status factor_impl(kkt_ctx* c, const double* d_Wval, const double* d_
     return KKT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Bounds-check builds: after a factor or solve call, the device error word;
+// a recorded failure becomes KKT_ERR_INTERNAL (the word is cleared for the
+// next call).  Ordinary builds return the call's own status.
+kkt_status bounds_verdict(kkt_ctx* c, cudaStream_t st, kkt_status s0) {
+#if KKT_BOUNDS_CHECK
+    if (!c || !c->d_berr) return s0;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->d_berr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return set_err(c, KKT_ERR_CUDA, "bounds check: the error word could not be read");
+    if (h == 0) return s0;
+    cudaMemsetAsync(c->d_berr, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    static const char* what[] = {"", "assembly slot outside the panel storage",
+                                 "level or task entry outside the supernodes",
+                                 "update segment target is not an ancestor",
+                                 "Schur update column outside its target supernode",
+                                 "relative row outside its target supernode",
+                                 "solve row index outside 0..n-1"};
+    return set_err(c, KKT_ERR_INTERNAL,
+                   std::string("device bounds check failed: ") + (h >= 1 && h <= 6 ? what[h] : "unknown code"));
+#else
+    (void)c;
+    (void)st;
+    return s0;
+#endif
+}
+}  // namespace
+
+extern "C" {
+
 kkt_status kkt_factor(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
                       const double* d_D, double delta_x, cudaStream_t st, kkt_info* info) {
-    return factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, nullptr, st, info);
+    return bounds_verdict(c, st, factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, nullptr, st, info));
 }
 
 kkt_status kkt_factor_batch(kkt_ctx* c, const double* d_Wval, const double* d_Jval,
                             const double* d_sigma, const double* d_D, const double* delta_x,
                             cudaStream_t st, kkt_info* info) {
     if (!delta_x) return set_err(c, KKT_ERR_ARG, "delta_x is NULL");
-    return factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, 0.0, delta_x, st, info);
+    return bounds_verdict(c, st, factor_impl(c, d_Wval, d_Jval, d_sigma, d_D, 0.0, delta_x, st, info));
 }
+
+static kkt_status solve_impl(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
+                             double* d_ds, cudaStream_t st, kkt_info* info);
 
 kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
                      double* d_ds, cudaStream_t st, kkt_info* info) {
+    return bounds_verdict(c, st, solve_impl(c, d_rx, d_ry, d_dx, d_dy, d_ds, st, info));
+}
+
+static kkt_status solve_impl(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
+                             double* d_ds, cudaStream_t st, kkt_info* info) {
     if (!c) return KKT_ERR_ARG;
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_solve called without a successful kkt_factor");
     if (!d_rx || !d_ry || !d_dx || !d_dy) return set_err(c, KKT_ERR_ARG, "NULL vector");
@@ -2023,6 +2085,7 @@ kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve called without a factor");
     TRY(apply_kinv(c, d_b, d_x, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
+    TRY(bounds_verdict(c, st, KKT_OK));
     spans_collect(c);
     return KKT_OK;
 }
@@ -2059,6 +2122,28 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
     return KKT_OK;
+}
+
+kkt_status kkt_debug_corrupt_map(kkt_ctx* c, int what) {
+#if KKT_BOUNDS_CHECK
+    if (!c || !c->device_ready || c->opt.solver != 0) return set_err(c, KKT_ERR_STATE, "no supernodal device context");
+    if (c->dbg_relmap_pos < 0) return set_err(c, KKT_ERR_STATE, "no Schur update in this tree");
+    int* p = const_cast<int*>(c->plan.relmap) + c->dbg_relmap_pos;
+    if (what == 1 && !c->dbg_corrupted) {
+        CUDA_TRY(c, cudaMemcpy(&c->dbg_relmap_old, p, sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(p, &c->dbg_relmap_bad, sizeof(int), cudaMemcpyHostToDevice));
+        c->dbg_corrupted = true;
+    } else if (what == 0 && c->dbg_corrupted) {
+        CUDA_TRY(c, cudaMemcpy(p, &c->dbg_relmap_old, sizeof(int), cudaMemcpyHostToDevice));
+        c->dbg_corrupted = false;
+    } else if (what != 0 && what != 1) {
+        return set_err(c, KKT_ERR_ARG, "what must be 0 (restore) or 1 (corrupt)");
+    }
+    return KKT_OK;
+#else
+    (void)what;
+    return set_err(c, KKT_ERR_STATE, "kkt_debug_corrupt_map needs a bounds-check build");
+#endif
 }
 
 kkt_status kkt_factor_export(kkt_ctx* c, int64_t* colptr, int* rowind, double* val) {
@@ -2162,7 +2247,6 @@ __global__ void eval_fn_kernel(int fn, int n, const double* __restrict__ x, doub
         switch (fn) {
             case KKT_FN_RSQRT: r = kktgb::rsqrt_householder(a); break;
             case KKT_FN_RCP: r = kktgb::rcp_pos(a); break;
-            case KKT_FN_RCP_FAST: r = kktgb::rcp_pos_fast(a); break;
             case KKT_FN_SPLIT_M:
             case KKT_FN_SPLIT_E: {
                 double m;
@@ -2183,7 +2267,7 @@ __global__ void eval_fn_kernel(int fn, int n, const double* __restrict__ x, doub
 }  // namespace
 
 extern "C" kkt_status kkt_eval_fn(int fn, int n, const double* x, double* y, void* stream) {
-    if (fn < KKT_FN_RSQRT || fn > KKT_FN_RCP_FAST || n < 0 || (n > 0 && (!x || !y))) return KKT_ERR_ARG;
+    if (fn < KKT_FN_RSQRT || fn > KKT_FN_F32_ROUNDTRIP || n < 0 || (n > 0 && (!x || !y))) return KKT_ERR_ARG;
     if (n == 0) return KKT_OK;
     eval_fn_kernel<<<std::min((n + 255) / 256, 152 * 8), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
     return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_ERR_CUDA;

@@ -110,6 +110,12 @@ typedef struct {
                             analysis rejects other patterns (KKT_ERR_ARG);
                             kkt_factor_export is not available               */
     int block;           /* block size for solver 1 (2k+1 for the column)    */
+    int staged_solve;    /* 1 (default): the level-scheduled triangular
+                            solves stage each supernode's panel in shared
+                            memory and start while the previous level runs
+                            (programmatic dependent launch); 0: the plain
+                            level kernels.  Levels whose panels do not fit
+                            96 KB use the plain kernels either way          */
 } kkt_options;
 
 /* Per-call report.  Fields not touched by a call keep their values. */

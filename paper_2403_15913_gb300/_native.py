@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
                 ("tol_cg", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("target_relaxed", ctypes.c_int),
                 ("subtree_cols", ctypes.c_int), ("precision", ctypes.c_int),
-                ("solver", ctypes.c_int), ("block", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("block", ctypes.c_int),
+                ("staged_solve", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -644,9 +644,10 @@ normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __re
 // loads), the warps given to a row block split its columns, and their partial
 // sums meet in shared memory.  Each thread's column loads are issued in
 // batches of eight, so a batch costs one memory latency and the dependent
-// FMA chain per thread is c / (warps per row block) long, not c.
+// FMA chain per thread is c / (warps per row block) long, not c.  A has the
+// leading dimension ld: r in global memory, a padded stride when staged.
 template <typename T>
-__device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, int r,
+__device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, int r, int ld,
                                               const T* __restrict__ u, const int* __restrict__ rows,
                                               T* __restrict__ x, T (*part)[32], int* berr, int n) {
     const int tid = threadIdx.x, nw = blockDim.x >> 5, warp = tid >> 5, lane = tid & 31;
@@ -664,7 +665,7 @@ __device__ __forceinline__ void scatter_below(const T* __restrict__ A, int c, in
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int k = k0 + j * wpr;
-                    v[j] = k < c ? a[(long long)k * r] : T(0.0);
+                    v[j] = k < c ? a[(long long)k * ld] : T(0.0);
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -717,7 +718,7 @@ forward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict
         if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
     }
     __syncthreads();
-    scatter_below(A, c, r, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
+    scatter_below(A, c, r, r, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
 }
 
 // Backward substitution L^T w = z, one CTA per supernode of a level
@@ -793,6 +794,154 @@ backward_level_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restric
     }
 }
 
+// ------------------------------------------------------------- staged levels
+// Programmatic dependent launch: a level kernel lets the next one start at
+// once (launch_dependents), so the next level's CTAs load what does not
+// depend on x (the panel, its row indices, the pivots) while this level
+// still runs; grid_dependency_wait then blocks until the previous grid has
+// completed and its writes are visible.  Without the launch attribute the
+// wait returns at once and the trigger does nothing.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Leading dimension of a panel staged in shared memory: odd, so the lanes of
+// a column-strided access (lane = column) fall in different banks.
+__host__ __device__ __forceinline__ int staged_ld(int r) { return r | 1; }
+
+// Copy the r x c panel A (leading dimension r) to S (leading dimension ld).
+template <typename T>
+__device__ __forceinline__ void stage_panel(const T* __restrict__ A, int c, int r, int ld, T* __restrict__ S) {
+    const int tid = threadIdx.x, nt = blockDim.x, rc = r * c;
+    for (int e0 = tid; e0 < rc; e0 += 4 * nt) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * nt;
+            v[u] = e < rc ? A[e] : T(0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * nt;
+            if (e < rc) S[(e % r) + (e / r) * ld] = v[u];
+        }
+    }
+}
+
+// Forward substitution of one level with the panel staged in shared memory
+// before the wait on the previous level; after the wait it costs the warp
+// substitution and Lhat21 u.  Same arithmetic as forward_level_kernel.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+forward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
+                            T* __restrict__ x, const int* __restrict__ active) {
+    pdl_launch_dependents();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);   // panel, leading dimension staged_ld(r)
+    __shared__ T z[64];
+    __shared__ T part[kThreads / 32][32];
+    const int s = lvl_sn[blockIdx.x];
+    const bool ok = kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode);
+    const int f = ok ? P.sn_f[s] : 0, c = ok ? P.sn_c[s] : 0, r = ok ? P.sn_r[s] : 0;
+    const int ld = staged_ld(r);
+    if (ok) stage_panel(Lx + P.sn_lptr[s], c, r, ld, S);
+    grid_dependency_wait();
+    KKT_RETURN_IF_INACTIVE(active);
+    if (!ok) return;
+    __syncthreads();
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        const int lane = tid;
+        T z0 = lane < c ? __ldcg(x + f + lane) : T(0.0);
+        T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : T(0.0);
+        warp_lower_solve(S, ld, c, lane, z0, z1);   // unit lower triangular (normalised factor)
+        if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
+        if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
+    }
+    __syncthreads();
+    scatter_below(S, c, r, ld, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
+}
+
+// Backward substitution of one level, staged like the forward kernel (the
+// panel, the row indices below and the reciprocal pivots before the wait).
+// Shared memory: panel (arc elements), then x of the rows below (mrb), then
+// their indices (mrb ints).  Supernodes of <= 32 columns sum L21^T w with a
+// warp instruction over 32 / cp rows (lane = row group, column k < cp).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+backward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
+                             const T* __restrict__ dinv, T* __restrict__ x, int arc, int mrb,
+                             const int* __restrict__ active) {
+    pdl_launch_dependents();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    T* xb = S + arc;
+    int* rix = reinterpret_cast<int*>(xb + mrb);
+    __shared__ T part[kThreads / 32][64];
+    const int s = lvl_sn[blockIdx.x];
+    const bool ok = kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode);
+    const int f = ok ? P.sn_f[s] : 0, c = ok ? P.sn_c[s] : 0, r = ok ? P.sn_r[s] : 0;
+    const int ld = staged_ld(r), rb = r - c;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    T di0 = 0.0, di1 = 0.0;
+    if (ok) {
+        stage_panel(Lx + P.sn_lptr[s], c, r, ld, S);
+        const int* rows = P.rows + P.sn_rptr[s] + c;
+        for (int i = tid; i < rb; i += nt) {
+            const int rw = rows[i];
+            rix[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? rw : -1;
+        }
+        if (tid < 32) {
+            di0 = lane < c ? dinv[f + lane] : T(0.0);
+            di1 = lane + 32 < c ? dinv[f + lane + 32] : T(0.0);
+        }
+    }
+    grid_dependency_wait();
+    KKT_RETURN_IF_INACTIVE(active);
+    if (!ok) return;
+    __syncthreads();
+    for (int i = tid; i < rb; i += nt) xb[i] = rix[i] >= 0 ? __ldcg(x + rix[i]) : T(0.0);
+    __syncthreads();
+    if (c <= 32) {
+        const int cp = c == 1 ? 1 : 1 << (32 - __clz(c - 1));
+        const int k = lane & (cp - 1), G = 32 / cp;
+        T s0 = 0.0;
+        if (k < c)
+            for (int i = warp * G + lane / cp; i < rb; i += nw * G) s0 = fma(S[c + i + k * ld], xb[i], s0);
+        for (int off = cp; off < 32; off <<= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        if (lane < cp) part[warp][lane] = s0;
+    } else {
+        T s0 = 0.0, s1 = 0.0;
+        for (int i = warp; i < rb; i += nw) {
+            const T xv = xb[i];
+            s0 = fma(S[c + i + lane * ld], xv, s0);
+            if (lane + 32 < c) s1 = fma(S[c + i + (lane + 32) * ld], xv, s1);
+        }
+        part[warp][lane] = s0;
+        part[warp][lane + 32] = s1;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
+        T t0 = 0.0, t1 = 0.0;
+        if (lane < c) {
+            t0 = part[0][lane];
+            for (int w = 1; w < nw; ++w) t0 += part[w][lane];
+            t0 = fma(__ldcg(x + f + lane) * di0, di0, -t0);
+        }
+        if (lane + 32 < c) {
+            t1 = part[0][lane + 32];
+            for (int w = 1; w < nw; ++w) t1 += part[w][lane + 32];
+            t1 = fma(__ldcg(x + f + lane + 32) * di1, di1, -t1);
+        }
+        warp_upper_solve(S, ld, c, lane, t0, t1);   // unit upper triangular
+        if (lane < c) x[f + lane] = t0;
+        if (lane + 32 < c) x[f + lane + 32] = t1;
+    }
+}
+
 // ------------------------------------------------------------- subtrees
 // Small subtrees of the supernodal tree (task = its supernodes in
 // postorder) are processed by one CTA each, without per-level launches.
@@ -828,6 +977,7 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
                        const T* __restrict__ Lx, const T* __restrict__ dinv,
                        T* __restrict__ x,
     const int* __restrict__ active) {
+    pdl_launch_dependents();   // the first staged level may stage its panels during the last wave
     KKT_RETURN_IF_INACTIVE(active);
     __shared__ T z[64];
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -37,6 +37,7 @@ namespace {
 
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
 constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
+constexpr size_t kStagedSmemBytes = 96 * 1024;   // staged level solves: panel (+ x and indices below)
 constexpr int kSyrkStageBytes = 96 * 1024;       // split-level SYRK: L21 staged in shared memory
 constexpr int kClusterLevelMax = 32;             // split levels this small run as one cluster launch
 constexpr int kClusterSmemBytes = 96 * 1024;     // its diagonal block / staged L21
@@ -864,6 +865,39 @@ void set_backward_smem_limit() {
                          kBackwardSmemBytes);
     cudaFuncSetAttribute(backward_level_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kBackwardSmemBytes);
+    cudaFuncSetAttribute(forward_level_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kStagedSmemBytes);
+    cudaFuncSetAttribute(backward_level_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kStagedSmemBytes);
+}
+
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream runs; it waits for that kernel's
+// completion itself (grid_dependency_wait).  Captured into a graph this is
+// a programmatic dependency edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Shared memory of the staged level kernels for level l: the widest panel at
+// the padded leading dimension, and for the backward pass x and the row
+// indices of the rows below.
+size_t staged_panel_elems(const kkt_ctx* c, int l) { return (size_t)c->lvl_max_rc[l] + c->lvl_max_c[l]; }
+template <typename T>
+size_t staged_backward_bytes(const kkt_ctx* c, int l) {
+    return (staged_panel_elems(c, l) + c->lvl_max_rb[l]) * sizeof(T) + (size_t)c->lvl_max_rb[l] * sizeof(int);
 }
 
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
@@ -879,10 +913,16 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
     // (six per SM by registers) run 128-thread CTAs with the diagonal block
     // sized for the level's widest supernode: one wave instead of two.
     // Narrower levels keep a fixed 64 x 64 block.
+    // Levels whose panels fit kStagedSmemBytes run the staged kernels with
+    // programmatic dependent launch.
     for (int l = 0; l < c->nlev; ++l) {
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
-        if (cnt > 6 * kNumSMs) {
+        const size_t fsm = staged_panel_elems(c, l) * sizeof(T);
+        if (c->opt.staged_solve && fsm <= kStagedSmemBytes) {
+            launch_pdl(forward_level_staged_kernel<T>, cnt, cnt > 6 * kNumSMs ? kThreads / 2 : kThreads, fsm, st,
+                       c->plan, lsn, (const T*)Lx, xp, active);
+        } else if (cnt > 6 * kNumSMs) {
             const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
             forward_level_kernel<T, true><<<cnt, kThreads / 2, dsm, st>>>(c->plan, lsn, Lx, dinv, xp, active);
         } else {
@@ -893,6 +933,12 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
         const bool wide = cnt > 6 * kNumSMs;
+        const size_t bsm = staged_backward_bytes<T>(c, l);
+        if (c->opt.staged_solve && bsm <= kStagedSmemBytes) {
+            launch_pdl(backward_level_staged_kernel<T>, cnt, wide ? kThreads / 2 : kThreads, bsm, st, c->plan, lsn,
+                       (const T*)Lx, (const T*)dinv, xp, (int)staged_panel_elems(c, l), c->lvl_max_rb[l], active);
+            continue;
+        }
         const int dsz = wide ? c->lvl_max_c[l] * c->lvl_max_c[l] : 0;
         const size_t xsm = (size_t)c->lvl_max_rb[l] * sizeof(T);
         const size_t dbytes = wide ? (size_t)dsz * sizeof(T) : 64 * 64 * sizeof(T);   // dynamic or static
@@ -1319,6 +1365,7 @@ void kkt_default_options(kkt_options* o) {
     o->precision = 0;
     o->solver = 0;
     o->block = 0;
+    o->staged_solve = 1;
 }
 
 namespace {

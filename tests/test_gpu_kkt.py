@@ -134,13 +134,15 @@ def test_nonfinite_values_report_oracle_column(where, bad):
     assert s.info.failed_col == e.value.column
 
 
+@pytest.mark.parametrize("staged", [1, 0])
 @pytest.mark.parametrize("sig,D,dx0", [((1e-2, 1e2), 1e2, 10.0), ((1e-6, 1e6), 1e8, 0.0)])
-def test_backsolve_matches_oracle(sig, D, dx0):
+def test_backsolve_matches_oracle(sig, D, dx0, staged):
     """K^{-1} b by the supernodal triangular solves equals the oracle's
-    left-looking factor + column substitutions."""
+    left-looking factor + column substitutions (staged and plain level
+    kernels)."""
     torch = torch_cuda()
     p, pt, W, J = instance(32, 50, 0, sigma_range=sig)
-    s = solver_for(p, W, J, scheme="lifted", **OPTS)
+    s = solver_for(p, W, J, scheme="lifted", staged_solve=staged, **OPTS)
     assert s.factor(to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma),
                     to_dev(torch, np.full(p.m, D)), dx0) == 0
     b = np.random.default_rng(3).standard_normal(p.n)

@@ -138,6 +138,10 @@ def parse():
                     help="batch workload: pick the supernode partition with kkt_autotune_batch first")
     ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batch workload: kkt_factor_batch + kkt_solve instead of the one-graph step")
+    ap.add_argument("--no-serial", action="store_true",
+                    help="batch workload: skip the one-context-per-instance comparison")
     ap.add_argument("--no-sub", action="store_true",
                     help="default workload: skip the sub-records of the other configurations")
     ap.add_argument("--seed", type=int, default=0)
@@ -797,7 +801,13 @@ def run_batch(args, ws, rank, local):
         bad = bs.results()["failed_col"] >= 0
         delta[bad] = np.where(delta[bad] == 0, 1e-4, delta[bad] * 8)
 
+    # FP64: the whole step as one graph launch (kkt_factor_solve); the FP32
+    # factor (with its FP64 fallback) keeps the two calls
+    use_graph = prec == 0 and not getattr(args, "no_graph", False)
+
     def step(d):
+        if use_graph:
+            return bs.factor_solve(d["W"], d["J"], d["sigma"], None, delta, d["rx"], d["ry"], dx, dy)
         bs.factor_batch(d["W"], d["J"], d["sigma"], None, delta)
         return bs.solve(d["rx"], d["ry"], dx, dy)
 
@@ -865,15 +875,14 @@ def run_batch(args, ws, rank, local):
     # end to end: values and right-hand sides host->device, batched factor +
     # solve, (dx, dy) device->host
     h_out = torch.empty(bs.n + bs.m, dtype=torch.float64).pin_memory()
-    d_e2e = {k: torch.empty_like(v) for k, v in d_in.items()}
     e2e = []
     for rep in range(4):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for k in d_e2e:
-            d_e2e[k].copy_(h_in[k], non_blocking=True)
-        step(d_e2e)
+        for k in d_in:   # into the buffers the graph was captured with
+            d_in[k].copy_(h_in[k], non_blocking=True)
+        step(d_in)
         h_out[:bs.n].copy_(dx, non_blocking=True)
         h_out[bs.n:].copy_(dy, non_blocking=True)
         e1.record(stream)
@@ -905,10 +914,16 @@ def run_batch(args, ws, rank, local):
                    "autotuned": tuned,
                    "l2": "flushed (256 MB write) between timed steps",
                    "analyse_s": round(t_analyse, 3), "factor_gflop": sym.flops / 1e9,
-                   "factor_ms": factor_ms, "kinv_ms": st["solve_ms"] / max(1, st["kinv_calls"]),
+                   "factor_ms": factor_ms,
+                   "kinv_ms": None if use_graph else st["solve_ms"] / max(1, st["kinv_calls"]),
+                   "refinement_ms": st["solve_ms"] / max(1, args.steps) if use_graph else None,
                    "tree_levels": sym.levels, "statuses": sorted(statuses),
                    "max_bwd_err": max(etas), "max_refine_iters": int(res["refine_iters"].max()),
                    "fp64_fallbacks": st["fp64_fallbacks"],
+                   "step": ("one CUDA graph launch per step (kkt_factor_solve: factor, refinement "
+                            "sweeps as a conditional WHILE node)" if use_graph
+                            else "kkt_factor_batch + kkt_solve"),
+                   "graph_launches_per_step": st["graph_steps"] / max(1, args.steps),
                    "delta_x_nonzero": int((delta > 0).sum()),
                    "per_instance_fp64_path": ({"ms_per_batch": statistics.mean(ser_ms),
                                                "solves_per_s": args.batch / (statistics.mean(ser_ms) * 1e-3),
@@ -1084,7 +1099,8 @@ def sub_records(args, local):
         return {"solves_per_s": ln["value"], "ms_per_batch": ln["ms_per_step"],
                 "e2e_solves_per_s": ln["e2e"]["value"], "factor_ms": c["factor_ms"],
                 "factor_frac_of_peak": ln["roofline"]["frac"], "max_bwd_err": c["max_bwd_err"],
-                "per_instance_fp64": c["per_instance_fp64_path"], "steps": ln["steps"],
+                "per_instance_fp64": c["per_instance_fp64_path"], "step": c["step"],
+                "graph_launches_per_step": c["graph_launches_per_step"], "steps": ln["steps"],
                 "clocks": ln["clocks"]}
 
     def serve():

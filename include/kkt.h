@@ -251,6 +251,33 @@ kkt_status kkt_factor_batch(kkt_ctx* ctx, const double* d_Wval, const double* d_
                             const double* d_sigma, const double* d_D, const double* delta_x,
                             cudaStream_t stream, kkt_info* info);
 
+/* One Newton step's linear algebra (Sec. III, the factorisation of Sec. V-B
+ * and the refined Lifted-KKT or HyKKT solve of Sec. IV) as ONE CUDA graph
+ * launch: kkt_factor_batch(d_Wval, d_Jval, d_sigma, d_D, delta_x) followed
+ * by kkt_solve(d_rx, d_ry, d_dx, d_dy, NULL), with the refinement sweeps
+ * (and HyKKT's CG iterations) as conditional WHILE nodes whose conditions
+ * kernels set on the device, so that the host waits once, at the end.  The
+ * stopping rules, kernels and per-instance results (kkt_batch_results,
+ * info) are those of the two calls; kkt_solve and kkt_backsolve may follow
+ * with the factor left behind.
+ *   delta_x: host array of one value >= 0 per instance (one value for a
+ *            kkt_analyse context), copied to pinned memory and from there
+ *            to the device inside the graph;
+ *   the device buffers as for kkt_factor_batch and kkt_solve (all but d_D
+ *            non-NULL).
+ * The graph is captured on the first call and replayed while the eight
+ * device pointers stay the same; other pointers capture it again (a few
+ * ms).  Supernodal FP64 factor only (options solver 0, precision 0; other
+ * settings return KKT_ERR_ARG).  Returns KKT_ERR_NOT_SPD when some
+ * instance's pivot failed (kkt_batch_results names them; the others are
+ * solved), else KKT_OK, KKT_ERR_MAXIT or KKT_ERR_STALL as kkt_solve.
+ * Synchronises the stream; the pinned buffers of the context are reused,
+ * so calls on one context from several host threads must be serialised. */
+kkt_status kkt_factor_solve(kkt_ctx* ctx, const double* d_Wval, const double* d_Jval,
+                            const double* d_sigma, const double* d_D, const double* delta_x,
+                            const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
+                            cudaStream_t stream, kkt_info* info);
+
 /* Autotuner of the supernode partition (the panel shapes the factor
  * kernels work on) for a batch, on this GPU: up to `sample` instances
  * (evenly spaced; <= 0 means 32) are analysed with each candidate setting of
@@ -339,6 +366,8 @@ typedef struct {
                                 double-float, precision 1 or 2)           */
     int64_t fp64_fallbacks;  /* FP64 refactorizations after an FP32 factor
                                 failed or did not refine to tol_refine    */
+    int64_t graph_steps;     /* kkt_factor_solve calls (one graph launch
+                                each)                                     */
 } kkt_stats;
 
 kkt_status kkt_set_profiling(kkt_ctx* ctx, int enable);

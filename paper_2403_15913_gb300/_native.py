@@ -31,7 +31,7 @@ EXPORTED = [
     "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
     "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_backsolve_noalloc",
     "kkt_factor_export", "kkt_analyse_batch", "kkt_analyse_batch_host", "kkt_batch_layout",
-    "kkt_factor_batch", "kkt_batch_results", "kkt_autotune_batch",
+    "kkt_factor_batch", "kkt_factor_solve", "kkt_batch_results", "kkt_autotune_batch",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
     "kkt_ipm_default_options", "kkt_ipm_create", "kkt_ipm_init", "kkt_ipm_step", "kkt_ipm_solve",
@@ -75,7 +75,8 @@ class Stats(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("factor_launches", ctypes.c_int64),
                 ("factor_calls", ctypes.c_int64), ("kinv_calls", ctypes.c_int64),
-                ("fp32_factors", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64)]
+                ("fp32_factors", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64),
+                ("graph_steps", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -171,6 +172,8 @@ def load(path):
     L.kkt_batch_layout.restype = ctypes.c_int
     L.kkt_factor_batch.argtypes = [P, P, P, P, P, F64P, P, ctypes.POINTER(Info)]
     L.kkt_factor_batch.restype = ctypes.c_int
+    L.kkt_factor_solve.argtypes = [P, P, P, P, P, F64P, P, P, P, P, P, ctypes.POINTER(Info)]
+    L.kkt_factor_solve.restype = ctypes.c_int
     L.kkt_autotune_batch.argtypes = [ctypes.c_int, I32P, I32P, I32PP, I32PP, I32PP, I32PP,
                                      ctypes.POINTER(Options), ctypes.c_int, P, ctypes.POINTER(Options),
                                      F64P]

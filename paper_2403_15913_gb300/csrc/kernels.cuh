@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "fp64_lean.cuh"
 #include "sparse_dot.cuh"
@@ -1419,6 +1420,93 @@ cg_check_kernel(int nb, double* __restrict__ cgs, int* __restrict__ cgi, int max
     }
     mine = block_or(mine);
     if (threadIdx.x == 0) any[0] = mine;
+}
+
+// ---- the one-graph step (kkt_factor_solve): refinement and CG loops as
+// conditional WHILE nodes whose conditions these kernels set.
+// Per instance rst[4 i + {0: state, 1: stalled sweeps, 2: sweeps, 3: CG
+// iterations}], reta[2 i + {0: eta, 1: previous eta}]; ctl[0] = index of
+// the next sweep.
+constexpr int kRefineRunning = 1;
+
+// Before the first sweep: instances with a factor run, the others report
+// not-SPD (code nspd); the loop runs if any instance does.  One CTA.
+__global__ void __launch_bounds__(kThreads)
+refine_init_kernel(int nb, const int* __restrict__ fail, int nofail, int nspd, int* __restrict__ act,
+                   int* __restrict__ rst, double* __restrict__ reta, int* __restrict__ ctl,
+                   cudaGraphConditionalHandle loop) {
+    int mine = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const int run = fail[i] == nofail ? 1 : 0;
+        rst[4 * i + 0] = run ? kRefineRunning : nspd;
+        rst[4 * i + 1] = 0;
+        rst[4 * i + 2] = 0;
+        rst[4 * i + 3] = 0;
+        reta[2 * i + 0] = CUDART_INF;
+        reta[2 * i + 1] = CUDART_INF;
+        act[i] = run;
+        mine |= run;
+    }
+    mine = block_or(mine);
+    if (threadIdx.x == 0) {
+        ctl[0] = 0;
+        cudaGraphSetConditional(loop, mine ? 1u : 0u);
+    }
+}
+
+// After sweep k = ctl[0]: the backward error of every running instance,
+// eta = ||r||_inf / (||K||_inf ||v||_inf + ||b||_inf) from the residual
+// maxima red[3 i + {r, v, b}], then the stopping rules (tol: KKT_OK, two
+// successive sweeps above 0.9 of the previous eta: code stall); the loop
+// continues while an instance runs and k + 1 <= max_refine.  One CTA.
+__global__ void __launch_bounds__(kThreads)
+refine_update_kernel(int nb, const double* __restrict__ red, const double* __restrict__ knorm, double tol,
+                     int max_refine, int ok_code, int stall_code, int* __restrict__ act, int* __restrict__ rst,
+                     double* __restrict__ reta, int* __restrict__ ctl, cudaGraphConditionalHandle loop) {
+    const int k = ctl[0];
+    int mine = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        if (rst[4 * i] != kRefineRunning) continue;
+        const double rmax = red[3 * i], vmax = red[3 * i + 1], bmax = red[3 * i + 2];
+        const double den = knorm[i] * vmax + bmax;
+        const double e = den > 0 ? rmax / den : (rmax > 0 ? CUDART_INF : 0.0);
+        int state = kRefineRunning;
+        rst[4 * i + 2] = k;
+        if (e <= tol) {
+            state = ok_code;
+        } else if (k > 0 && e > 0.9 * reta[2 * i + 1]) {
+            if (++rst[4 * i + 1] >= 2) state = stall_code;
+        } else {
+            rst[4 * i + 1] = 0;
+        }
+        rst[4 * i] = state;
+        reta[2 * i + 1] = e;
+        reta[2 * i] = e;
+        act[i] = state == kRefineRunning ? 1 : 0;
+        mine |= act[i];
+    }
+    mine = block_or(mine);
+    if (threadIdx.x == 0) {
+        ctl[0] = k + 1;
+        cudaGraphSetConditional(loop, (mine && k + 1 <= max_refine) ? 1u : 0u);
+    }
+}
+
+// CG loop condition: some instance's CG still runs (flag any[0] of
+// cg_init_kernel / cg_check_kernel); count[0] += inc counts the iterations
+// the loop ran.
+__global__ void cg_cond_kernel(const int* __restrict__ any, cudaGraphConditionalHandle loop,
+                               int* __restrict__ count, int inc) {
+    if (threadIdx.x == 0) {
+        count[0] += inc;
+        cudaGraphSetConditional(loop, any[0] ? 1u : 0u);
+    }
+}
+
+// After an inner HyKKT solve: add every instance's CG iterations.
+__global__ void cg_count_kernel(int nb, const int* __restrict__ cgi, int* __restrict__ rst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+        rst[4 * i + 3] += cgi[2 * i + 1];
 }
 
 }  // namespace kktgb

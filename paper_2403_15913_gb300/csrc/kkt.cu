@@ -193,6 +193,24 @@ struct kkt_ctx {
         int kind;   // 0 assemble, 1 factor, 2 solve, 3 other
     };
     std::vector<Span> spans;
+    // one-graph factor + refined solve (kkt_factor_solve): the graph, the
+    // device pointers it was captured with, its capture streams (main,
+    // refinement body, CG body) and external event nodes (factor start,
+    // factor end, end); device refinement state; pinned results; kernel
+    // launches per replay (before the loop, per sweep, per CG iteration)
+    bool capturing = false;   // enqueue solves directly, no nested graph launch
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    const void* step_key[9] = {};
+    cudaStream_t cap[3] = {};
+    cudaEvent_t step_ev[3] = {};
+    int* d_rst = nullptr;       // 4 per instance (state, stalled, sweeps, CG iterations)
+    double* d_reta = nullptr;   // 2 per instance (eta, previous eta)
+    int* d_rctl = nullptr;      // next sweep, CG iterations run
+    int* h_rst = nullptr;       // pinned: rst (4 nb), fail (nb), ctl (2)
+    double* h_reta = nullptr;   // pinned: reta (2 nb), knorm (nb)
+    double* hp_delta = nullptr; // pinned: delta_x per instance
+    long long step_pre = 0, step_sweep = 0, step_cgit = 0, step_fl = 0;
 };
 
 namespace {
@@ -995,7 +1013,7 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
         scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_xp32, out, nullptr);
     } else {
         gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, in, c->w_xp, nullptr);
-        if (c->tri_exec) {
+        if (c->tri_exec && !c->capturing) {
             CUDA_TRY(c, cudaGraphLaunch(c->tri_exec, st));
         } else {
             enqueue_triangular_solves(c, c->w_xp, st, nullptr);
@@ -1020,15 +1038,21 @@ void seg_dot(kkt_ctx* c, const double* a, const double* b, int slot, cudaStream_
 
 // r = b - K_orig v and the backward error of every instance (host sync):
 // eta_i = ||r_i||_inf / (||K_i||_inf ||v_i||_inf + ||b_i||_inf).
-kkt_status residual(kkt_ctx* c, const double* bx, const double* by, const double* vx,
-                    const double* vy, double* rx, double* ry, cudaStream_t st, std::vector<double>& eta) {
-    const int n = c->n, nb = c->nb;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_red, 0, 3 * (size_t)nb * sizeof(double), st));
+kkt_status enqueue_residual(kkt_ctx* c, const double* bx, const double* by, const double* vx,
+                            const double* vy, double* rx, double* ry, cudaStream_t st) {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_red, 0, 3 * (size_t)c->nb * sizeof(double), st));
     c->stats.launches += 1;
     residual_kernel<<<c->nch_xy, kThreads, 0, st>>>(
-        c->d_ch_xy, n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_j_col,
+        c->d_ch_xy, c->n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx, c->f_W, c->d_j_ptr, c->d_j_col,
         c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->f_J, c->f_sigma, c->f_delta_x, c->f_dvec, c->f_C,
         bx, by, vx, vy, rx, ry, c->d_red);
+    return KKT_OK;
+}
+
+kkt_status residual(kkt_ctx* c, const double* bx, const double* by, const double* vx,
+                    const double* vy, double* rx, double* ry, cudaStream_t st, std::vector<double>& eta) {
+    const int nb = c->nb;
+    TRY(enqueue_residual(c, bx, by, vx, vy, rx, ry, st));
     CUDA_TRY(c, cudaMemcpyAsync(c->h_red, c->d_red, 3 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     eta.resize(nb);
@@ -2127,6 +2151,345 @@ static kkt_status solve_impl(kkt_ctx* c, const double* d_rx, const double* d_ry,
     return result;
 }
 
+}  // extern "C"
+
+namespace {
+// ------------------------------------------------------------- one-graph step
+// A WHILE node on the conditional handle h after the work captured so far on
+// st; the capture continues after the node.  Returns the (empty) body graph.
+kkt_status add_while_node(kkt_ctx* c, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(c, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return set_err(c, KKT_ERR_INTERNAL, "WHILE node outside a capture");
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(c, cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    *body = np.conditional.phGraph_out[0];
+    CUDA_TRY(c, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return KKT_OK;
+}
+
+// Kernel nodes of a graph (not counting the bodies of its conditional nodes).
+long long kernel_nodes(cudaGraph_t g) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return 0;
+    long long k = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+kkt_status new_handle(kkt_ctx* c, cudaStream_t st, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(c, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return set_err(c, KKT_ERR_INTERNAL, "handle outside a capture");
+    CUDA_TRY(c, cudaGraphConditionalHandleCreate(h, g, 0, 0));
+    return KKT_OK;
+}
+
+// HyKKT inner solve inside the captured step: the steps of hykkt_inner,
+// with the CG loop as a WHILE node (condition: some instance's CG runs,
+// checked after every iteration) and the CG counts added on the device.
+kkt_status hykkt_inner_graph(kkt_ctx* c, const double* rx, const double* ry, double* dx, double* dy,
+                             cudaStream_t st) {
+    const int n = c->n, m = c->m, nb = c->nb;
+    const double gamma = c->f_Dconst;
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                     c->f_J, rx, ry, nullptr, 1.0, gamma, c->w_rg, nullptr);
+    TRY(apply_kinv(c, c->w_rg, c->w_q, st));
+    j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->f_J, c->w_q, ry,
+                                                     nullptr, 1.0, c->w_res, nullptr);
+    CUDA_TRY(c, cudaMemsetAsync(c->w_cgx, 0, m * sizeof(double), st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->w_p, c->w_res, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    seg_dot(c, c->w_res, c->w_res, 0, st);
+    cg_init_kernel<<<1, kThreads, 0, st>>>(nb, c->d_cgs, c->d_cgi, c->d_act, c->opt.tol_cg, c->opt.max_cg,
+                                           c->d_cg);
+    cudaGraphConditionalHandle h;
+    TRY(new_handle(c, st, &h));
+    cg_cond_kernel<<<1, 32, 0, st>>>(c->d_cg, h, c->d_rctl + 1, 0);
+    cudaGraph_t body = nullptr;
+    TRY(add_while_node(c, st, h, &body));
+    cudaStream_t bs = c->cap[2];
+    CUDA_TRY(c, cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_cg_iteration<double>(c, c->d_Lx, c->d_dinv, c->w_xp, bs);
+    cg_cond_kernel<<<1, 32, 0, bs>>>(c->d_cg, h, c->d_rctl + 1, 1);
+    cudaGraph_t done = nullptr;
+    CUDA_TRY(c, cudaStreamEndCapture(bs, &done));
+    c->step_cgit = kernel_nodes(body);
+    cg_count_kernel<<<grid_for(nb), kThreads, 0, st>>>(nb, c->d_cgi, c->d_rst);
+    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                     c->f_J, c->w_rg, c->w_cgx, nullptr, 1.0, -1.0,
+                                                     c->w_tn, nullptr);
+    TRY(apply_kinv(c, c->w_tn, dx, st));
+    CUDA_TRY(c, cudaMemcpyAsync(dy, c->w_cgx, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return KKT_OK;
+}
+
+// The whole step on the capture stream: input copies, per-instance
+// delta_x, assembly and factorisation (||K||_inf on the side stream),
+// then the refinement loop as a WHILE node and the copies of the results
+// to pinned host memory.  The f_* inputs are set by the caller.
+kkt_status capture_step_body(kkt_ctx* c, const double* W, const double* J, const double* sigma,
+                             const double* D, const double* d_rx, const double* d_ry, double* d_dx,
+                             double* d_dy) {
+    cudaStream_t st = c->cap[0];
+    const int n = c->n, m = c->m, nb = c->nb;
+    CUDA_TRY(c, cudaEventRecordWithFlags(c->step_ev[0], st, cudaEventRecordExternal));
+    if (c->nnzW > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_W, W, (size_t)c->nnzW * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (c->nnzJ > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_J, J, (size_t)c->nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->v_sigma, sigma, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (c->f_D && m > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->v_D, D, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_dval, c->hp_delta, (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    expand_kernel<<<c->nch_x, kThreads, 0, st>>>(c->d_ch_xy, c->d_dval, c->d_dvec);
+    if (c->nnzJ > 0)
+        scale_rows_sqrt_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->f_J, c->f_D, c->f_Dconst,
+                                                                 c->v_Js);
+    CUDA_TRY(c, cudaEventRecord(c->ev_in, st));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_in, 0));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_knorm, 0, (size_t)nb * sizeof(double), c->side));
+    if (c->f_C) {
+        if (c->f_D) recip_kernel<<<grid_for(m), kThreads, 0, c->side>>>(m, c->f_D, c->d_Cbuf.p);
+        else fill_kernel<<<grid_for(m), kThreads, 0, c->side>>>(m, c->opt.delta, c->d_Cbuf.p);
+    }
+    knorm_kernel<<<c->nch_xy, kThreads, 0, c->side>>>(c->d_ch_xy, n, c->d_wf_ptr, c->d_wf_col, c->d_wf_idx,
+                                                      c->f_W, c->d_j_ptr, c->d_jt_ptr, c->d_jt_idx, c->f_J,
+                                                      c->f_sigma, 0.0, c->f_dvec, c->f_C, c->d_knorm);
+    CUDA_TRY(c, cudaEventRecord(c->ev_side, c->side));
+    const long long f0 = c->stats.factor_launches;
+    TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, 0.0, st));
+    c->step_fl = c->stats.factor_launches - f0;
+    CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev_side, 0));
+    CUDA_TRY(c, cudaEventRecordWithFlags(c->step_ev[1], st, cudaEventRecordExternal));
+    // refinement (the rules of kkt_solve, on the device)
+    double* rx = c->w_r;
+    double* ry = c->w_r + n;
+    double* dx = c->w_d;
+    double* dy = c->w_d + n;
+    CUDA_TRY(c, cudaMemsetAsync(d_dx, 0, n * sizeof(double), st));
+    CUDA_TRY(c, cudaMemsetAsync(d_dy, 0, m * sizeof(double), st));
+    CUDA_TRY(c, cudaMemcpyAsync(rx, d_rx, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(ry, d_ry, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_rctl, 0, 2 * sizeof(int), st));
+    cudaGraphConditionalHandle h;
+    TRY(new_handle(c, st, &h));
+    refine_init_kernel<<<1, kThreads, 0, st>>>(nb, c->d_fail, kNoFail, (int)KKT_ERR_NOT_SPD, c->d_act, c->d_rst,
+                                               c->d_reta, c->d_rctl, h);
+    cudaGraph_t body = nullptr;
+    TRY(add_while_node(c, st, h, &body));
+    cudaStream_t bs = c->cap[1];
+    CUDA_TRY(c, cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (c->opt.scheme == KKT_LIFTED) {
+        TRY(lifted_precond(c, rx, ry, dx, dy, bs));
+    } else {
+        TRY(hykkt_inner_graph(c, rx, ry, dx, dy, bs));
+    }
+    seg_axpy_kernel<<<c->nch_xy, kThreads, 0, bs>>>(c->d_ch_xy, n, c->d_act, dx, dy, d_dx, d_dy);
+    TRY(enqueue_residual(c, d_rx, d_ry, d_dx, d_dy, rx, ry, bs));
+    refine_update_kernel<<<1, kThreads, 0, bs>>>(nb, c->d_red, c->d_knorm, c->opt.tol_refine, c->opt.max_refine,
+                                                 (int)KKT_OK, (int)KKT_ERR_STALL, c->d_act, c->d_rst, c->d_reta,
+                                                 c->d_rctl, h);
+    cudaGraph_t done = nullptr;
+    CUDA_TRY(c, cudaStreamEndCapture(bs, &done));
+    c->step_sweep = kernel_nodes(body);
+    CUDA_TRY(c, cudaEventRecordWithFlags(c->step_ev[2], st, cudaEventRecordExternal));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_rst, c->d_rst, 4 * (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_rst + 4 * nb, c->d_fail, (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_rst + 5 * nb, c->d_rctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_reta, c->d_reta, 2 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_reta + 2 * nb, c->d_knorm, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                st));
+    return KKT_OK;
+}
+
+kkt_status build_step_graph(kkt_ctx* c, const double* W, const double* J, const double* sigma, const double* D,
+                            const double* d_rx, const double* d_ry, double* d_dx, double* d_dy) {
+    const int nb = c->nb;
+    for (auto& s : c->cap)
+        if (!s) CUDA_TRY(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (auto& e : c->step_ev)
+        if (!e) CUDA_TRY(c, cudaEventCreate(&e));
+    if (!c->d_rst) {
+        TRY(alloc(c, &c->d_rst, 4 * (size_t)nb));
+        TRY(alloc(c, &c->d_reta, 2 * (size_t)nb));
+        TRY(alloc(c, &c->d_rctl, 2));
+        CUDA_TRY(c, cudaMallocHost((void**)&c->h_rst, (5 * (size_t)nb + 2) * sizeof(int)));
+        CUDA_TRY(c, cudaMallocHost((void**)&c->h_reta, 3 * (size_t)nb * sizeof(double)));
+    }
+    if (!c->d_dvec) TRY(alloc(c, &c->d_dvec, c->n));
+    if (!c->d_dval) TRY(alloc(c, &c->d_dval, nb));
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->step_graph) cudaGraphDestroy(c->step_graph);
+    c->step_exec = nullptr;
+    c->step_graph = nullptr;
+    const kkt_stats saved = c->stats;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    c->capturing = true;
+    c->step_cgit = 0;
+    kkt_status r = KKT_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap[0], cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        r = capture_step_body(c, W, J, sigma, D, d_rx, d_ry, d_dx, d_dy);
+        e = cudaStreamEndCapture(c->cap[0], &g);
+    }
+    c->capturing = false;
+    c->profiling = prof;
+    c->stats = saved;
+    if (r == KKT_OK && e != cudaSuccess) r = set_err(c, KKT_ERR_CUDA, std::string("step graph capture: ") +
+                                                                       cudaGetErrorString(e));
+    if (r == KKT_OK) {
+        e = cudaGraphInstantiate(&c->step_exec, g, 0);
+        if (e != cudaSuccess) r = set_err(c, KKT_ERR_CUDA, std::string("step graph instantiate: ") +
+                                                             cudaGetErrorString(e));
+    }
+    if (r != KKT_OK) {
+        if (g) cudaGraphDestroy(g);
+        c->step_exec = nullptr;
+        cudaGetLastError();
+        return r;
+    }
+    c->step_graph = g;
+    c->step_pre = kernel_nodes(g);
+    c->step_key[0] = W;
+    c->step_key[1] = J;
+    c->step_key[2] = sigma;
+    c->step_key[3] = D;
+    c->step_key[4] = d_rx;
+    c->step_key[5] = d_ry;
+    c->step_key[6] = d_dx;
+    c->step_key[7] = d_dy;
+    c->step_key[8] = reinterpret_cast<const void*>((intptr_t)(c->opt.target_relaxed + 2));
+    return KKT_OK;
+}
+
+kkt_status factor_solve_impl(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
+                             const double* d_D, const double* delta_x, const double* d_rx, const double* d_ry,
+                             double* d_dx, double* d_dy, cudaStream_t st, kkt_info* info) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->device_ready) return set_err(c, KKT_ERR_STATE, "context was analysed on the host only");
+    if (c->opt.solver != 0 || c->opt.precision != 0)
+        return set_err(c, KKT_ERR_ARG, "kkt_factor_solve: supernodal FP64 factor only (solver 0, precision 0)");
+    if (!d_Wval && c->nnzW > 0) return set_err(c, KKT_ERR_ARG, "d_Wval is NULL");
+    if (!d_Jval && c->nnzJ > 0) return set_err(c, KKT_ERR_ARG, "d_Jval is NULL");
+    if (!d_sigma) return set_err(c, KKT_ERR_ARG, "d_sigma is NULL");
+    if (!d_rx || !d_ry || !d_dx || !d_dy) return set_err(c, KKT_ERR_ARG, "NULL vector");
+    if (!delta_x) return set_err(c, KKT_ERR_ARG, "delta_x is NULL");
+    if (c->opt.scheme == KKT_HYKKT && d_D) return set_err(c, KKT_ERR_ARG, "HyKKT takes D = gamma");
+    const int nb = c->nb, m = c->m;
+    for (int i = 0; i < nb; ++i)
+        if (!(std::isfinite(delta_x[i]) && delta_x[i] >= 0))
+            return set_err(c, KKT_ERR_ARG, "bad delta_x of instance " + std::to_string(i));
+    if (!c->hp_delta) CUDA_TRY(c, cudaMallocHost((void**)&c->hp_delta, (size_t)nb * sizeof(double)));
+    // the launch below reads hp_delta: no earlier replay may still be in flight
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    for (int i = 0; i < nb; ++i) c->hp_delta[i] = delta_x[i];
+    c->factored = false;
+    const bool hasD = c->opt.scheme == KKT_LIFTED && d_D;
+    c->f_W = c->v_W;
+    c->f_J = c->v_J;
+    c->f_sigma = c->v_sigma;
+    c->f_D = hasD ? c->v_D : nullptr;
+    c->f_Dconst = c->opt.scheme == KKT_LIFTED ? 1.0 / c->opt.delta : c->opt.gamma;
+    c->f_delta_x = 0.0;
+    c->f_C = nullptr;
+    if (c->opt.scheme == KKT_LIFTED && c->opt.target_relaxed) {
+        if (!c->d_Cbuf.p) {
+            TRY(alloc(c, &c->d_Cbuf.p, m));
+            c->d_Cbuf.n = m;
+        }
+        c->f_C = c->d_Cbuf.p;
+    }
+    if (!c->d_dvec) TRY(alloc(c, &c->d_dvec, c->n));
+    c->f_dvec = c->d_dvec;
+    const void* key[9] = {d_Wval, d_Jval, d_sigma, hasD ? d_D : nullptr, d_rx, d_ry, d_dx, d_dy,
+                          reinterpret_cast<const void*>((intptr_t)(c->opt.target_relaxed + 2))};
+    if (!c->step_exec || !std::equal(key, key + 9, c->step_key))
+        TRY(build_step_graph(c, d_Wval, d_Jval, d_sigma, hasD ? d_D : nullptr, d_rx, d_ry, d_dx, d_dy));
+    CUDA_TRY(c, cudaGraphLaunch(c->step_exec, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    // results and counters
+    const int* rs = c->h_rst;
+    const int* fail = c->h_rst + 4 * nb;
+    const int sweeps = c->h_rst[5 * nb], cgits = c->h_rst[5 * nb + 1];
+    c->stats.graph_steps++;
+    c->stats.factor_calls++;
+    c->stats.factor_launches += c->step_fl;
+    c->stats.launches += c->step_pre + (long long)sweeps * c->step_sweep + (long long)cgits * c->step_cgit;
+    c->stats.kinv_calls += c->opt.scheme == KKT_LIFTED ? sweeps : 2LL * sweeps + cgits;
+    if (c->profiling) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, c->step_ev[0], c->step_ev[1]) == cudaSuccess) c->stats.factor_ms += a;
+        if (cudaEventElapsedTime(&b, c->step_ev[1], c->step_ev[2]) == cudaSuccess) c->stats.solve_ms += b;
+    }
+    int nfail = 0, first_fail = -1, refine_max = 0, cg_total = 0;
+    double eta_max = 0.0;
+    kkt_status result = KKT_OK;
+    for (int i = 0; i < nb; ++i) {
+        const bool failed = fail[i] != kNoFail;
+        int state = rs[4 * i];
+        if (state == kRefineRunning) state = KKT_ERR_MAXIT;
+        c->r_fail[i] = failed ? fail[i] : -1;
+        c->r_status[i] = state;
+        c->r_refine[i] = rs[4 * i + 2];
+        c->r_cg[i] = rs[4 * i + 3];
+        c->r_eta[i] = failed ? INFINITY : c->h_reta[2 * i];
+        c->h_knorm[i] = c->h_reta[2 * nb + i];
+        cg_total += c->r_cg[i];
+        if (failed) {
+            ++nfail;
+            if (first_fail < 0) first_fail = fail[i];
+            continue;
+        }
+        refine_max = std::max(refine_max, c->r_refine[i]);
+        eta_max = std::max(eta_max, c->r_eta[i]);
+        if (state != KKT_OK && result == KKT_OK) result = (kkt_status)state;
+    }
+    c->knorm = c->h_knorm[0];
+    c->cur_prec = 0;
+    c->factored = nfail == 0 || (nb > 1 && nfail < nb);
+    if (info) {
+        info->failed_col = first_fail;
+        info->delta_x = c->hp_delta[0];
+        info->status_detail = 0;
+        info->refine_iters = refine_max;
+        info->cg_iters = cg_total;
+        info->bwd_err = eta_max;
+    }
+    if (nfail > 0)
+        return set_err(c, KKT_ERR_NOT_SPD, "factorization: non-positive pivot in column " +
+                                               std::to_string(first_fail) + " (" + std::to_string(nfail) +
+                                               " of " + std::to_string(nb) + " instances failed)");
+    if (result != KKT_OK)
+        set_err(c, result, result == KKT_ERR_STALL ? "refinement stalled" : "refinement hit max_refine");
+    return result;
+}
+}  // namespace
+
+extern "C" {
+
+kkt_status kkt_factor_solve(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
+                            const double* d_D, const double* delta_x, const double* d_rx, const double* d_ry,
+                            double* d_dx, double* d_dy, cudaStream_t st, kkt_info* info) {
+    return bounds_verdict(c, st, factor_solve_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, d_rx, d_ry, d_dx,
+                                                   d_dy, st, info));
+}
+
 kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_t st) {
     if (!c || !d_b || !d_x) return set_err(c, KKT_ERR_ARG, "NULL argument");
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve called without a factor");
@@ -2270,6 +2633,15 @@ void kkt_destroy(kkt_ctx* c) {
     if (c->tri_graph) cudaGraphDestroy(c->tri_graph);
     if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
     if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->step_graph) cudaGraphDestroy(c->step_graph);
+    for (cudaStream_t q : c->cap)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : c->step_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->h_rst) cudaFreeHost(c->h_rst);
+    if (c->h_reta) cudaFreeHost(c->h_reta);
+    if (c->hp_delta) cudaFreeHost(c->hp_delta);
     if (c->h_cg) cudaFreeHost(c->h_cg);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_side) cudaEventDestroy(c->ev_side);

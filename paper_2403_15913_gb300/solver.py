@@ -121,6 +121,19 @@ class KKTSolver:
             self._check(st)
         return st
 
+    def factor_solve(self, Wval, Jval, sigma, D, delta_x, rx, ry, dx, dy, stream=None):
+        """``factor`` then ``solve`` as one CUDA graph launch
+        (``kkt_factor_solve``); ``delta_x`` is one value per instance (a
+        float for a single system).  Returns the status (KKT_ERR_NOT_SPD
+        when some instance's pivot failed, else as ``solve``)."""
+        d = np.ascontiguousarray(np.atleast_1d(np.asarray(delta_x, dtype=np.float64)))
+        st = nat.lib().kkt_factor_solve(self._ctx, _dptr(Wval), _dptr(Jval), _dptr(sigma), _dptr(D),
+                                        nat.ptr_f64(d), _dptr(rx), _dptr(ry), _dptr(dx), _dptr(dy),
+                                        _stream(stream), ctypes.byref(self.info))
+        if st not in (nat.KKT_OK, nat.KKT_ERR_MAXIT, nat.KKT_ERR_STALL, nat.KKT_ERR_NOT_SPD):
+            self._check(st)
+        return st
+
     def backsolve(self, b, x, stream=None):
         """x = K^{-1} b with the current factor (condensed matrix only)."""
         self._check(nat.lib().kkt_backsolve(self._ctx, _dptr(b), _dptr(x), _stream(stream)))

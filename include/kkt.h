@@ -504,6 +504,55 @@ kkt_status kkt_ipm_device_bytes(const kkt_ipm* ipm, int64_t* bytes);
 kkt_status kkt_device_bytes(const kkt_ctx* ctx, int64_t* bytes);
 
 /* ------------------------------------------------------------------------
+ * Batched IPM: `count` column problems (one kkt_ipm each, "members") solved
+ * in lock-step with ONE KKT system per iteration.  Every member keeps its
+ * own iterate, barrier parameter, filter, inertia-correction ladder and line
+ * search (the steps of kkt_ipm_step); the Newton step of Sec. III for all
+ * members that still iterate is one factorisation and refined solve of the
+ * block-diagonal union of their KKT systems (kkt_analyse_batch; with kopt
+ * precision 0 one kkt_factor_solve graph launch, with precision 1 or 2 the
+ * reduced-precision factor with FP64 refinement and fallback).  Members
+ * that converged or failed keep their last block in the union (it still
+ * factorises) and take no further steps.
+ * ---------------------------------------------------------------------- */
+typedef struct kkt_ipm_batch kkt_ipm_batch;
+
+/* tray_params: count x 16 values (member i at tray_params + 16 i); kopt and
+ * iopt apply to every member (either may be NULL). */
+kkt_status kkt_ipm_batch_create(int count, const double* tray_params, const kkt_options* kopt,
+                                const kkt_ipm_options* iopt, kkt_ipm_batch** out);
+
+/* Member i (0 <= i < count), for kkt_ipm_init / kkt_ipm_init_shifted /
+ * kkt_ipm_init_warm / kkt_ipm_set_initial_state / kkt_ipm_get.  Calling
+ * kkt_ipm_step or kkt_ipm_solve on a member returns KKT_ERR_STATE. */
+kkt_ipm* kkt_ipm_batch_member(kkt_ipm_batch* batch, int i);
+
+/* Marks every member as iterating (each must have been initialised). */
+kkt_status kkt_ipm_batch_start(kkt_ipm_batch* batch);
+
+/* One lock-step iteration of every member still iterating; info (may be
+ * NULL) receives count reports, written for the members that took a step
+ * or stopped in this call.  Returns KKT_CONVERGED when no member iterates
+ * any more (per-member results: kkt_ipm_batch_solve's status array, or the
+ * reports), KKT_OK otherwise, another code on a batch-wide error. */
+kkt_status kkt_ipm_batch_step(kkt_ipm_batch* batch, cudaStream_t stream, kkt_ipm_info* info);
+
+/* kkt_ipm_batch_start, then steps until no member iterates: status[i]
+ * (KKT_CONVERGED, KKT_ERR_MAXIT after max_iter steps, KKT_ERR_STALL,
+ * KKT_ERR_NOT_SPD, ...) and iters[i] per member (either may be NULL), info
+ * as for kkt_ipm_batch_step (the last report of each member).  Returns
+ * KKT_CONVERGED when every member converged, else the first member's
+ * failure code. */
+kkt_status kkt_ipm_batch_solve(kkt_ipm_batch* batch, cudaStream_t stream, int* status, int* iters,
+                               kkt_ipm_info* info);
+
+/* The batch's KKT context (stats, profiling) and its last error message. */
+kkt_ctx* kkt_ipm_batch_kkt(kkt_ipm_batch* batch);
+const char* kkt_ipm_batch_last_error(const kkt_ipm_batch* batch);
+
+void kkt_ipm_batch_destroy(kkt_ipm_batch* batch);
+
+/* ------------------------------------------------------------------------
  * NMPC serving (no counterpart in the paper, whose use case it serves: a
  * controller re-solves its horizon-T problem from each new state, reusing
  * the symbolic factorisation, Sec. V-B).  A server holds clients (one

@@ -5,5 +5,5 @@ dynamic NLPs, with the Lifted-KKT and HyKKT hybrid solvers of Pacaud & Shin
 arguments."""
 from .solver import KKTBatchSolver, KKTSolver, KKTError, autotune_batch, default_options  # noqa: F401
 from .tray import TrayModel  # noqa: F401
-from .ipm import IPMSolver  # noqa: F401
+from .ipm import IPMBatch, IPMSolver  # noqa: F401
 from .serve import NMPCServer  # noqa: F401

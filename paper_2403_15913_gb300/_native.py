@@ -38,6 +38,8 @@ EXPORTED = [
     "kkt_ipm_get",
     "kkt_ipm_kkt", "kkt_ipm_destroy", "kkt_ipm_set_initial_state", "kkt_ipm_init_shifted", "kkt_ipm_init_warm",
     "kkt_ipm_device_bytes", "kkt_device_bytes",
+    "kkt_ipm_batch_create", "kkt_ipm_batch_member", "kkt_ipm_batch_start", "kkt_ipm_batch_step",
+    "kkt_ipm_batch_solve", "kkt_ipm_batch_kkt", "kkt_ipm_batch_last_error", "kkt_ipm_batch_destroy",
     "kkt_server_default_options", "kkt_server_create", "kkt_server_add_client", "kkt_server_submit",
     "kkt_server_wait", "kkt_server_drain", "kkt_server_get_stats", "kkt_server_destroy",
     "kkt_eval_fn", "kkt_debug_corrupt_map",
@@ -235,6 +237,23 @@ def load(path):
     L.kkt_ipm_init_warm.restype = ctypes.c_int
     L.kkt_ipm_device_bytes.argtypes = [P, I64P]
     L.kkt_ipm_device_bytes.restype = ctypes.c_int
+    L.kkt_ipm_batch_create.argtypes = [ctypes.c_int, F64P, ctypes.POINTER(Options), ctypes.POINTER(IPMOptions),
+                                       ctypes.POINTER(P)]
+    L.kkt_ipm_batch_create.restype = ctypes.c_int
+    L.kkt_ipm_batch_member.argtypes = [P, ctypes.c_int]
+    L.kkt_ipm_batch_member.restype = P
+    L.kkt_ipm_batch_start.argtypes = [P]
+    L.kkt_ipm_batch_start.restype = ctypes.c_int
+    L.kkt_ipm_batch_step.argtypes = [P, P, ctypes.POINTER(IPMInfo)]
+    L.kkt_ipm_batch_step.restype = ctypes.c_int
+    L.kkt_ipm_batch_solve.argtypes = [P, P, I32P, I32P, ctypes.POINTER(IPMInfo)]
+    L.kkt_ipm_batch_solve.restype = ctypes.c_int
+    L.kkt_ipm_batch_kkt.argtypes = [P]
+    L.kkt_ipm_batch_kkt.restype = P
+    L.kkt_ipm_batch_last_error.argtypes = [P]
+    L.kkt_ipm_batch_last_error.restype = ctypes.c_char_p
+    L.kkt_ipm_batch_destroy.argtypes = [P]
+    L.kkt_ipm_batch_destroy.restype = None
     L.kkt_device_bytes.argtypes = [P, I64P]
     L.kkt_device_bytes.restype = ctypes.c_int
     L.kkt_eval_fn.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]

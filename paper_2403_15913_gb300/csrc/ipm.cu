@@ -396,6 +396,11 @@ struct kkt_ipm {
     int launches = 0;   // kernels launched by the driver in the current step
     bool started = false;
     cudaEvent_t ev[4] = {};
+    // the iteration in progress: its report, the objective at its start,
+    // and whether the report is complete (a result to hand back)
+    kkt_ipm_info cur{};
+    double fval = 0.0;
+    bool report = false;
 };
 
 namespace {
@@ -489,8 +494,12 @@ void kkt_ipm_default_options(kkt_ipm_options* o) {
     o->tau_relax = 1e-8;
 }
 
-kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const kkt_ipm_options* iopt,
-                          kkt_ipm** out) {
+namespace {
+// own_kkt = false: a member of a kkt_ipm_batch -- no KKT context, and the
+// KKT inputs and outputs (Wv, Jv, sigma, rx, ry, D, dx, dy) are slices of
+// the batch's concatenated arrays, set by the batch.
+kkt_status create_impl(const double* params, const kkt_options* kopt, const kkt_ipm_options* iopt,
+                       bool own_kkt, kkt_ipm** out) {
     if (!params || !out) return KKT_ERR_ARG;
     *out = nullptr;
     kkt_ipm* p = new (std::nothrow) kkt_ipm();
@@ -517,10 +526,12 @@ kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const k
     const int n = p->n, m = p->m;
     std::vector<int> Wc(n + 1), Wr(p->nnzW), Jr(m + 1), Jc(p->nnzJ);
     kkt_tray_pattern(params, Wc.data(), Wr.data(), Jr.data(), Jc.data());
-    stt = kkt_analyse(n, m, Wc.data(), Wr.data(), Jr.data(), Jc.data(), &ko, &p->kkt);
-    if (stt != KKT_OK) {
-        delete p;
-        return stt;
+    if (own_kkt) {
+        stt = kkt_analyse(n, m, Wc.data(), Wr.data(), Jr.data(), Jc.data(), &ko, &p->kkt);
+        if (stt != KKT_OK) {
+            delete p;
+            return stt;
+        }
     }
     // CSC of J for J^T y
     std::vector<int> cp(n + 1, 0), ri(p->nnzJ), idx(p->nnzJ);
@@ -546,16 +557,23 @@ kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const k
         kkt_ipm_destroy(p);
         return s;
     };
-    double** vecs_n[] = {&p->x, &p->zl, &p->zu, &p->xlo, &p->xhi, &p->grad, &p->jty, &p->sigma,
-                         &p->rx, &p->dx, &p->dzl, &p->dzu, &p->xt};
+    double** vecs_n[] = {&p->x, &p->zl, &p->zu, &p->xlo, &p->xhi, &p->grad, &p->jty, &p->dzl, &p->dzu, &p->xt};
     for (double** v : vecs_n)
         if (dalloc(p, v, n) != KKT_OK) return fail(KKT_ERR_OOM);
-    double** vecs_m[] = {&p->s, &p->y, &p->vl, &p->vu, &p->c, &p->ry, &p->D, &p->dy, &p->ds,
-                         &p->dvl, &p->dvu, &p->st, &p->ct};
+    double** vecs_m[] = {&p->s, &p->y, &p->vl, &p->vu, &p->c, &p->ds, &p->dvl, &p->dvu, &p->st, &p->ct};
     for (double** v : vecs_m)
         if (dalloc(p, v, m) != KKT_OK) return fail(KKT_ERR_OOM);
-    if (dalloc(p, &p->Jv, p->nnzJ) != KKT_OK || dalloc(p, &p->Wv, p->nnzW) != KKT_OK ||
-        dalloc(p, &p->part, (size_t)kRB * kQ) != KKT_OK || dalloc(p, &p->red, kQ) != KKT_OK ||
+    if (own_kkt) {
+        double** kn[] = {&p->sigma, &p->rx, &p->dx};
+        for (double** v : kn)
+            if (dalloc(p, v, n) != KKT_OK) return fail(KKT_ERR_OOM);
+        double** km[] = {&p->ry, &p->D, &p->dy};
+        for (double** v : km)
+            if (dalloc(p, v, m) != KKT_OK) return fail(KKT_ERR_OOM);
+        if (dalloc(p, &p->Jv, p->nnzJ) != KKT_OK || dalloc(p, &p->Wv, p->nnzW) != KKT_OK)
+            return fail(KKT_ERR_OOM);
+    }
+    if (dalloc(p, &p->part, (size_t)kRB * kQ) != KKT_OK || dalloc(p, &p->red, kQ) != KKT_OK ||
         dalloc(p, &p->f, 1) != KKT_OK || dalloc(p, &p->count, 1) != KKT_OK ||
         dalloc(p, &p->jt_cp, n + 1) != KKT_OK || dalloc(p, &p->jt_ri, p->nnzJ) != KKT_OK ||
         dalloc(p, &p->jt_idx, p->nnzJ) != KKT_OK)
@@ -572,6 +590,12 @@ kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const k
         if (cudaEventCreate(&e) != cudaSuccess) return fail(KKT_ERR_CUDA);
     *out = p;
     return KKT_OK;
+}
+}  // namespace
+
+kkt_status kkt_ipm_create(const double* params, const kkt_options* kopt, const kkt_ipm_options* iopt,
+                          kkt_ipm** out) {
+    return create_impl(params, kopt, iopt, true, out);
 }
 
 kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
@@ -610,13 +634,16 @@ kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
     return KKT_OK;
 }
 
-kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
-    if (!p) return KKT_ERR_ARG;
-    if (!p->started) return ierr(p, KKT_ERR_STATE, "kkt_ipm_step before kkt_ipm_init");
+namespace {
+
+// Steps 1-3 of an iteration (KKT_CONVERGED when the optimality error is
+// <= tol); the iteration's report accumulates in p->cur.
+kkt_status step_begin(kkt_ipm* p, cudaStream_t st) {
     const int n = p->n, m = p->m;
     const int rel = p->opt.relaxed;
     const Bounds B = bounds_of(p);
-    kkt_ipm_info inf{};
+    kkt_ipm_info& inf = p->cur;
+    inf = kkt_ipm_info{};
     inf.iter = p->it;
     p->launches = 0;
     cudaEventRecord(p->ev[0], st);
@@ -642,7 +669,8 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     inf.err0 = e0;
     inf.mu = p->mu;
     if (e0 <= p->opt.tol) {
-        { inf.launches = p->launches; if (info) *info = inf; }
+        inf.launches = p->launches;
+        p->report = true;
         return KKT_CONVERGED;
     }
     while (p->mu > p->opt.tol / 10) {
@@ -652,11 +680,20 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     }
     const double mu = p->mu;
     inf.mu = mu;
+    p->fval = fval;
     // 3. right-hand side and diagonals
     prepare_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, p->x, p->s, p->y, p->zl,
                                                         p->zu, p->vl, p->vu, p->grad, p->jty, p->c,
                                                         p->sigma, p->rx, p->ry, p->D);
     p->launches += 1;
+    return KKT_OK;
+}
+
+// Step 4 with the context's own KKT system: factor with the inertia-
+// correction ladder, then the refined solve.
+kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
+    kkt_ipm_info& inf = p->cur;
+    const int rel = p->opt.relaxed;
     // 4. factor with inertia correction, solve
     kkt_info ki{};
     double delta = 0.0;
@@ -679,6 +716,16 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     inf.refine_iters = ki.refine_iters;
     inf.cg_iters = ki.cg_iters;
     inf.bwd_err = ki.bwd_err;
+    return KKT_OK;
+}
+
+// Steps 5-7: recovery, filter line search, update.
+kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
+    kkt_ipm_info& inf = p->cur;
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    const Bounds B = bounds_of(p);
+    const double mu = p->mu, fval = p->fval;
     cudaEventRecord(p->ev[2], st);
     // 5. recovery, fraction to boundary, directional derivative
     const double tau = std::max(kTauMin, 1.0 - mu);
@@ -728,7 +775,8 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     }
     inf.ls_trials = ls;
     if (!accepted) {
-        { inf.launches = p->launches; if (info) *info = inf; }
+        inf.launches = p->launches;
+        p->report = true;
         return ierr(p, KKT_ERR_STALL, "line search failed (no restoration phase)");
     }
     // 7. update
@@ -750,8 +798,23 @@ kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
     p->it++;
     inf.iter = p->it;
     ICUDA(p, cudaGetLastError());
-    { inf.launches = p->launches; if (info) *info = inf; }
+    inf.launches = p->launches;
+    p->report = true;
     return KKT_OK;
+}
+
+}  // namespace
+
+kkt_status kkt_ipm_step(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
+    if (!p) return KKT_ERR_ARG;
+    if (!p->started) return ierr(p, KKT_ERR_STATE, "kkt_ipm_step before kkt_ipm_init");
+    if (!p->kkt) return ierr(p, KKT_ERR_STATE, "a member of a kkt_ipm_batch steps with the batch");
+    p->report = false;
+    kkt_status r = step_begin(p, st);
+    if (r == KKT_OK) r = step_kkt(p, st);
+    if (r == KKT_OK) r = step_end(p, st);
+    if (info && p->report) *info = p->cur;
+    return r;
 }
 
 kkt_status kkt_ipm_solve(kkt_ipm* p, cudaStream_t st, kkt_ipm_info* info) {
@@ -859,8 +922,10 @@ kkt_status kkt_ipm_init_warm(kkt_ipm* p, double mu, int recenter, cudaStream_t s
 kkt_status kkt_ipm_device_bytes(const kkt_ipm* p, int64_t* bytes) {
     if (!p || !bytes) return KKT_ERR_ARG;
     int64_t kb = 0;
-    kkt_status s = kkt_device_bytes(p->kkt, &kb);
-    if (s != KKT_OK) return s;
+    if (p->kkt) {   // a batch member's KKT system belongs to the batch
+        kkt_status s = kkt_device_bytes(p->kkt, &kb);
+        if (s != KKT_OK) return s;
+    }
     *bytes = kb + p->dev_bytes;
     return KKT_OK;
 }
@@ -888,6 +953,271 @@ void kkt_ipm_destroy(kkt_ipm* p) {
     if (p->h_red) cudaFreeHost(p->h_red);
     if (p->kkt) kkt_destroy(p->kkt);
     delete p;
+}
+
+
+// ---------------------------------------------------------------- batches
+// Lock-step IPMs over many column problems with one KKT system: every
+// member keeps its own iterate, barrier parameter, filter and line search
+// (steps 1-3 and 5-7 above, unchanged), while step 4 factorises and solves
+// the block-diagonal union of the members' KKT systems in one call (the
+// batch context of kkt_analyse_batch; one graph launch in FP64, or the FP32
+// factor with FP64 refinement).  The members' KKT inputs and outputs are
+// slices of the batch's concatenated arrays, so nothing is copied.
+}  // extern "C"
+
+struct kkt_ipm_batch {
+    int count = 0;
+    std::vector<kkt_ipm*> mem;
+    kkt_ctx* kkt = nullptr;
+    std::vector<void*> allocs;
+    double *Wv = nullptr, *Jv = nullptr, *sigma = nullptr, *rx = nullptr, *ry = nullptr, *D = nullptr,
+           *dx = nullptr, *dy = nullptr;
+    std::vector<int> state;      // KKT_OK while a member iterates, else its final status
+    std::vector<char> stepping;  // members in the current iteration's KKT step
+    std::vector<double> delta;   // delta_x of every member's block in the last factor
+    std::vector<int> fcol;       // scratch: failing columns of the last factor
+    bool relaxed = false, graph = false;
+    long long kkt_steps = 0, factor_calls = 0;
+    std::string err;
+};
+
+namespace {
+kkt_status berr(kkt_ipm_batch* b, kkt_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    return st;
+}
+#define TRY_B(b, x)                   \
+    do {                              \
+        kkt_status s_ = (x);          \
+        if (s_ != KKT_OK) return s_;  \
+    } while (0)
+}  // namespace
+
+extern "C" {
+
+kkt_status kkt_ipm_batch_create(int count, const double* params, const kkt_options* kopt,
+                                const kkt_ipm_options* iopt, kkt_ipm_batch** out) {
+    if (count < 1 || !params || !out) return KKT_ERR_ARG;
+    *out = nullptr;
+    kkt_ipm_batch* b = new (std::nothrow) kkt_ipm_batch();
+    if (!b) return KKT_ERR_OOM;
+    auto fail = [&](kkt_status st) {
+        kkt_ipm_batch_destroy(b);
+        return st;
+    };
+    b->count = count;
+    b->mem.assign(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        kkt_status st = create_impl(params + 16 * (size_t)i, kopt, iopt, false, &b->mem[i]);
+        if (st != KKT_OK) return fail(st);
+    }
+    kkt_options ko;
+    if (kopt) ko = *kopt; else kkt_default_options(&ko);
+    b->relaxed = b->mem[0]->opt.relaxed != 0;
+    ko.target_relaxed = b->relaxed ? 1 : 0;
+    b->graph = ko.precision == 0 && ko.solver == 0;
+    std::vector<int> n(count), m(count);
+    std::vector<std::vector<int>> Wc(count), Wr(count), Jr(count), Jc(count);
+    std::vector<const int*> pWc(count), pWr(count), pJr(count), pJc(count);
+    long long N = 0, M = 0, NW = 0, NJ = 0;
+    for (int i = 0; i < count; ++i) {
+        kkt_ipm* p = b->mem[i];
+        n[i] = p->n;
+        m[i] = p->m;
+        Wc[i].resize(p->n + 1);
+        Wr[i].resize(std::max(1, p->nnzW));
+        Jr[i].resize(p->m + 1);
+        Jc[i].resize(std::max(1, p->nnzJ));
+        kkt_tray_pattern(p->params, Wc[i].data(), Wr[i].data(), Jr[i].data(), Jc[i].data());
+        pWc[i] = Wc[i].data();
+        pWr[i] = Wr[i].data();
+        pJr[i] = Jr[i].data();
+        pJc[i] = Jc[i].data();
+        N += p->n;
+        M += p->m;
+        NW += p->nnzW;
+        NJ += p->nnzJ;
+    }
+    kkt_status st = kkt_analyse_batch(count, n.data(), m.data(), pWc.data(), pWr.data(), pJr.data(), pJc.data(),
+                                      &ko, &b->kkt);
+    if (st != KKT_OK) return fail(st);
+    auto dal = [&](double** v, long long cnt) {
+        if (cudaMalloc((void**)v, std::max<long long>(1, cnt) * sizeof(double)) != cudaSuccess) return false;
+        b->allocs.push_back(*v);
+        return true;
+    };
+    if (!dal(&b->Wv, NW) || !dal(&b->Jv, NJ) || !dal(&b->sigma, N) || !dal(&b->rx, N) || !dal(&b->dx, N) ||
+        !dal(&b->ry, M) || !dal(&b->D, M) || !dal(&b->dy, M))
+        return fail(KKT_ERR_OOM);
+    // the union concatenates the members in order: variables, constraints,
+    // W and J values
+    long long xo = 0, yo = 0, wo = 0, jo = 0;
+    for (int i = 0; i < count; ++i) {
+        kkt_ipm* p = b->mem[i];
+        p->Wv = b->Wv + wo;
+        p->Jv = b->Jv + jo;
+        p->sigma = b->sigma + xo;
+        p->rx = b->rx + xo;
+        p->dx = b->dx + xo;
+        p->ry = b->ry + yo;
+        p->D = b->D + yo;
+        p->dy = b->dy + yo;
+        xo += p->n;
+        yo += p->m;
+        wo += p->nnzW;
+        jo += p->nnzJ;
+    }
+    std::vector<int> lx(count + 1), ly(count + 1);
+    st = kkt_batch_layout(b->kkt, nullptr, lx.data(), ly.data());
+    if (st != KKT_OK) return fail(st);
+    long long cx = 0, cy = 0;
+    for (int i = 0; i < count; ++i) {
+        if (lx[i] != cx || ly[i] != cy) return fail(berr(b, KKT_ERR_INTERNAL, "batch layout mismatch"));
+        cx += n[i];
+        cy += m[i];
+    }
+    b->state.assign(count, (int)KKT_ERR_STATE);
+    b->stepping.assign(count, 0);
+    b->delta.assign(count, 0.0);
+    b->fcol.assign(count, -1);
+    *out = b;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_batch_start(kkt_ipm_batch* b) {
+    if (!b) return KKT_ERR_ARG;
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->mem[i]->started) return berr(b, KKT_ERR_STATE, "member " + std::to_string(i) + " not initialised");
+        b->state[i] = KKT_OK;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* info) {
+    if (!b) return KKT_ERR_ARG;
+    const int cnt = b->count;
+    int running = 0;
+    // steps 1-3 of every member still iterating
+    for (int i = 0; i < cnt; ++i) {
+        b->stepping[i] = 0;
+        if (b->state[i] != KKT_OK) continue;
+        kkt_ipm* p = b->mem[i];
+        p->report = false;
+        const kkt_status r = step_begin(p, st);
+        if (r == KKT_OK) {
+            b->stepping[i] = 1;
+            ++running;
+        } else {
+            b->state[i] = r;
+        }
+        if (info && p->report) info[i] = p->cur;
+    }
+    if (running == 0) return KKT_CONVERGED;
+    // step 4 for all of them at once: the inertia-correction ladder per
+    // member (a member whose block fails raises its own delta_x), members
+    // that stopped keep their last block and delta_x
+    std::vector<double> d(cnt);
+    for (int i = 0; i < cnt; ++i) d[i] = b->stepping[i] ? 0.0 : b->delta[i];
+    kkt_info ki{};
+    while (true) {
+        kkt_status fs;
+        if (b->graph) {
+            fs = kkt_factor_solve(b->kkt, b->Wv, b->Jv, b->sigma, b->relaxed ? b->D : nullptr, d.data(), b->rx, b->ry,
+                                  b->dx, b->dy, st, &ki);
+        } else {
+            fs = kkt_factor_batch(b->kkt, b->Wv, b->Jv, b->sigma, b->relaxed ? b->D : nullptr, d.data(), st, &ki);
+        }
+        ++b->factor_calls;
+        if (fs != KKT_OK && fs != KKT_ERR_NOT_SPD && fs != KKT_ERR_MAXIT && fs != KKT_ERR_STALL)
+            return berr(b, fs, std::string("batch KKT step: ") + kkt_last_error(b->kkt));
+        kkt_status rs = kkt_batch_results(b->kkt, nullptr, nullptr, nullptr, nullptr, b->fcol.data());
+        if (rs != KKT_OK) return berr(b, rs, "kkt_batch_results");
+        bool again = false;
+        for (int i = 0; i < cnt; ++i) {
+            if (b->fcol[i] < 0 || !b->stepping[i]) continue;
+            kkt_ipm* p = b->mem[i];
+            if (d[i] == 0.0)
+                d[i] = p->delta_last == 0.0 ? kDeltaW0 : std::max(kDeltaMin, kKappaWMinus * p->delta_last);
+            else
+                d[i] *= p->delta_last == 0.0 ? kKappaWPlusBar : kKappaWPlus;
+            if (d[i] > kDeltaMax) {   // this member gives up; the others go on
+                b->stepping[i] = 0;
+                b->state[i] = KKT_ERR_NOT_SPD;
+                ierr(p, KKT_ERR_NOT_SPD, "inertia correction gave up");
+                --running;
+            } else {
+                again = true;
+            }
+        }
+        if (!again) break;
+    }
+    if (!b->graph && running > 0) {
+        const kkt_status ss = kkt_solve(b->kkt, b->rx, b->ry, b->dx, b->dy, nullptr, st, &ki);
+        if (ss != KKT_OK && ss != KKT_ERR_MAXIT && ss != KKT_ERR_STALL && ss != KKT_ERR_NOT_SPD)
+            return berr(b, ss, std::string("batch kkt_solve: ") + kkt_last_error(b->kkt));
+    }
+    ++b->kkt_steps;
+    std::vector<int> ref(cnt), cg(cnt);
+    std::vector<double> eta(cnt);
+    kkt_status rs = kkt_batch_results(b->kkt, nullptr, ref.data(), cg.data(), eta.data(), nullptr);
+    if (rs != KKT_OK) return berr(b, rs, "kkt_batch_results");
+    // steps 5-7 per member
+    for (int i = 0; i < cnt; ++i) {
+        if (!b->stepping[i]) continue;
+        kkt_ipm* p = b->mem[i];
+        b->delta[i] = d[i];
+        if (d[i] > 0) p->delta_last = d[i];
+        p->cur.delta_x = d[i];
+        p->cur.refine_iters = ref[i];
+        p->cur.cg_iters = cg[i];
+        p->cur.bwd_err = eta[i];
+        const kkt_status r = step_end(p, st);
+        if (r != KKT_OK) b->state[i] = r;
+        if (info && p->report) info[i] = p->cur;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_batch_solve(kkt_ipm_batch* b, cudaStream_t st, int* status, int* iters,
+                               kkt_ipm_info* info) {
+    if (!b) return KKT_ERR_ARG;
+    TRY_B(b, kkt_ipm_batch_start(b));
+    int max_iter = 0;
+    for (kkt_ipm* p : b->mem) max_iter = std::max(max_iter, p->opt.max_iter);
+    kkt_status r = KKT_OK;
+    for (int k = 0; k <= max_iter + 1; ++k) {
+        r = kkt_ipm_batch_step(b, st, info);
+        if (r != KKT_OK) break;
+        for (int i = 0; i < b->count; ++i)
+            if (b->state[i] == KKT_OK && b->mem[i]->it > b->mem[i]->opt.max_iter) b->state[i] = KKT_ERR_MAXIT;
+    }
+    if (r != KKT_OK && r != KKT_CONVERGED) return r;
+    kkt_status out = KKT_CONVERGED;
+    for (int i = 0; i < b->count; ++i) {
+        if (b->state[i] == KKT_OK) b->state[i] = KKT_ERR_MAXIT;
+        if (status) status[i] = b->state[i];
+        if (iters) iters[i] = b->mem[i]->it;
+        if (b->state[i] != KKT_CONVERGED && out == KKT_CONVERGED) out = (kkt_status)b->state[i];
+    }
+    return out;
+}
+
+kkt_ipm* kkt_ipm_batch_member(kkt_ipm_batch* b, int i) {
+    return b && i >= 0 && i < b->count ? b->mem[i] : nullptr;
+}
+
+kkt_ctx* kkt_ipm_batch_kkt(kkt_ipm_batch* b) { return b ? b->kkt : nullptr; }
+
+const char* kkt_ipm_batch_last_error(const kkt_ipm_batch* b) { return b ? b->err.c_str() : ""; }
+
+void kkt_ipm_batch_destroy(kkt_ipm_batch* b) {
+    if (!b) return;
+    for (kkt_ipm* p : b->mem)
+        if (p) kkt_ipm_destroy(p);
+    for (void* a : b->allocs) cudaFree(a);
+    if (b->kkt) kkt_destroy(b->kkt);
+    delete b;
 }
 
 }  // extern "C"

@@ -112,3 +112,87 @@ class IPMSolver:
             self.close()
         except Exception:
             pass
+
+
+class _Member(IPMSolver):
+    """A member of an IPMBatch: the IPMSolver calls that set up or read one
+    problem (init, init_shifted, init_warm, set_initial_state, get); it steps
+    only with its batch and does not own its handle."""
+
+    def __init__(self, handle, params):
+        self._h = handle
+        self._owned = False
+        self.params = params
+        L = nat.lib()
+        n, m = ctypes.c_int(), ctypes.c_int()
+        L.kkt_tray_sizes(nat.ptr_f64(self.params), ctypes.byref(n), ctypes.byref(m), None, None)
+        self.n, self.m = n.value, m.value
+        self.info = nat.IPMInfo()
+
+    def close(self):
+        self._h = None
+
+
+class IPMBatch:
+    """Lock-step IPMs over many column problems with one batched KKT factor
+    and solve per iteration (kkt_ipm_batch_*)."""
+
+    def __init__(self, params_list, scheme="lifted", tol=1e-8, max_iter=200, mu_init=0.1,
+                 relaxed=None, tau_relax=1e-8, **kkt_options):
+        self.params = np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.float64) for p in params_list]))
+        self.count = len(params_list)
+        L = nat.lib()
+        ko = default_options(scheme=scheme, **kkt_options)
+        io = nat.IPMOptions()
+        L.kkt_ipm_default_options(ctypes.byref(io))
+        io.tol, io.max_iter, io.mu_init, io.tau_relax = tol, max_iter, mu_init, tau_relax
+        io.relaxed = -1 if relaxed is None else int(bool(relaxed))
+        h = ctypes.c_void_p()
+        st = L.kkt_ipm_batch_create(self.count, nat.ptr_f64(self.params), ctypes.byref(ko),
+                                    ctypes.byref(io), ctypes.byref(h))
+        if st != nat.KKT_OK:
+            raise KKTError(st, "kkt_ipm_batch_create failed")
+        self._h = h
+        self.members = [_Member(L.kkt_ipm_batch_member(h, i), self.params[i]) for i in range(self.count)]
+        self.infos = (nat.IPMInfo * self.count)()
+
+    def init(self, stream=None):
+        for mem in self.members:
+            mem.init(stream=stream)
+
+    def step(self, stream=None):
+        """One lock-step iteration: 0 while some member iterates, 1 when none
+        does, negative on a batch-wide error."""
+        return nat.lib().kkt_ipm_batch_step(self._h, _stream(stream), self.infos)
+
+    def solve(self, stream=None):
+        """Iterate until no member iterates; returns (statuses, iterations)
+        per member (1 = converged)."""
+        status = np.zeros(self.count, np.int32)
+        iters = np.zeros(self.count, np.int32)
+        st = nat.lib().kkt_ipm_batch_solve(self._h, _stream(stream), nat.ptr_i32(status), nat.ptr_i32(iters),
+                                           self.infos)
+        if st not in (nat.KKT_CONVERGED, nat.KKT_ERR_MAXIT, nat.KKT_ERR_STALL, nat.KKT_ERR_NOT_SPD):
+            raise KKTError(st, nat.lib().kkt_ipm_batch_last_error(self._h).decode())
+        return status, iters
+
+    def info(self, i):
+        return self.infos[i].as_dict()
+
+    def kkt_stats(self):
+        out = nat.Stats()
+        nat.lib().kkt_get_stats(nat.lib().kkt_ipm_batch_kkt(self._h), ctypes.byref(out))
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for mem in self.members:
+                mem.close()
+            nat.lib().kkt_ipm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,8 +54,10 @@ typedef enum {
     KKT_ERR_NOT_SPD = -4,   /* non-positive pivot: kkt_info.failed_col is set */
     KKT_ERR_MAXIT = -5,     /* CG or refinement hit its iteration limit       */
     KKT_ERR_STALL = -6,     /* refinement stopped improving (eta stagnated)   */
-    KKT_ERR_TIMEOUT = -7,   /* reserved: no call of this library waits on the
-                               device with a time limit, so none returns it  */
+    KKT_ERR_TIMEOUT = -7,   /* a dependency wait of the dataflow triangular
+                               solves (staged_solve 2, 3) gave up after one
+                               second: the solution is invalid; the solve
+                               state is reset, so the next call starts clean */
     KKT_ERR_STATE = -8,     /* call out of order (e.g. solve before factor)   */
     KKT_ERR_INTERNAL = -9   /* a consistency check of the analysis' index
                                maps failed on the host (a library bug)       */
@@ -115,7 +117,16 @@ typedef struct {
                             memory and start while the previous level runs
                             (programmatic dependent launch); 0: the plain
                             level kernels.  Levels whose panels do not fit
-                            96 KB use the plain kernels either way          */
+                            96 KB use the plain kernels either way.
+                            2: dataflow triangular solves, one launch per
+                            direction: CTAs take the subtree tasks and level
+                            supernodes by ticket in a topological order of
+                            the tree and wait (bounded) on per-item arrival
+                            counters in L2 instead of one launch per level;
+                            3: the same for the level supernodes only, the
+                            subtree tasks in their own launches.  2 and 3
+                            are used when the widest staged panel fits
+                            100 KB, else 1 is                                */
 } kkt_options;
 
 /* Per-call report.  Fields not touched by a call keep their values. */
@@ -334,8 +345,11 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* ctx, const double* d_b, double* d_x,
  * out-of-bounds access; not a step of the paper's method).  what = 1
  * overwrites one entry of the Schur-update relative-row map with a row one
  * past its target supernode's rows -- a wrong index that still lies inside
- * the factor storage -- so that a test can exercise the checks; what = 0
- * restores it.  KKT_ERR_STATE in other builds. */
+ * the factor storage -- so that a test can exercise the checks; what = 2
+ * raises by one the arrival count the last item of the dataflow solves
+ * waits for, so that its bounded wait runs out (the solve then returns
+ * KKT_ERR_TIMEOUT); what = 0 restores both.  KKT_ERR_STATE in other
+ * builds. */
 kkt_status kkt_debug_corrupt_map(kkt_ctx* ctx, int what);
 
 /* Diagnostic: copy the numeric factor L (permuted order) as CSC with the

@@ -830,6 +830,26 @@ __device__ __forceinline__ void stage_panel(const T* __restrict__ A, int c, int 
     }
 }
 
+// Forward substitution of supernode s once its panel is staged in S (leading
+// dimension ld) and every contribution to x[f, f + c) has arrived: the warp
+// substitution, then Lhat21 u scattered into the rows below.
+template <typename T>
+__device__ __forceinline__ void forward_staged_supernode(const Plan& P, int s, const T* S, int ld,
+                                                         T* __restrict__ x, T* z, T (*part)[32]) {
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        const int lane = tid;
+        T z0 = lane < c ? __ldcg(x + f + lane) : T(0.0);
+        T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : T(0.0);
+        warp_lower_solve(S, ld, c, lane, z0, z1);   // unit lower triangular (normalised factor)
+        if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
+        if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
+    }
+    __syncthreads();
+    scatter_below(S, c, r, ld, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
+}
+
 // Forward substitution of one level with the panel staged in shared memory
 // before the wait on the previous level; after the wait it costs the warp
 // substitution and Lhat21 u.  Same arithmetic as forward_level_kernel.
@@ -844,65 +864,49 @@ forward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __r
     __shared__ T part[kThreads / 32][32];
     const int s = lvl_sn[blockIdx.x];
     const bool ok = kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode);
-    const int f = ok ? P.sn_f[s] : 0, c = ok ? P.sn_c[s] : 0, r = ok ? P.sn_r[s] : 0;
+    const int c = ok ? P.sn_c[s] : 0, r = ok ? P.sn_r[s] : 0;
     const int ld = staged_ld(r);
     if (ok) stage_panel(Lx + P.sn_lptr[s], c, r, ld, S);
     grid_dependency_wait();
     KKT_RETURN_IF_INACTIVE(active);
     if (!ok) return;
     __syncthreads();
-    const int tid = threadIdx.x;
-    if (tid < 32) {
-        const int lane = tid;
-        T z0 = lane < c ? __ldcg(x + f + lane) : T(0.0);
-        T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : T(0.0);
-        warp_lower_solve(S, ld, c, lane, z0, z1);   // unit lower triangular (normalised factor)
-        if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
-        if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
-    }
-    __syncthreads();
-    scatter_below(S, c, r, ld, z, P.rows + P.sn_rptr[s], x, part, P.berr, P.n);
+    forward_staged_supernode(P, s, S, ld, x, z, part);
 }
 
-// Backward substitution of one level, staged like the forward kernel (the
-// panel, the row indices below and the reciprocal pivots before the wait).
-// Shared memory: panel (arc elements), then x of the rows below (mrb), then
-// their indices (mrb ints).  Supernodes of <= 32 columns sum L21^T w with a
-// warp instruction over 32 / cp rows (lane = row group, column k < cp).
+// Backward substitution of supernode s, the part that does not depend on x:
+// the panel staged in S (leading dimension ld), the row indices below in rix
+// (-1 where a bounds check failed) and the first warp's reciprocal pivots.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-backward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
-                             const T* __restrict__ dinv, T* __restrict__ x, int arc, int mrb,
-                             const int* __restrict__ active) {
-    pdl_launch_dependents();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);
-    T* xb = S + arc;
-    int* rix = reinterpret_cast<int*>(xb + mrb);
-    __shared__ T part[kThreads / 32][64];
-    const int s = lvl_sn[blockIdx.x];
-    const bool ok = kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode);
-    const int f = ok ? P.sn_f[s] : 0, c = ok ? P.sn_c[s] : 0, r = ok ? P.sn_r[s] : 0;
-    const int ld = staged_ld(r), rb = r - c;
+__device__ __forceinline__ void backward_stage_supernode(const Plan& P, int s, const T* __restrict__ Lx,
+                                                         const T* __restrict__ dinv, T* S, int ld, int* rix,
+                                                         T& di0, T& di1) {
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    stage_panel(Lx + P.sn_lptr[s], c, r, ld, S);
+    const int* rows = P.rows + P.sn_rptr[s] + c;
+    for (int i = tid; i < rb; i += nt) {
+        const int rw = rows[i];
+        rix[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? rw : -1;
+    }
+    if (tid < 32) {
+        di0 = lane < c ? dinv[f + lane] : T(0.0);
+        di1 = lane + 32 < c ? dinv[f + lane + 32] : T(0.0);
+    }
+}
+
+// Backward substitution of a staged supernode once x of its rows below is
+// final (the caller has synchronised the CTA after staging): xb gathers
+// those values, t = u / l^2 - L21^T w, then the warp substitution with the
+// diagonal block.  Supernodes of <= 32 columns sum L21^T w with a warp
+// instruction over 32 / cp rows (lane = row group, column k < cp).
+template <typename T>
+__device__ __forceinline__ void backward_staged_supernode(const Plan& P, int s, const T* S, int ld, T* xb,
+                                                          const int* rix, T di0, T di1, T* __restrict__ x,
+                                                          T (*part)[64]) {
+    const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    T di0 = 0.0, di1 = 0.0;
-    if (ok) {
-        stage_panel(Lx + P.sn_lptr[s], c, r, ld, S);
-        const int* rows = P.rows + P.sn_rptr[s] + c;
-        for (int i = tid; i < rb; i += nt) {
-            const int rw = rows[i];
-            rix[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? rw : -1;
-        }
-        if (tid < 32) {
-            di0 = lane < c ? dinv[f + lane] : T(0.0);
-            di1 = lane + 32 < c ? dinv[f + lane + 32] : T(0.0);
-        }
-    }
-    grid_dependency_wait();
-    KKT_RETURN_IF_INACTIVE(active);
-    if (!ok) return;
-    __syncthreads();
     for (int i = tid; i < rb; i += nt) xb[i] = rix[i] >= 0 ? __ldcg(x + rix[i]) : T(0.0);
     __syncthreads();
     if (c <= 32) {
@@ -943,6 +947,34 @@ backward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __
     }
 }
 
+// Backward substitution of one level, staged like the forward kernel (the
+// panel, the row indices below and the reciprocal pivots before the wait).
+// Shared memory: panel (arc elements), then x of the rows below (mrb), then
+// their indices (mrb ints).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+backward_level_staged_kernel(Plan P, const int* __restrict__ lvl_sn, const T* __restrict__ Lx,
+                             const T* __restrict__ dinv, T* __restrict__ x, int arc, int mrb,
+                             const int* __restrict__ active) {
+    pdl_launch_dependents();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    T* xb = S + arc;
+    int* rix = reinterpret_cast<int*>(xb + mrb);
+    __shared__ T part[kThreads / 32][64];
+    const int s = lvl_sn[blockIdx.x];
+    const bool ok = kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode);
+    const int r = ok ? P.sn_r[s] : 0;
+    const int ld = staged_ld(r);
+    T di0 = 0.0, di1 = 0.0;
+    if (ok) backward_stage_supernode(P, s, Lx, dinv, S, ld, rix, di0, di1);
+    grid_dependency_wait();
+    KKT_RETURN_IF_INACTIVE(active);
+    if (!ok) return;
+    __syncthreads();
+    backward_staged_supernode(P, s, S, ld, xb, rix, di0, di1, x, part);
+}
+
 // ------------------------------------------------------------- subtrees
 // Small subtrees of the supernodal tree (task = its supernodes in
 // postorder) are processed by one CTA each, without per-level launches.
@@ -971,20 +1003,14 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
     }
 }
 
-// Forward substitution over a subtree task (supernodes in postorder).
+// Forward substitution over the supernodes task_sn[q0 .. q1) of one subtree
+// task, in postorder (D: shared memory for the c x c diagonal block).
 template <typename T>
-__global__ void __launch_bounds__(kSubtreeThreads)
-forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                       const T* __restrict__ Lx, const T* __restrict__ dinv,
-                       T* __restrict__ x,
-    const int* __restrict__ active) {
-    pdl_launch_dependents();   // the first staged level may stage its panels during the last wave
-    KKT_RETURN_IF_INACTIVE(active);
-    __shared__ T z[64];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* D = reinterpret_cast<T*>(smem_raw);   // diagonal block of the current supernode
+__device__ __forceinline__ void forward_subtree_task(const Plan& P, const int* __restrict__ task_sn, int q0,
+                                                     int q1, const T* __restrict__ Lx, T* __restrict__ x, T* D,
+                                                     T* z) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
+    for (int q = q0; q < q1; ++q) {
         const int s = task_sn[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
@@ -1012,20 +1038,32 @@ forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __re
     }
 }
 
-// Backward substitution over a subtree task (supernodes in reverse postorder).
+// Forward substitution over a subtree task (supernodes in postorder).
 template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
-backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
-                        const T* __restrict__ Lx, const T* __restrict__ dinv,
-                        T* __restrict__ x,
+forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                       const T* __restrict__ Lx, const T* __restrict__ dinv,
+                       T* __restrict__ x,
     const int* __restrict__ active) {
+    pdl_launch_dependents();   // the first staged level may stage its panels during the last wave
     KKT_RETURN_IF_INACTIVE(active);
-    __shared__ T part[kSubtreeThreads / 32][64];
+    __shared__ T z[64];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* dyn = reinterpret_cast<T*>(smem_raw);   // [diagonal block | x of the rows below]
+    T* D = reinterpret_cast<T*>(smem_raw);   // diagonal block of the current supernode
+    forward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, x, D, z);
+}
+
+// Backward substitution over the supernodes task_sn[q0 .. q1) of one subtree
+// task, in reverse postorder (dyn: shared memory for the diagonal block and
+// x of the rows below; part: one row of 64 per warp).
+template <typename T>
+__device__ __forceinline__ void backward_subtree_task(const Plan& P, const int* __restrict__ task_sn, int q0,
+                                                      int q1, const T* __restrict__ Lx,
+                                                      const T* __restrict__ dinv, T* __restrict__ x, T* dyn,
+                                                      T (*part)[64]) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    for (int q = task_ptr[blockIdx.x + 1] - 1; q >= task_ptr[blockIdx.x]; --q) {
+    for (int q = q1 - 1; q >= q0; --q) {
         const int s = task_sn[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
@@ -1092,6 +1130,187 @@ backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __r
         __threadfence();
         __syncthreads();
     }
+}
+
+// Backward substitution over a subtree task (supernodes in reverse postorder).
+template <typename T>
+__global__ void __launch_bounds__(kSubtreeThreads)
+backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                        const T* __restrict__ Lx, const T* __restrict__ dinv,
+                        T* __restrict__ x,
+    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
+    __shared__ T part[kSubtreeThreads / 32][64];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* dyn = reinterpret_cast<T*>(smem_raw);   // [diagonal block | x of the rows below]
+    backward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, dinv, x, dyn, part);
+}
+
+// ------------------------------------------------------------- dataflow solves
+// One launch per direction for the whole triangular solve.  The work items
+// are the subtree tasks and the supernodes of the levels, listed in a
+// topological order of the tree (tasks, then the levels bottom-up).  CTAs
+// take items by ticket (an atomic counter): a CTA with ticket i only waits
+// for items with smaller tickets, which CTAs already running hold, so every
+// wait ends however many CTAs are resident.  A level supernode stages its
+// panel before it waits, so the wait overlaps the loads; it then waits on
+// one word in L2:
+//   forward:  cnt[i] counts the items below it whose contributions to x are
+//             in (their atomics fenced before the count), until nchild[i];
+//             the waiter re-arms it to zero for the next solve;
+//   backward: done[up] holds the epoch of the solve in which its parent
+//             finished (x of the parent's columns final); the epoch is the
+//             solve count, advanced by the last CTA to leave.
+// The waits are bounded (one second by the global timer, and at most
+// kFlowSpinLimit polls with backoff): a wait that gives up records 1 in the
+// mapped host word herr and goes on, so the kernel always completes and the
+// host reports the failure (its x is then invalid).
+struct Flow {
+    const int* item;     // forward order: >= 0 supernode of the levels, < 0 subtree task -(b + 1)
+    const int* up;       // index of the item the item's forward result feeds (its parent), -1: none
+    const int* nchild;   // forward: items feeding each item
+    int* cnt;            // forward arrival counters (zero between solves)
+    unsigned* done;      // backward: epoch at which each level supernode finished
+    unsigned* ctrl;      // [0] next ticket, [1] CTAs that left, [2] epoch of the last backward solve
+    int* herr;           // mapped host word: a wait gave up
+    int first, nitems;   // the items [first, nitems) take part (first > 0: the subtree tasks run
+                         // in their own launches, before the forward and after the backward)
+};
+constexpr int kFlowThreads = 128;
+constexpr int kFlowSpinLimit = 1 << 24;
+constexpr unsigned long long kFlowWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const void* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One thread waits until *p == want (bounded, see above).
+__device__ __forceinline__ void flow_wait(const void* p, unsigned want, int* herr) {
+    const unsigned long long t0 = global_ns();
+    for (int it = 0;; ++it) {
+        if (ld_acquire_gpu(p) == want) break;
+        if (it >= kFlowSpinLimit || global_ns() - t0 > kFlowWaitNs) {
+            *(volatile int*)herr = 1;
+            break;
+        }
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    __threadfence();
+}
+
+// Ticket of the calling CTA's next item (all threads receive it).
+__device__ __forceinline__ int flow_ticket(const Flow& F, int* s_ticket) {
+    if (threadIdx.x == 0) *s_ticket = (int)atomicAdd(F.ctrl, 1u);
+    __syncthreads();
+    return *s_ticket;
+}
+
+// The last CTA to leave resets the ticket counters (and publishes the epoch).
+__device__ __forceinline__ void flow_leave(const Flow& F, bool backward, unsigned epoch) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(F.ctrl + 1, 1u) == gridDim.x - 1) {
+            F.ctrl[0] = 0;
+            F.ctrl[1] = 0;
+            if (backward) F.ctrl[2] = epoch;
+        }
+    }
+}
+
+// L z = b on the permuted vector x.  Dynamic shared memory: the widest staged
+// panel (staged_ld(r) x c) or subtree diagonal block.
+template <typename T>
+__global__ void __launch_bounds__(kFlowThreads)
+forward_flow_kernel(Plan P, Flow F, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                    const T* __restrict__ Lx, T* __restrict__ x, const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T z[64];
+    __shared__ T part[kFlowThreads / 32][32];
+    __shared__ int s_ticket;
+    const int tid = threadIdx.x;
+    while (true) {
+        const int i = F.first + flow_ticket(F, &s_ticket);
+        if (i >= F.nitems) break;
+        const int it = F.item[i];
+        if (it < 0) {
+            const int b = -it - 1;
+            forward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, x, S, z);
+        } else if (kkt_in(P.berr, it < P.ns, kBcSupernode)) {
+            const int c = P.sn_c[it], r = P.sn_r[it], ld = staged_ld(r);
+            stage_panel(Lx + P.sn_lptr[it], c, r, ld, S);
+            if (tid == 0 && F.nchild[i] > 0) {
+                flow_wait(F.cnt + i, (unsigned)F.nchild[i], F.herr);
+                F.cnt[i] = 0;
+            }
+            __syncthreads();
+            forward_staged_supernode(P, it, S, ld, x, z, part);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && F.up[i] >= 0) {
+            __threadfence();
+            atomicAdd(F.cnt + F.up[i], 1);
+        }
+    }
+    flow_leave(F, false, 0u);
+}
+
+// L^T w = z in place, items in the reverse order.  Dynamic shared memory:
+// the widest staged panel with x and the indices of its rows below, or the
+// widest subtree diagonal block with its rows below.
+template <typename T>
+__global__ void __launch_bounds__(kFlowThreads)
+backward_flow_kernel(Plan P, Flow F, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
+                     const T* __restrict__ Lx, const T* __restrict__ dinv, T* __restrict__ x,
+                     const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T part[kFlowThreads / 32][64];
+    __shared__ int s_ticket;
+    const int tid = threadIdx.x;
+    const unsigned epoch = *(volatile unsigned*)(F.ctrl + 2) + 1u;
+    while (true) {
+        const int i = F.nitems - 1 - flow_ticket(F, &s_ticket);
+        if (i < F.first) break;
+        const int it = F.item[i], up = F.up[i];
+        if (it < 0) {
+            const int b = -it - 1;
+            if (tid == 0 && up >= 0) flow_wait(F.done + up, epoch, F.herr);
+            __syncthreads();
+            backward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, dinv, x, S, part);
+        } else if (kkt_in(P.berr, it < P.ns, kBcSupernode)) {
+            const int c = P.sn_c[it], r = P.sn_r[it], ld = staged_ld(r);
+            T* xb = S + (size_t)ld * c;
+            int* rix = reinterpret_cast<int*>(xb + (r - c));
+            T di0 = 0.0, di1 = 0.0;
+            backward_stage_supernode(P, it, Lx, dinv, S, ld, rix, di0, di1);
+            if (tid == 0 && up >= 0) flow_wait(F.done + up, epoch, F.herr);
+            __syncthreads();
+            backward_staged_supernode(P, it, S, ld, xb, rix, di0, di1, x, part);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release_gpu(F.done + i, epoch);
+            }
+        }
+        __syncthreads();
+    }
+    flow_leave(F, true, epoch);
 }
 
 template <typename Tin, typename Tout>

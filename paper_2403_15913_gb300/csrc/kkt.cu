@@ -38,6 +38,7 @@ namespace {
 constexpr long long kSmemCapElems = (200 * 1024) / 8;   // panel kept in smem up to 200 KB
 constexpr int kBackwardSmemBytes = 192 * 1024;   // backward level solve: diagonal block + staged x
 constexpr size_t kStagedSmemBytes = 96 * 1024;   // staged level solves: panel (+ x and indices below)
+constexpr size_t kFlowSmemBytes = 100 * 1024;    // dataflow solves: widest staged panel (+ x and indices below)
 constexpr int kSyrkStageBytes = 96 * 1024;       // split-level SYRK: L21 staged in shared memory
 constexpr int kClusterLevelMax = 32;             // split levels this small run as one cluster launch
 constexpr int kClusterSmemBytes = 96 * 1024;     // its diagonal block / staged L21
@@ -88,6 +89,20 @@ struct kkt_ctx {
     int n_norm_fused = 0;
     int* d_norm_list_fused = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
+    // dataflow triangular solves (staged_solve = 2): work items in
+    // topological order, the item each one feeds and its number of feeders,
+    // arrival counters, epochs and tickets; the mapped host word a wait that
+    // gave up sets; shared memory bounds and launch grids per precision
+    // (0 double, 1 float, 2 double-float) and direction (0 forward)
+    bool flow = false;
+    int flow_items = 0;
+    int *d_flow_item = nullptr, *d_flow_up = nullptr, *d_flow_nchild = nullptr, *d_flow_cnt = nullptr;
+    int* d_flow_nchild_lv = nullptr;   // feeders among the level supernodes only (staged_solve = 3)
+    unsigned *d_flow_done = nullptr, *d_flow_ctrl = nullptr;
+    int* h_flow_err = nullptr;   // pinned, mapped
+    int* d_flow_err = nullptr;   // its device address
+    long long flow_fwd_elems = 0, flow_bwd_elems = 0, flow_bwd_ints = 0;
+    int flow_grid[3][2] = {};
     // device allocations (all freed in kkt_destroy) and their total size
     std::vector<void*> allocs;
     long long dev_bytes = 0;
@@ -133,6 +148,7 @@ struct kkt_ctx {
     long long dbg_relmap_pos = -1;
     int dbg_relmap_bad = 0, dbg_relmap_old = 0;
     bool dbg_corrupted = false;
+    bool dbg_flow_raised = false;
     // CUDA graphs captured once after the analysis: the triangular solves on
     // w_xp, and one HyKKT CG iteration on the internal CG vectors
     cudaGraph_t tri_graph = nullptr, cg_graph = nullptr, tri_graph32 = nullptr, cg_graph32 = nullptr;
@@ -809,6 +825,54 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     TRY(upload(c, &c->d_task_ptr, task_ptr));
 
     TRY(upload(c, &c->d_task_sn, task_sn));
+    // ---- dataflow solves: the subtree tasks, then the supernodes of the
+    // levels bottom-up (a topological order of the tree: every item comes
+    // after the items that feed it); each item feeds the item holding the
+    // parent of its (root) supernode
+    {
+        const int nitems = c->ntasks + (int)c->h_lvl_sn.size();
+        std::vector<int> item(nitems), up(nitems, -1), nchild(nitems, 0), item_of(ns, -1);
+        for (int b = 0; b < c->ntasks; ++b) item[b] = -(b + 1);
+        for (size_t q = 0; q < c->h_lvl_sn.size(); ++q) {
+            item[c->ntasks + q] = c->h_lvl_sn[q];
+            item_of[c->h_lvl_sn[q]] = c->ntasks + (int)q;
+        }
+        std::vector<int> nchild_lv(nitems, 0);
+        for (int i = 0; i < nitems; ++i) {
+            const int s = item[i] >= 0 ? item[i] : task_root[-item[i] - 1];
+            const int p = S.sn_parent[s];
+            if (p < 0) continue;
+            up[i] = item_of[p];
+            if (up[i] <= i) return set_err(c, KKT_ERR_INTERNAL, "dataflow solve order is not topological");
+            nchild[up[i]]++;
+            if (item[i] >= 0) nchild_lv[up[i]]++;
+        }
+        c->flow_fwd_elems = c->task_max_cc;
+        c->flow_bwd_elems = c->task_max_ccrb;
+        c->flow_bwd_ints = 0;
+        for (int s : c->h_lvl_sn) {
+            const long long ldc = (long long)staged_ld(sn_r[s]) * sn_c[s], rb = sn_r[s] - sn_c[s];
+            c->flow_fwd_elems = std::max(c->flow_fwd_elems, ldc);
+            c->flow_bwd_elems = std::max(c->flow_bwd_elems, ldc + rb);
+            c->flow_bwd_ints = std::max(c->flow_bwd_ints, rb);
+        }
+        c->flow_items = nitems;
+        if (nitems > 0) {
+            TRY(upload(c, &c->d_flow_item, item));
+            TRY(upload(c, &c->d_flow_up, up));
+            TRY(upload(c, &c->d_flow_nchild, nchild));
+            TRY(upload(c, &c->d_flow_nchild_lv, nchild_lv));
+            TRY(alloc(c, &c->d_flow_cnt, nitems));
+            TRY(alloc(c, &c->d_flow_done, nitems));
+            TRY(alloc(c, &c->d_flow_ctrl, 4));
+            CUDA_TRY(c, cudaMemset(c->d_flow_cnt, 0, (size_t)nitems * sizeof(int)));
+            CUDA_TRY(c, cudaMemset(c->d_flow_done, 0, (size_t)nitems * sizeof(unsigned)));
+            CUDA_TRY(c, cudaMemset(c->d_flow_ctrl, 0, 4 * sizeof(unsigned)));
+            CUDA_TRY(c, cudaHostAlloc((void**)&c->h_flow_err, sizeof(int), cudaHostAllocMapped));
+            *c->h_flow_err = 0;
+            CUDA_TRY(c, cudaHostGetDevicePointer((void**)&c->d_flow_err, c->h_flow_err, 0));
+        }
+    }
     TRY(upload(c, &c->d_syrk_tasks, syrk_tasks));
     TRY(alloc(c, &c->d_dinv, n));
     TRY(upload(c, &c->d_perm, S.perm));
@@ -918,12 +982,92 @@ size_t staged_backward_bytes(const kkt_ctx* c, int l) {
     return (staged_panel_elems(c, l) + c->lvl_max_rb[l]) * sizeof(T) + (size_t)c->lvl_max_rb[l] * sizeof(int);
 }
 
+template <typename T>
+constexpr int flow_prec() {
+    return std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2;
+}
+template <typename T>
+size_t flow_fwd_bytes(const kkt_ctx* c) {
+    return (size_t)c->flow_fwd_elems * sizeof(T);
+}
+template <typename T>
+size_t flow_bwd_bytes(const kkt_ctx* c) {
+    return (size_t)c->flow_bwd_elems * sizeof(T) + (size_t)c->flow_bwd_ints * sizeof(int);
+}
+// staged_solve = 3: the subtree tasks keep their own launches, the dataflow
+// kernels take the level supernodes only
+bool flow_levels_only(const kkt_ctx* c) { return c->opt.staged_solve == 3 && c->ntasks > 0; }
+Flow flow_of(const kkt_ctx* c) {
+    const bool lv = flow_levels_only(c);
+    return Flow{c->d_flow_item, c->d_flow_up, lv ? c->d_flow_nchild_lv : c->d_flow_nchild, c->d_flow_cnt,
+                c->d_flow_done, c->d_flow_ctrl, c->d_flow_err, lv ? c->ntasks : 0, c->flow_items};
+}
+
+// Dataflow solves are used with staged_solve = 2 (3: levels only) when the
+// widest staged panel fits kFlowSmemBytes; the launch grid is what stays
+// resident on the device
+// (a CTA waits only for items that running CTAs hold, so fewer resident
+// CTAs make it slower, never stuck).
+template <typename T>
+bool flow_grids(kkt_ctx* c, int sms) {
+    const int p = flow_prec<T>();
+    const size_t fb = flow_fwd_bytes<T>(c), bb = flow_bwd_bytes<T>(c);
+    // the attribute is per kernel, not per context: every context sets the
+    // same bound, so contexts of other sizes (e.g. the clients of a server,
+    // created on several threads) never lower it below what one needs
+    if (cudaFuncSetAttribute(forward_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFlowSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(backward_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFlowSmemBytes) != cudaSuccess)
+        return false;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, forward_flow_kernel<T>, kFlowThreads, fb) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, backward_flow_kernel<T>, kFlowThreads, bb) != cudaSuccess ||
+        a < 1 || b < 1)
+        return false;
+    c->flow_grid[p][0] = std::max(1, std::min(c->flow_items, a * sms));
+    c->flow_grid[p][1] = std::max(1, std::min(c->flow_items, b * sms));
+    return true;
+}
+
+void setup_flow(kkt_ctx* c) {
+    c->flow = false;
+    if (c->opt.staged_solve < 2 || c->opt.solver != 0 || c->flow_items == 0 || !c->h_flow_err) return;
+    if (flow_bwd_bytes<double>(c) > kFlowSmemBytes) return;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return;
+    }
+    c->flow = flow_grids<double>(c, sms) && flow_grids<float>(c, sms) && flow_grids<df64>(c, sms);
+    cudaGetLastError();
+}
+
 // L z = xp, L^T w = z in place on the permuted vector xp: subtree tasks and
 // levels bottom-up, then levels top-down and subtree tasks (panels Lx and
 // reciprocal pivots dinv of the precision T).
 template <typename T>
 void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStream_t st,
                                const int* active) {
+    if (c->flow) {   // one dependency-driven launch per direction
+        const int p = flow_prec<T>();
+        const Flow F = flow_of(c);
+        const bool tasks = flow_levels_only(c);
+        if (tasks)
+            forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
+                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+        if (F.nitems > F.first) {
+            forward_flow_kernel<T><<<c->flow_grid[p][0], kFlowThreads, flow_fwd_bytes<T>(c), st>>>(
+                c->plan, F, c->d_task_ptr, c->d_task_sn, Lx, xp, active);
+            backward_flow_kernel<T><<<c->flow_grid[p][1], kFlowThreads, flow_bwd_bytes<T>(c), st>>>(
+                c->plan, F, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+        }
+        if (tasks)
+            backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(T), st>>>(
+                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+        return;
+    }
     if (c->ntasks > 0)
         forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
             c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
@@ -986,7 +1130,7 @@ kkt_status apply_kinv(kkt_ctx* c, const double* in, double* out, cudaStream_t st
     const int n = c->n;
     const int sp = span_begin(c, 2, st);
     c->stats.kinv_calls++;
-    c->stats.launches += 2 + 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0);
+    c->stats.launches += 2 + (c->flow ? 2LL + (flow_levels_only(c) ? 2 : 0) : 2LL * c->nlev + (c->ntasks > 0 ? 2 : 0));
     if (c->opt.solver == 1) {
         CUDA_TRY(c, cudaMemcpyAsync(c->w_xp, in, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (c->tri_exec) {
@@ -1515,6 +1659,7 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         set_backward_smem_limit<df64>();
         set_backward_smem_limit<double>();
         set_backward_smem_limit<float>();
+        setup_flow(c);
         st = capture_graphs(c);
         if (st != KKT_OK) {
             set_err(nullptr, st, c->err);
@@ -1995,6 +2140,18 @@ kkt_status bounds_verdict(kkt_ctx* c, cudaStream_t st, kkt_status s0) {
     return s0;
 #endif
 }
+// After a call that synchronised its stream: a dataflow solve whose wait
+// gave up has left x invalid and its counters unknown; they are cleared so
+// the next solve starts clean, and the call reports KKT_ERR_TIMEOUT.
+kkt_status flow_verdict(kkt_ctx* c, kkt_status s0) {
+    if (!c || !c->h_flow_err || *(volatile int*)c->h_flow_err == 0) return s0;
+    *(volatile int*)c->h_flow_err = 0;
+    cudaMemset(c->d_flow_cnt, 0, (size_t)c->flow_items * sizeof(int));
+    cudaMemset(c->d_flow_done, 0, (size_t)c->flow_items * sizeof(unsigned));
+    cudaMemset(c->d_flow_ctrl, 0, 4 * sizeof(unsigned));
+    cudaDeviceSynchronize();
+    return set_err(c, KKT_ERR_TIMEOUT, "a dependency wait of the dataflow triangular solve gave up");
+}
 }  // namespace
 
 extern "C" {
@@ -2016,7 +2173,7 @@ static kkt_status solve_impl(kkt_ctx* c, const double* d_rx, const double* d_ry,
 
 kkt_status kkt_solve(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
                      double* d_ds, cudaStream_t st, kkt_info* info) {
-    return bounds_verdict(c, st, solve_impl(c, d_rx, d_ry, d_dx, d_dy, d_ds, st, info));
+    return flow_verdict(c, bounds_verdict(c, st, solve_impl(c, d_rx, d_ry, d_dx, d_dy, d_ds, st, info)));
 }
 
 static kkt_status solve_impl(kkt_ctx* c, const double* d_rx, const double* d_ry, double* d_dx, double* d_dy,
@@ -2486,8 +2643,8 @@ extern "C" {
 kkt_status kkt_factor_solve(kkt_ctx* c, const double* d_Wval, const double* d_Jval, const double* d_sigma,
                             const double* d_D, const double* delta_x, const double* d_rx, const double* d_ry,
                             double* d_dx, double* d_dy, cudaStream_t st, kkt_info* info) {
-    return bounds_verdict(c, st, factor_solve_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, d_rx, d_ry, d_dx,
-                                                   d_dy, st, info));
+    return flow_verdict(c, bounds_verdict(c, st, factor_solve_impl(c, d_Wval, d_Jval, d_sigma, d_D, delta_x, d_rx,
+                                                                   d_ry, d_dx, d_dy, st, info)));
 }
 
 kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_t st) {
@@ -2495,7 +2652,7 @@ kkt_status kkt_backsolve(kkt_ctx* c, const double* d_b, double* d_x, cudaStream_
     if (!c->factored) return set_err(c, KKT_ERR_STATE, "kkt_backsolve called without a factor");
     TRY(apply_kinv(c, d_b, d_x, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    TRY(bounds_verdict(c, st, KKT_OK));
+    TRY(flow_verdict(c, bounds_verdict(c, st, KKT_OK)));
     spans_collect(c);
     return KKT_OK;
 }
@@ -2531,23 +2688,44 @@ kkt_status kkt_backsolve_noalloc(kkt_ctx* c, const double* d_b, double* d_x, cud
     }
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    return KKT_OK;
+    return flow_verdict(c, KKT_OK);
 }
 
 kkt_status kkt_debug_corrupt_map(kkt_ctx* c, int what) {
 #if KKT_BOUNDS_CHECK
     if (!c || !c->device_ready || c->opt.solver != 0) return set_err(c, KKT_ERR_STATE, "no supernodal device context");
+    if (what < 0 || what > 2)
+        return set_err(c, KKT_ERR_ARG, "what must be 0 (restore), 1 (corrupt the row map) or 2 (raise a wait)");
+    // the arrival count the last dataflow item waits for, raised by one
+    // (what = 2, no solve can meet it, so the wait runs out) or restored
+    auto flow_target = [&](int delta) -> kkt_status {
+        int* q = c->d_flow_nchild + (c->flow_items - 1);
+        int v = 0;
+        CUDA_TRY(c, cudaMemcpy(&v, q, sizeof(int), cudaMemcpyDeviceToHost));
+        v += delta;
+        CUDA_TRY(c, cudaMemcpy(q, &v, sizeof(int), cudaMemcpyHostToDevice));
+        return KKT_OK;
+    };
+    if (what == 2) {
+        if (!c->flow) return set_err(c, KKT_ERR_STATE, "the dataflow solves are not in use");
+        if (!c->dbg_flow_raised) TRY(flow_target(1));
+        c->dbg_flow_raised = true;
+        return KKT_OK;
+    }
+    if (what == 0 && c->dbg_flow_raised) {
+        TRY(flow_target(-1));
+        c->dbg_flow_raised = false;
+    }
+    if (what == 0 && !c->dbg_corrupted) return KKT_OK;
     if (c->dbg_relmap_pos < 0) return set_err(c, KKT_ERR_STATE, "no Schur update in this tree");
     int* p = const_cast<int*>(c->plan.relmap) + c->dbg_relmap_pos;
     if (what == 1 && !c->dbg_corrupted) {
         CUDA_TRY(c, cudaMemcpy(&c->dbg_relmap_old, p, sizeof(int), cudaMemcpyDeviceToHost));
         CUDA_TRY(c, cudaMemcpy(p, &c->dbg_relmap_bad, sizeof(int), cudaMemcpyHostToDevice));
         c->dbg_corrupted = true;
-    } else if (what == 0 && c->dbg_corrupted) {
+    } else if (what == 0) {
         CUDA_TRY(c, cudaMemcpy(p, &c->dbg_relmap_old, sizeof(int), cudaMemcpyHostToDevice));
         c->dbg_corrupted = false;
-    } else if (what != 0 && what != 1) {
-        return set_err(c, KKT_ERR_ARG, "what must be 0 (restore) or 1 (corrupt)");
     }
     return KKT_OK;
 #else
@@ -2651,6 +2829,7 @@ void kkt_destroy(kkt_ctx* c) {
     if (c->h_red) cudaFreeHost(c->h_red);
     if (c->h_act) cudaFreeHost(c->h_act);
     if (c->h_int) cudaFreeHost(c->h_int);
+    if (c->h_flow_err) cudaFreeHost(c->h_flow_err);
     delete c;
 }
 

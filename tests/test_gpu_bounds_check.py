@@ -30,13 +30,13 @@ def checked_lib():
         nat._lib = prev
 
 
-def _case(torch, nat):
+def _case(torch, nat, **opts):
     from paper_2403_15913_gb300 import KKTSolver
     p = TrayParams(k=8, T=20)
     pt = kkt_point(p, 3, sigma_range=(1e-2, 1e2))
     W = tray.hessian_lower_csc(p, pt.w, pt.lam)
     J = tray.jacobian_csr(p, pt.w)
-    s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], scheme="lifted")
+    s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], scheme="lifted", **opts)
     vals = (to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma))
     return p, pt, W, J, s, vals
 
@@ -69,6 +69,43 @@ def test_corrupted_row_map_is_reported_and_recoverable(checked_lib):
     assert "relative row" in str(e.value)
     assert L.kkt_debug_corrupt_map(s._ctx, 0) == nat.KKT_OK
     assert s.factor(Wv, Jv, sv, None, 10.0) == nat.KKT_OK
+    s.close()
+
+
+def test_dataflow_wait_that_runs_out_is_reported_and_recoverable(checked_lib):
+    """The waits of the dataflow triangular solves are bounded: with the
+    arrival count of the tree's last item raised by one (no solve can meet
+    it) the wait gives up after about a second, the kernel still completes,
+    and the solve returns KKT_ERR_TIMEOUT; once restored, the context solves
+    correctly again (its counters were reset)."""
+    import time
+    torch = torch_cuda()
+    nat = checked_lib
+    from paper_2403_15913_gb300 import KKTError
+    p, pt, W, J, s, (Wv, Jv, sv) = _case(torch, nat, staged_solve=2)
+    L = nat.lib()
+    delta_x = 10.0
+    assert s.factor(Wv, Jv, sv, None, delta_x) == nat.KKT_OK
+    b = np.random.default_rng(5).standard_normal(p.n)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    assert L.kkt_debug_corrupt_map(s._ctx, 2) == nat.KKT_OK
+    t0 = time.perf_counter()
+    with pytest.raises(KKTError) as e:
+        s.backsolve(to_dev(torch, b), x)
+    waited = time.perf_counter() - t0
+    assert e.value.status == nat.KKT_ERR_TIMEOUT
+    assert "gave up" in str(e.value)
+    assert 0.5 <= waited <= 20.0, waited
+    assert L.kkt_debug_corrupt_map(s._ctx, 0) == nat.KKT_OK
+    Kc = okkt.condensed_coo(p.n, W, J, pt.sigma, delta_x, np.full(p.m, 1e8))   # D = 1/delta (delta = 1e-8)
+    import scipy.sparse as sp
+    K = sp.coo_matrix((Kc[2], (Kc[0], Kc[1])), shape=(p.n, p.n)).tocsr()
+    for _ in range(2):
+        x.zero_()
+        s.backsolve(to_dev(torch, b), x)
+        xg = x.cpu().numpy()
+        res = np.max(np.abs(K @ xg - b)) / (okkt.inf_norm(K) * np.max(np.abs(xg)) + np.max(np.abs(b)))
+        assert res <= 1e-15, res
     s.close()
 
 

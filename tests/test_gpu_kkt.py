@@ -134,12 +134,12 @@ def test_nonfinite_values_report_oracle_column(where, bad):
     assert s.info.failed_col == e.value.column
 
 
-@pytest.mark.parametrize("staged", [1, 0])
+@pytest.mark.parametrize("staged", [3, 2, 1, 0])
 @pytest.mark.parametrize("sig,D,dx0", [((1e-2, 1e2), 1e2, 10.0), ((1e-6, 1e6), 1e8, 0.0)])
 def test_backsolve_matches_oracle(sig, D, dx0, staged):
     """K^{-1} b by the supernodal triangular solves equals the oracle's
-    left-looking factor + column substitutions (staged and plain level
-    kernels)."""
+    left-looking factor + column substitutions (dataflow, staged and plain
+    level kernels)."""
     torch = torch_cuda()
     p, pt, W, J = instance(32, 50, 0, sigma_range=sig)
     s = solver_for(p, W, J, scheme="lifted", staged_solve=staged, **OPTS)
@@ -158,6 +158,38 @@ def test_backsolve_matches_oracle(sig, D, dx0, staged):
     assert res <= 1e-15, res
     if D < 1e3:
         assert np.max(np.abs(xg - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("k,T,opts", [(32, 50, OPTS), (8, 400, dict(leaf_size=16, subtree_cols=16)),
+                                       (16, 120, dict(subtree_cols=0))])
+def test_dataflow_solves_repeat_and_match_the_oracle(k, T, opts, mode):
+    """The dataflow triangular solves (staged_solve 2: one launch per
+    direction; 3: the subtree tasks in their own launches) re-arm their
+    arrival counters and epochs: five solves in a row with different right-
+    hand sides each match the oracle's factor substitution, on a tree with
+    subtree tasks and many levels, and on one without subtree tasks; each
+    K^{-1} costs four launches (gather, forward, backward, scatter), two
+    more with the subtree tasks apart."""
+    torch = torch_cuda()
+    p, pt, W, J = instance(k, T, 1, sigma_range=(1e-2, 1e2))
+    s = solver_for(p, W, J, scheme="lifted", staged_solve=mode, **opts)
+    D = np.full(p.m, 1e2)
+    assert s.factor(to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma), to_dev(torch, D), 1.0) == 0
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **OPTS)   # K^{-1} b does not depend on the ordering
+    Kr, Kc, Kv = okkt.condensed_coo(p.n, W, J, pt.sigma, 1.0, D)
+    chol = cholesky.SparseCholesky(sym, p.n, Kr, Kc, Kv)
+    rng = np.random.default_rng(11)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    for rep in range(5):
+        b = rng.standard_normal(p.n) * 10.0 ** rep
+        s.reset_stats()
+        s.backsolve(to_dev(torch, b), x)
+        assert s.stats()["launches"] in ((4,) if mode == 2 else (4, 6))
+        ref = chol.solve(b)
+        xg = x.cpu().numpy()
+        assert np.max(np.abs(xg - ref)) <= 1e-10 * np.max(np.abs(ref)), rep
+    s.close()
 
 
 def _solve(p, pt, W, J, scheme, delta_x=0.0, D=None, **opts):

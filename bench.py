@@ -133,6 +133,10 @@ def parse():
     ap.add_argument("--requests", type=int, default=400, help="serve workload: timed requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrivals per s")
     ap.add_argument("--slots", type=int, default=8, help="serve workload: concurrent solves")
+    ap.add_argument("--cohort", type=int, default=4,
+                    help="serve workload: clients per cohort of the batched server (0: not run)")
+    ap.add_argument("--cohort-slots", type=int, default=8,
+                    help="serve workload: cohorts the batched server runs at a time")
     ap.add_argument("--batch", type=int, default=256, help="batch workload: instances")
     ap.add_argument("--autotune", action="store_true",
                     help="batch workload: pick the supernode partition with kkt_autotune_batch first")
@@ -965,15 +969,19 @@ def run_serve(args, ws, rank, local):
     gaps = rng.exponential(1.0 / args.rate, args.requests)
     who = rng.integers(0, args.clients, args.requests)
 
-    def serve(slots, precision, rate=None, count=None):
+    def serve(slots, precision, rate=None, count=None, cohort=0):
         gaps_, who_ = gaps, who
         if rate is not None:
             r2 = np.random.default_rng(args.seed + 31)
             gaps_ = r2.exponential(1.0 / rate, count)
             who_ = r2.integers(0, args.clients, count)
         srv = NMPCServer(slots=slots, hbm_budget_gb=40.0, scheme=args.scheme, precision=precision,
-                         gamma=args.gamma)
-        cl = [srv.add_client(p.as_array()) for p in params]
+                         gamma=args.gamma, batch=cohort)
+        # a batched server groups clients into cohorts in the order they are
+        # added: added by size, so a cohort's members have similar trees
+        cl = [None] * len(params)
+        for i in (sorted(range(len(params)), key=lambda j: params[j].n) if cohort else range(len(params))):
+            cl[i] = srv.add_client(params[i].as_array())
         t0 = time.perf_counter()
         for t in [srv.submit(c) for c in cl]:        # contexts created, first solves (untimed)
             srv.wait(t)
@@ -994,6 +1002,7 @@ def run_serve(args, ws, rank, local):
         srv.close()
         lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
         span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) * 1e-3
+        objective[(slots, precision, cohort, rate)] = {r["id"]: r["objective"] for r in res}
         return {"solves_per_s": len(res) / span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "iters_mean": float(np.mean([r["iters"] for r in res])),
@@ -1002,9 +1011,35 @@ def run_serve(args, ws, rank, local):
                 "contexts": st["contexts_created"], "evictions": st["evictions"],
                 "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "clocks": clk}
 
+    objective = {}
+
+    def obj_diff(a, b):
+        """largest relative objective difference of the same requests"""
+        oa, ob = objective[a], objective[b]
+        return float(max(abs(oa[i] - ob[i]) / max(abs(ob[i]), 1e-300) for i in oa))
+
     prec = PREC[args.precision]
     conc = serve(args.slots, prec)
     serial = serve(1, 0)
+    batched = {}
+    if args.cohort > 0:
+        # the batched server: cohorts of clients, one union KKT factor and
+        # solve per IPM iteration of a cohort, in FP64 and with the FP32
+        # factor and FP64 refinement; accuracy against the serial FP64 path
+        # request by request (same stream, same per-client order)
+        for name, pr in (("fp64", 0), ("fp32_factor", 1)):
+            r = serve(args.cohort_slots, pr, cohort=args.cohort)
+            r.pop("clocks")
+            r["max_rel_objective_diff_vs_serial_fp64"] = obj_diff((args.cohort_slots, pr, args.cohort, None),
+                                                                  (1, 0, 0, None))
+            r["speedup_vs_serial_fp64"] = r["solves_per_s"] / serial["solves_per_s"]
+            batched[name] = r
+        best = batched["fp32_factor"]
+        light_b_rate = 0.7 * best["solves_per_s"]
+        lb = serve(args.cohort_slots, 1, rate=light_b_rate, count=min(args.requests, 200), cohort=args.cohort)
+        lb.pop("clocks")
+        lb["rate_per_s"] = light_b_rate
+        batched["fp32_factor"]["at_70pct_of_capacity"] = lb
     # service latency below saturation: the same server at 70% of the
     # throughput it just sustained
     light_rate = 0.7 * conc["solves_per_s"]
@@ -1027,6 +1062,7 @@ def run_serve(args, ws, rank, local):
                                    f"{args.rate:g}/s, each a full {args.scheme} IPM solve to 1e-8 warm-started "
                                    f"from the shifted previous solution, 40 GB admission budget",
                        "slots": args.slots, "concurrent": conc, "serial_fp64_one_slot": serial,
+                       "batched": dict(batched, cohort=args.cohort, cohort_slots=args.cohort_slots),
                        "at_70pct_of_capacity": light,
                        "speedup_vs_serial": conc["solves_per_s"] / serial["solves_per_s"],
                        "step": "one request = one full IPM solve; value = requests / (last done - first "
@@ -1112,6 +1148,10 @@ def sub_records(args, local):
                                          for k in ("solves_per_s", "p50_ms", "p99_ms")},
                 "at_70pct_of_capacity": {k: c["at_70pct_of_capacity"][k]
                                          for k in ("rate_per_s", "solves_per_s", "p50_ms", "p99_ms")},
+                "batched": {name: {k: v for k, v in r.items() if k in (
+                    "solves_per_s", "p50_ms", "p99_ms", "iters_mean", "converged",
+                    "max_rel_objective_diff_vs_serial_fp64", "speedup_vs_serial_fp64", "at_70pct_of_capacity")}
+                    for name, r in c["batched"].items() if isinstance(r, dict)},
                 "iters_mean": c["concurrent"]["iters_mean"], "clocks": ln["clocks"]}
 
     safe("hykkt_gamma_1e4", lambda: hykkt(1e4))

@@ -303,6 +303,27 @@ kkt_status kkt_autotune_batch(int count, const int* n, const int* m,
                               const kkt_options* base, int sample, cudaStream_t stream,
                               kkt_options* best, double* best_ms);
 
+/* Precision of the following factorisations: 0 (FP64) or the reduced
+ * precision the context was analysed with (kkt_options.precision 1 or 2,
+ * whose storage exists), else KKT_ERR_ARG.  For a driver that knows the
+ * reduced precision will not refine (e.g. it fell back to FP64 at the
+ * previous IPM iteration: late iterations only grow the spread of Sigma)
+ * and would otherwise pay both factorisations; the paper keeps FP64
+ * throughout (Sec. V-B), the reduced precision is an extension. */
+kkt_status kkt_set_precision(kkt_ctx* ctx, int precision);
+
+/* Per-instance switch of the factorisation of a batch: active[i] = 0 makes
+ * the following factorisations leave instance i's panels as the assembly
+ * leaves them (no factorisation work), so a solve of instance i is valid
+ * only for a zero right-hand side (which gives zero); NULL switches every
+ * instance on (the default).  Takes effect at the next kkt_factor,
+ * kkt_factor_batch or kkt_factor_solve on the context; the array is copied,
+ * but it must not change while a factorisation of this context is in
+ * flight.  KKT_ERR_ARG for a non-NULL array on a single system.  (An
+ * extension for batched serving, which the paper does not have: members of
+ * a batch that take no step cost no factorisation.) */
+kkt_status kkt_batch_set_active(kkt_ctx* ctx, const int* active);
+
 /* Per-instance results of the last kkt_factor / kkt_solve (host arrays of
  * count entries, any may be NULL): status (KKT_OK, KKT_ERR_STALL,
  * KKT_ERR_MAXIT, KKT_ERR_NOT_SPD), refinement sweeps, CG iterations,
@@ -525,9 +546,13 @@ kkt_status kkt_device_bytes(const kkt_ctx* ctx, int64_t* bytes);
  * members that still iterate is one factorisation and refined solve of the
  * block-diagonal union of their KKT systems (kkt_analyse_batch; with kopt
  * precision 0 one kkt_factor_solve graph launch, with precision 1 or 2 the
- * reduced-precision factor with FP64 refinement and fallback).  Members
- * that converged or failed keep their last block in the union (it still
- * factorises) and take no further steps.
+ * reduced-precision factor with FP64 refinement and fallback).  Each
+ * phase of an iteration enqueues the kernels of every stepping member on
+ * the one stream and synchronises once.  Members start and stop
+ * independently (continuous batching, kkt_ipm_batch_start_member): one that
+ * does not step is switched off in the union's factorisation
+ * (kkt_batch_set_active) and has a zero right-hand side, so it costs no
+ * factorisation work and its refinement stops at once.
  * ---------------------------------------------------------------------- */
 typedef struct kkt_ipm_batch kkt_ipm_batch;
 
@@ -543,6 +568,21 @@ kkt_ipm* kkt_ipm_batch_member(kkt_ipm_batch* batch, int i);
 
 /* Marks every member as iterating (each must have been initialised). */
 kkt_status kkt_ipm_batch_start(kkt_ipm_batch* batch);
+
+/* Continuous batching: member i, initialised since it last stopped
+ * (kkt_ipm_init / kkt_ipm_init_shifted / kkt_ipm_init_warm), takes part in
+ * the following kkt_ipm_batch_step calls while the other members go on.
+ * KKT_ERR_STATE if it never was initialised or still iterates. */
+kkt_status kkt_ipm_batch_start_member(kkt_ipm_batch* batch, int i);
+
+/* Member i's state: status KKT_OK while it iterates, else its final status
+ * (KKT_CONVERGED, KKT_ERR_MAXIT after max_iter steps, KKT_ERR_STALL, ...;
+ * KKT_ERR_STATE before it first started); iters its iteration count. */
+kkt_status kkt_ipm_batch_member_status(const kkt_ipm_batch* batch, int i, int* status, int* iters);
+
+/* Device memory of the batch: the union's KKT context, the members' IPM
+ * buffers and the union's value and vector arrays, in bytes. */
+kkt_status kkt_ipm_batch_device_bytes(const kkt_ipm_batch* batch, int64_t* bytes);
 
 /* One lock-step iteration of every member still iterating; info (may be
  * NULL) receives count reports, written for the members that took a step
@@ -594,6 +634,18 @@ typedef struct {
     int warm_start;         /* 1: start from the shifted previous iterate (1)     */
     double warm_mu;         /* barrier parameter of warm starts (1e-4)            */
     int warm_recenter;      /* 1: warm starts recentre the bound multipliers (1)  */
+    int batch;              /* 0 (default): one solve per slot.  b > 0: batched
+                               serving -- clients are grouped, in the order
+                               they are added, into cohorts of up to b (a
+                               cohort closes when full or at the first
+                               request for one of its clients); a cohort is
+                               one kkt_ipm_batch, so each IPM iteration of
+                               all its running requests is one factorisation
+                               and refined solve of the union of their KKT
+                               systems (precision 1: FP32 factor, FP64
+                               refinement); requests join and leave between
+                               iterations; a slot runs one cohort at a time;
+                               cohorts are admitted and evicted as a unit     */
 } kkt_server_options;
 
 typedef struct {

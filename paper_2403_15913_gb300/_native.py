@@ -31,7 +31,8 @@ EXPORTED = [
     "kkt_default_options", "kkt_analyse", "kkt_analyse_host", "kkt_symbolic_sizes",
     "kkt_symbolic_export", "kkt_factor", "kkt_solve", "kkt_backsolve", "kkt_backsolve_noalloc",
     "kkt_factor_export", "kkt_analyse_batch", "kkt_analyse_batch_host", "kkt_batch_layout",
-    "kkt_factor_batch", "kkt_factor_solve", "kkt_batch_results", "kkt_autotune_batch",
+    "kkt_factor_batch", "kkt_factor_solve", "kkt_batch_results", "kkt_autotune_batch", "kkt_batch_set_active",
+    "kkt_set_precision",
     "kkt_last_error", "kkt_destroy", "kkt_tray_sizes", "kkt_tray_pattern",
     "kkt_tray_eval", "kkt_set_profiling", "kkt_get_stats", "kkt_reset_stats",
     "kkt_ipm_default_options", "kkt_ipm_create", "kkt_ipm_init", "kkt_ipm_step", "kkt_ipm_solve",
@@ -40,6 +41,7 @@ EXPORTED = [
     "kkt_ipm_device_bytes", "kkt_device_bytes",
     "kkt_ipm_batch_create", "kkt_ipm_batch_member", "kkt_ipm_batch_start", "kkt_ipm_batch_step",
     "kkt_ipm_batch_solve", "kkt_ipm_batch_kkt", "kkt_ipm_batch_last_error", "kkt_ipm_batch_destroy",
+    "kkt_ipm_batch_start_member", "kkt_ipm_batch_member_status", "kkt_ipm_batch_device_bytes",
     "kkt_server_default_options", "kkt_server_create", "kkt_server_add_client", "kkt_server_submit",
     "kkt_server_wait", "kkt_server_drain", "kkt_server_get_stats", "kkt_server_destroy",
     "kkt_eval_fn", "kkt_debug_corrupt_map",
@@ -108,7 +110,7 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget_gb", ctypes.c_double), ("scheme", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gamma", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double), ("warm_start", ctypes.c_int),
-                ("warm_mu", ctypes.c_double), ("warm_recenter", ctypes.c_int)]
+                ("warm_mu", ctypes.c_double), ("warm_recenter", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class RequestResult(ctypes.Structure):
@@ -182,6 +184,10 @@ def load(path):
     L.kkt_autotune_batch.restype = ctypes.c_int
     L.kkt_batch_results.argtypes = [P, I32P, I32P, I32P, F64P, I32P]
     L.kkt_batch_results.restype = ctypes.c_int
+    L.kkt_batch_set_active.argtypes = [P, I32P]
+    L.kkt_batch_set_active.restype = ctypes.c_int
+    L.kkt_set_precision.argtypes = [P, ctypes.c_int]
+    L.kkt_set_precision.restype = ctypes.c_int
     L.kkt_symbolic_sizes.argtypes = [P, I32P, I64P, I64P, I64P, I32P, F64P]
     L.kkt_symbolic_sizes.restype = ctypes.c_int
     L.kkt_symbolic_export.argtypes = [P, I32P, I32P, I32P, I32P, I32P, I32P]
@@ -244,6 +250,12 @@ def load(path):
     L.kkt_ipm_batch_member.restype = P
     L.kkt_ipm_batch_start.argtypes = [P]
     L.kkt_ipm_batch_start.restype = ctypes.c_int
+    L.kkt_ipm_batch_start_member.argtypes = [P, ctypes.c_int]
+    L.kkt_ipm_batch_start_member.restype = ctypes.c_int
+    L.kkt_ipm_batch_member_status.argtypes = [P, ctypes.c_int, I32P, I32P]
+    L.kkt_ipm_batch_member_status.restype = ctypes.c_int
+    L.kkt_ipm_batch_device_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.kkt_ipm_batch_device_bytes.restype = ctypes.c_int
     L.kkt_ipm_batch_step.argtypes = [P, P, ctypes.POINTER(IPMInfo)]
     L.kkt_ipm_batch_step.restype = ctypes.c_int
     L.kkt_ipm_batch_solve.argtypes = [P, P, I32P, I32P, ctypes.POINTER(IPMInfo)]

@@ -193,6 +193,7 @@ factor_fused_kernel(Plan P, const int* __restrict__ lvl_sn, int split, T* __rest
     __shared__ short2 tab[kFusedMaxC * (kFusedMaxC - 1) / 2];
     const int s = lvl_sn[blockIdx.x / split];
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    if (!sn_on(P, s)) return;
     const int rank = (int)(blockIdx.x % split);
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     T* U = reinterpret_cast<T*>(smem_raw);   // r x c, ld = r
@@ -249,6 +250,7 @@ factor_fused_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) {   // the whole cluster returns together
         return;
     }
+    if (!sn_on(P, s)) return;   // switched-off instance: the whole cluster returns together
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     const int i0 = (int)((long long)rb * rank / K), i1 = (int)((long long)rb * (rank + 1) / K);
     const int nr = i1 - i0;

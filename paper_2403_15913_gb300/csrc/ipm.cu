@@ -401,6 +401,11 @@ struct kkt_ipm {
     kkt_ipm_info cur{};
     double fval = 0.0;
     bool report = false;
+    // the filter line search in progress: step lengths, directional
+    // derivative, theta and barrier function at the current point, the
+    // trial step and the trials made
+    double a_pr = 0, a_du = 0, dphi = 0, th = 0, ph = 0, alpha = 0;
+    int ls = 0;
 };
 
 namespace {
@@ -434,23 +439,22 @@ kkt_status dalloc(kkt_ipm* p, T** out, size_t count) {
 
 Bounds bounds_of(const kkt_ipm* p) { return Bounds{p->xlo, p->xhi, p->opt.tau_relax}; }
 
-// copy the nq results the last CTA of a reduction kernel left in red
-kkt_status finish_reduce(kkt_ipm* p, int nq, cudaStream_t st, double* out) {
+// Each phase of an iteration enqueues its kernels, whose reductions leave
+// their results in slots of red, then one copy of the first nq slots to the
+// pinned h_red; the host reads them after one synchronisation of the stream
+// (shared by all members of a batch).
+kkt_status fetch_red(kkt_ipm* p, int nq, cudaStream_t st) {
     ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ICUDA(p, cudaStreamSynchronize(st));
-    for (int q = 0; q < nq; ++q) out[q] = p->h_red[q];
     return KKT_OK;
 }
 
 // objective at w via partials in part[b * kQ + kQ - 1] and the final reduce
-kkt_status objective(kkt_ipm* p, const double* w, cudaStream_t st, double* f) {
+// into red[slot]
+kkt_status objective(kkt_ipm* p, const double* w, cudaStream_t st, int slot) {
     if (!kktgb::tray_objective_partials(p->params, w, p->part + (kQ - 1), kQ, kRB, st))
         return ierr(p, KKT_ERR_CUDA, "objective kernel launch failed");
-    final_sum_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->red);
+    final_sum_kernel<<<1, 32, 0, st>>>(p->part + (kQ - 1), p->red + slot);
     p->launches += 2;
-    ICUDA(p, cudaMemcpyAsync(p->h_red, p->red, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ICUDA(p, cudaStreamSynchronize(st));
-    *f = p->h_red[0];
     return KKT_OK;
 }
 
@@ -469,15 +473,20 @@ double err_mu(const kkt_ipm* p, const Errors& e, double mu) {
     return std::max(std::max(e.du / s_d, e.pr), compl_mu / s_c);
 }
 
-kkt_status measures(kkt_ipm* p, const double* x, const double* s, const double* c, cudaStream_t st,
-                    double* theta, double* logsum) {
+// constraint violation theta and the barrier log-sum at (x, s) into
+// red[slot], red[slot + 1]
+void measures(kkt_ipm* p, const double* x, const double* s, const double* c, cudaStream_t st, int slot) {
     measure_kernel<<<kRB, kT, 0, st>>>(p->n, p->m, p->opt.relaxed, bounds_of(p), x, s, c, p->part, p->count,
-                                       p->red);
+                                       p->red + slot);
     p->launches += 1;
-    double out[2];
-    ITRY(finish_reduce(p, 2, st, out));
-    *theta = out[0];
-    *logsum = out[1];
+}
+
+// theta at the current point, on the host (one synchronisation)
+kkt_status theta_now(kkt_ipm* p, cudaStream_t st, double* th) {
+    measures(p, p->x, p->s, p->c, st, 0);
+    ITRY(fetch_red(p, 2, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    *th = p->h_red[0];
     return KKT_OK;
 }
 
@@ -621,8 +630,8 @@ kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
         fill_kernel<<<grid(m), kT, 0, st>>>(m, 1.0, p->vu);
     }
     ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
-    double th = 0, ls = 0;
-    ITRY(measures(p, p->x, p->s, p->c, st, &th, &ls));
+    double th = 0;
+    ITRY(theta_now(p, st, &th));
     p->theta_max = 1e4 * std::max(1.0, th);
     p->theta_min = 1e-4 * std::max(1.0, th);
     p->mu = p->opt.mu_init;
@@ -636,9 +645,14 @@ kkt_status kkt_ipm_init(kkt_ipm* p, const double* d_x0, cudaStream_t st) {
 
 namespace {
 
-// Steps 1-3 of an iteration (KKT_CONVERGED when the optimality error is
-// <= tol); the iteration's report accumulates in p->cur.
-kkt_status step_begin(kkt_ipm* p, cudaStream_t st) {
+// Steps 1-3 of an iteration, split where the host needs reduction results:
+// begin_issue enqueues the derivatives, the optimality-error reduction
+// (red[0..5]) and the objective (red[6]) with their copy to the host;
+// begin_finish, after the stream is synchronised, updates the barrier
+// parameter and enqueues the right-hand side and diagonals.  KKT_CONVERGED
+// when the optimality error is <= tol; the iteration's report accumulates
+// in p->cur.
+kkt_status begin_issue(kkt_ipm* p, cudaStream_t st) {
     const int n = p->n, m = p->m;
     const int rel = p->opt.relaxed;
     const Bounds B = bounds_of(p);
@@ -652,15 +666,22 @@ kkt_status step_begin(kkt_ipm* p, cudaStream_t st) {
     jt_kernel<<<grid(n), kT, 0, st>>>(n, p->jt_cp, p->jt_ri, p->jt_idx, p->Jv, p->y, p->jty);
     p->launches += 2;
     cudaEventRecord(p->ev[1], st);
-    // 2. optimality error and barrier update
+    // 2. optimality error and objective
     errors_kernel<<<kRB, kT, 0, st>>>(n, m, rel, B, p->x, p->s, p->y, p->zl, p->zu, p->vl, p->vu,
                                       p->grad, p->jty, p->c, p->part, p->count, p->red);
     p->launches += 1;
-    double ev6[6];
-    ITRY(finish_reduce(p, 6, st, ev6));
-    Errors E{ev6[0], ev6[1], ev6[2], ev6[3], ev6[4], ev6[5]};
-    double fval = 0.0;
-    ITRY(objective(p, p->x, st, &fval));
+    ITRY(objective(p, p->x, st, 6));
+    return fetch_red(p, 7, st);
+}
+
+kkt_status begin_finish(kkt_ipm* p, cudaStream_t st) {
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    const Bounds B = bounds_of(p);
+    kkt_ipm_info& inf = p->cur;
+    const double* h = p->h_red;
+    Errors E{h[0], h[1], h[2], h[3], h[4], h[5]};
+    const double fval = h[6];
     const double e0 = err_mu(p, E, 0.0);
     inf.objective = fval;
     inf.inf_du = E.du;
@@ -719,13 +740,19 @@ kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
     return KKT_OK;
 }
 
-// Steps 5-7: recovery, filter line search, update.
-kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
-    kkt_ipm_info& inf = p->cur;
+// Steps 5-7, split the same way: end_issue enqueues the recovery with the
+// fraction-to-the-boundary steps and the directional derivative (red[0..2])
+// and the measures at the current point (red[3..4]); end_search_begin reads
+// them and starts the filter line search.  Each trial enqueues its point,
+// model values, measures (red[0..1]) and objective (red[2]) (trial_issue)
+// and is judged after the synchronisation (trial_judge: 1 accepted, 0 try
+// the halved step, -1 no trial left); accept_issue enqueues the update, and
+// step_done closes the iteration once the stream has completed it.
+kkt_status end_issue(kkt_ipm* p, cudaStream_t st) {
     const int n = p->n, m = p->m;
     const int rel = p->opt.relaxed;
     const Bounds B = bounds_of(p);
-    const double mu = p->mu, fval = p->fval;
+    const double mu = p->mu;
     cudaEventRecord(p->ev[2], st);
     // 5. recovery, fraction to boundary, directional derivative
     const double tau = std::max(kTauMin, 1.0 - mu);
@@ -733,58 +760,83 @@ kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
                                        p->vu, p->grad, p->dx, p->dy, p->ds, p->dzl, p->dzu, p->dvl,
                                        p->dvu, p->part, p->count, p->red);
     p->launches += 1;
-    double rv[3];
-    ITRY(finish_reduce(p, 3, st, rv));
-    const double a_pr = rv[0], a_du = rv[1], dphi = rv[2];
-    // 6. filter line search
-    double th = 0, lsum = 0;
-    ITRY(measures(p, p->x, p->s, p->c, st, &th, &lsum));
-    const double ph = fval - mu * lsum;
-    double alpha = a_pr;
-    bool accepted = false;
-    int ls = 0;
-    for (ls = 1; ls <= kMaxLs; ++ls) {
-        trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, alpha, p->x, p->dx, p->s, p->ds,
-                                                          p->xt, p->st);
-        p->launches += 1;
-        ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
-        p->launches += 1;
-        double tht = 0, lst = 0, ft = 0;
-        ITRY(measures(p, p->xt, p->st, p->ct, st, &tht, &lst));
-        ITRY(objective(p, p->xt, st, &ft));
-        const double pht = ft - mu * lst;
-        bool ok = tht <= p->theta_max;
-        for (const auto& fe : p->filter)
-            if (!(tht < fe.first || pht < fe.second)) { ok = false; break; }
-        bool f_type = false;
-        if (ok) {
-            const bool switching = dphi < 0 && alpha * std::pow(-dphi, kSPhi) > kDelta * std::pow(th, kSTheta);
-            if (th <= p->theta_min && switching) {
-                ok = pht <= ph + kEtaPhi * alpha * dphi;
-                f_type = true;
-            } else {
-                ok = tht <= (1 - kGammaTheta) * th || pht <= ph - kGammaPhi * th;
-            }
+    measures(p, p->x, p->s, p->c, st, 3);
+    return fetch_red(p, 5, st);
+}
+
+void end_search_begin(kkt_ipm* p) {
+    const double* h = p->h_red;
+    p->a_pr = h[0];
+    p->a_du = h[1];
+    p->dphi = h[2];
+    p->th = h[3];
+    p->ph = p->fval - p->mu * h[4];
+    p->alpha = p->a_pr;
+    p->ls = 0;
+}
+
+// 6. filter line search: one trial step
+kkt_status trial_issue(kkt_ipm* p, cudaStream_t st) {
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    ++p->ls;
+    trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, p->alpha, p->x, p->dx, p->s, p->ds,
+                                                      p->xt, p->st);
+    p->launches += 1;
+    ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
+    p->launches += 1;
+    measures(p, p->xt, p->st, p->ct, st, 0);
+    ITRY(objective(p, p->xt, st, 2));
+    return fetch_red(p, 3, st);
+}
+
+int trial_judge(kkt_ipm* p) {
+    const double* h = p->h_red;
+    const double tht = h[0], pht = h[2] - p->mu * h[1];
+    const double th = p->th, ph = p->ph, alpha = p->alpha, dphi = p->dphi;
+    bool ok = tht <= p->theta_max;
+    for (const auto& fe : p->filter)
+        if (!(tht < fe.first || pht < fe.second)) { ok = false; break; }
+    bool f_type = false;
+    if (ok) {
+        const bool switching = dphi < 0 && alpha * std::pow(-dphi, kSPhi) > kDelta * std::pow(th, kSTheta);
+        if (th <= p->theta_min && switching) {
+            ok = pht <= ph + kEtaPhi * alpha * dphi;
+            f_type = true;
+        } else {
+            ok = tht <= (1 - kGammaTheta) * th || pht <= ph - kGammaPhi * th;
         }
-        if (ok) {
-            if (!f_type) p->filter.emplace_back((1 - kGammaTheta) * th, ph - kGammaPhi * th);
-            accepted = true;
-            break;
-        }
-        alpha *= 0.5;
     }
-    inf.ls_trials = ls;
-    if (!accepted) {
-        inf.launches = p->launches;
-        p->report = true;
-        return ierr(p, KKT_ERR_STALL, "line search failed (no restoration phase)");
+    if (ok) {
+        if (!f_type) p->filter.emplace_back((1 - kGammaTheta) * th, ph - kGammaPhi * th);
+        return 1;
     }
-    // 7. update
-    accept_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, mu, alpha, a_du, p->x, p->s,
+    p->alpha *= 0.5;
+    return p->ls >= kMaxLs ? -1 : 0;
+}
+
+kkt_status search_failed(kkt_ipm* p) {
+    p->cur.ls_trials = p->ls + 1;
+    p->cur.launches = p->launches;
+    p->report = true;
+    return ierr(p, KKT_ERR_STALL, "line search failed (no restoration phase)");
+}
+
+// 7. update
+void accept_issue(kkt_ipm* p, cudaStream_t st) {
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    const Bounds B = bounds_of(p);
+    p->cur.ls_trials = p->ls;
+    accept_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, B, p->mu, p->alpha, p->a_du, p->x, p->s,
                                                        p->y, p->zl, p->zu, p->vl, p->vu, p->dx,
                                                        p->ds, p->dy, p->dzl, p->dzu, p->dvl, p->dvu);
     p->launches += 1;
     cudaEventRecord(p->ev[3], st);
+}
+
+kkt_status step_done(kkt_ipm* p) {
+    kkt_ipm_info& inf = p->cur;
     ICUDA(p, cudaEventSynchronize(p->ev[3]));
     float t01 = 0, t12 = 0, t03 = 0;
     cudaEventElapsedTime(&t01, p->ev[0], p->ev[1]);
@@ -793,14 +845,37 @@ kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
     inf.t_eval_ms = t01;
     inf.t_kkt_ms = t12;
     inf.t_step_ms = t03;
-    inf.alpha_pr = alpha;
-    inf.alpha_du = a_du;
+    inf.alpha_pr = p->alpha;
+    inf.alpha_du = p->a_du;
     p->it++;
     inf.iter = p->it;
     ICUDA(p, cudaGetLastError());
     inf.launches = p->launches;
     p->report = true;
     return KKT_OK;
+}
+
+// Steps 1-3 and 5-7 of one problem, each phase followed by its own
+// synchronisation.
+kkt_status step_begin(kkt_ipm* p, cudaStream_t st) {
+    ITRY(begin_issue(p, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    return begin_finish(p, st);
+}
+
+kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
+    ITRY(end_issue(p, st));
+    ICUDA(p, cudaStreamSynchronize(st));
+    end_search_begin(p);
+    while (true) {
+        ITRY(trial_issue(p, st));
+        ICUDA(p, cudaStreamSynchronize(st));
+        const int v = trial_judge(p);
+        if (v > 0) break;
+        if (v < 0) return search_failed(p);
+    }
+    accept_issue(p, st);
+    return step_done(p);
 }
 
 }  // namespace
@@ -907,8 +982,8 @@ kkt_status kkt_ipm_init_warm(kkt_ipm* p, double mu, int recenter, cudaStream_t s
                                                   p->opt.tau_relax, mu, p->vl, p->vu);
     }
     ITRY(kktgb::tray_eval(p->params, p->x0v, p->x, nullptr, 1.0, nullptr, nullptr, p->c, nullptr, nullptr, st));
-    double th = 0, ls = 0;
-    ITRY(measures(p, p->x, p->s, p->c, st, &th, &ls));
+    double th = 0;
+    ITRY(theta_now(p, st, &th));
     p->theta_max = 1e4 * std::max(1.0, th);
     p->theta_min = 1e-4 * std::max(1.0, th);
     p->mu = mu;
@@ -963,7 +1038,13 @@ void kkt_ipm_destroy(kkt_ipm* p) {
 // the block-diagonal union of the members' KKT systems in one call (the
 // batch context of kkt_analyse_batch; one graph launch in FP64, or the FP32
 // factor with FP64 refinement).  The members' KKT inputs and outputs are
-// slices of the batch's concatenated arrays, so nothing is copied.
+// slices of the batch's concatenated arrays, so nothing is copied.  Each
+// phase enqueues the kernels of every member on the one stream and then
+// synchronises once, so a tick costs the same few host round trips however
+// many members step.  Members start and stop independently (continuous
+// batching): one that does not step is switched off in the factorisation
+// (kkt_batch_set_active) and has a zero right-hand side, so it costs no
+// factorisation work and its refinement stops at once.
 }  // extern "C"
 
 struct kkt_ipm_batch {
@@ -977,7 +1058,14 @@ struct kkt_ipm_batch {
     std::vector<char> stepping;  // members in the current iteration's KKT step
     std::vector<double> delta;   // delta_x of every member's block in the last factor
     std::vector<int> fcol;       // scratch: failing columns of the last factor
+    std::vector<char> searching; // scratch: members whose line search goes on
+    // reduced precision (kopt precision 1 or 2): members whose solve saw the
+    // union fall back to FP64; while one of them steps, the union is
+    // factorised in FP64 directly (later iterations only widen Sigma)
+    std::vector<char> fell_back;
+    int precision = 0;
     bool relaxed = false, graph = false;
+    long long dev_bytes = 0;     // the union's value and vector arrays
     long long kkt_steps = 0, factor_calls = 0;
     std::string err;
 };
@@ -1017,6 +1105,7 @@ kkt_status kkt_ipm_batch_create(int count, const double* params, const kkt_optio
     b->relaxed = b->mem[0]->opt.relaxed != 0;
     ko.target_relaxed = b->relaxed ? 1 : 0;
     b->graph = ko.precision == 0 && ko.solver == 0;
+    b->precision = ko.solver == 0 ? ko.precision : 0;
     std::vector<int> n(count), m(count);
     std::vector<std::vector<int>> Wc(count), Wr(count), Jr(count), Jc(count);
     std::vector<const int*> pWc(count), pWr(count), pJr(count), pJc(count);
@@ -1042,13 +1131,18 @@ kkt_status kkt_ipm_batch_create(int count, const double* params, const kkt_optio
     kkt_status st = kkt_analyse_batch(count, n.data(), m.data(), pWc.data(), pWr.data(), pJr.data(), pJc.data(),
                                       &ko, &b->kkt);
     if (st != KKT_OK) return fail(st);
-    auto dal = [&](double** v, long long cnt) {
-        if (cudaMalloc((void**)v, std::max<long long>(1, cnt) * sizeof(double)) != cudaSuccess) return false;
+    // zero values, unit diagonals: a member that never stepped has the
+    // identity block and a zero right-hand side
+    auto dal = [&](double** v, long long cnt, double fillv) {
+        const long long c1 = std::max<long long>(1, cnt);
+        if (cudaMalloc((void**)v, c1 * sizeof(double)) != cudaSuccess) return false;
         b->allocs.push_back(*v);
-        return true;
+        b->dev_bytes += c1 * (long long)sizeof(double);
+        std::vector<double> h((size_t)c1, fillv);
+        return cudaMemcpy(*v, h.data(), c1 * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
     };
-    if (!dal(&b->Wv, NW) || !dal(&b->Jv, NJ) || !dal(&b->sigma, N) || !dal(&b->rx, N) || !dal(&b->dx, N) ||
-        !dal(&b->ry, M) || !dal(&b->D, M) || !dal(&b->dy, M))
+    if (!dal(&b->Wv, NW, 0.0) || !dal(&b->Jv, NJ, 0.0) || !dal(&b->sigma, N, 1.0) || !dal(&b->rx, N, 0.0) ||
+        !dal(&b->dx, N, 0.0) || !dal(&b->ry, M, 0.0) || !dal(&b->D, M, 1.0) || !dal(&b->dy, M, 0.0))
         return fail(KKT_ERR_OOM);
     // the union concatenates the members in order: variables, constraints,
     // W and J values
@@ -1079,6 +1173,8 @@ kkt_status kkt_ipm_batch_create(int count, const double* params, const kkt_optio
     }
     b->state.assign(count, (int)KKT_ERR_STATE);
     b->stepping.assign(count, 0);
+    b->searching.assign(count, 0);
+    b->fell_back.assign(count, 0);
     b->delta.assign(count, 0.0);
     b->fcol.assign(count, -1);
     *out = b;
@@ -1094,31 +1190,96 @@ kkt_status kkt_ipm_batch_start(kkt_ipm_batch* b) {
     return KKT_OK;
 }
 
+kkt_status kkt_ipm_batch_start_member(kkt_ipm_batch* b, int i) {
+    if (!b || i < 0 || i >= b->count) return KKT_ERR_ARG;
+    if (!b->mem[i]->started) return berr(b, KKT_ERR_STATE, "member " + std::to_string(i) + " not initialised");
+    if (b->state[i] == KKT_OK) return berr(b, KKT_ERR_STATE, "member " + std::to_string(i) + " is iterating");
+    b->state[i] = KKT_OK;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_batch_member_status(const kkt_ipm_batch* b, int i, int* status, int* iters) {
+    if (!b || i < 0 || i >= b->count) return KKT_ERR_ARG;
+    if (status) *status = b->state[i];
+    if (iters) *iters = b->mem[i]->it;
+    return KKT_OK;
+}
+
+kkt_status kkt_ipm_batch_device_bytes(const kkt_ipm_batch* b, int64_t* bytes) {
+    if (!b || !bytes) return KKT_ERR_ARG;
+    int64_t total = b->dev_bytes, x = 0;
+    for (const kkt_ipm* p : b->mem) {
+        kkt_ipm_device_bytes(p, &x);
+        total += x;
+    }
+    if (kkt_device_bytes(b->kkt, &x) == KKT_OK) total += x;
+    *bytes = total;
+    return KKT_OK;
+}
+
 kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* info) {
     if (!b) return KKT_ERR_ARG;
     const int cnt = b->count;
-    int running = 0;
+    auto sync = [&]() -> kkt_status {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? KKT_OK : berr(b, KKT_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    };
+    auto stop = [&](int i, kkt_status r) {
+        b->stepping[i] = 0;
+        b->searching[i] = 0;
+        b->fell_back[i] = 0;
+        b->state[i] = r;
+        if (info && b->mem[i]->report) info[i] = b->mem[i]->cur;
+    };
     // steps 1-3 of every member still iterating
     for (int i = 0; i < cnt; ++i) {
         b->stepping[i] = 0;
         if (b->state[i] != KKT_OK) continue;
         kkt_ipm* p = b->mem[i];
         p->report = false;
-        const kkt_status r = step_begin(p, st);
-        if (r == KKT_OK) {
+        const kkt_status r = begin_issue(p, st);
+        if (r == KKT_OK)
             b->stepping[i] = 1;
+        else
+            stop(i, r);
+    }
+    TRY_B(b, sync());
+    int running = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (!b->stepping[i]) continue;
+        const kkt_status r = begin_finish(b->mem[i], st);
+        if (r == KKT_OK)
             ++running;
-        } else {
-            b->state[i] = r;
-        }
-        if (info && p->report) info[i] = p->cur;
+        else
+            stop(i, r);
     }
     if (running == 0) return KKT_CONVERGED;
+    // members that do not step keep their last block; a zero right-hand side
+    // ends their refinement at once
+    for (int i = 0; i < cnt; ++i) {
+        if (b->stepping[i]) continue;
+        const kkt_ipm* p = b->mem[i];
+        if (cudaMemsetAsync(p->rx, 0, (size_t)p->n * sizeof(double), st) != cudaSuccess ||
+            cudaMemsetAsync(p->ry, 0, (size_t)p->m * sizeof(double), st) != cudaSuccess)
+            return berr(b, KKT_ERR_CUDA, "batch step: clearing an idle member's right-hand side");
+    }
     // step 4 for all of them at once: the inertia-correction ladder per
-    // member (a member whose block fails raises its own delta_x), members
-    // that stopped keep their last block and delta_x
+    // member (a member whose block fails raises its own delta_x); members
+    // that do not step are switched off (no factorisation work; their zero
+    // right-hand side solves to zero)
     std::vector<double> d(cnt);
     for (int i = 0; i < cnt; ++i) d[i] = b->stepping[i] ? 0.0 : b->delta[i];
+    if (cnt > 1) {
+        std::vector<int> on(b->stepping.begin(), b->stepping.end());
+        const kkt_status as = kkt_batch_set_active(b->kkt, on.data());
+        if (as != KKT_OK) return berr(b, as, std::string("batch step: ") + kkt_last_error(b->kkt));
+    }
+    if (b->precision != 0) {
+        bool fp64 = false;
+        for (int i = 0; i < cnt; ++i) fp64 = fp64 || (b->stepping[i] && b->fell_back[i]);
+        const kkt_status ps = kkt_set_precision(b->kkt, fp64 ? 0 : b->precision);
+        if (ps != KKT_OK) return berr(b, ps, std::string("batch step: ") + kkt_last_error(b->kkt));
+    }
     kkt_info ki{};
     while (true) {
         kkt_status fs;
@@ -1142,9 +1303,7 @@ kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* i
             else
                 d[i] *= p->delta_last == 0.0 ? kKappaWPlusBar : kKappaWPlus;
             if (d[i] > kDeltaMax) {   // this member gives up; the others go on
-                b->stepping[i] = 0;
-                b->state[i] = KKT_ERR_NOT_SPD;
-                ierr(p, KKT_ERR_NOT_SPD, "inertia correction gave up");
+                stop(i, ierr(p, KKT_ERR_NOT_SPD, "inertia correction gave up"));
                 --running;
             } else {
                 again = true;
@@ -1152,17 +1311,23 @@ kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* i
         }
         if (!again) break;
     }
+    bool fell = ki.status_detail == 2;   // a reduced-precision pivot failed: refactorised in FP64
     if (!b->graph && running > 0) {
         const kkt_status ss = kkt_solve(b->kkt, b->rx, b->ry, b->dx, b->dy, nullptr, st, &ki);
+        fell = fell || ki.status_detail == 2;   // the refinement did not reach its tolerance
         if (ss != KKT_OK && ss != KKT_ERR_MAXIT && ss != KKT_ERR_STALL && ss != KKT_ERR_NOT_SPD)
             return berr(b, ss, std::string("batch kkt_solve: ") + kkt_last_error(b->kkt));
     }
     ++b->kkt_steps;
+    if (b->precision != 0 && fell)   // this iteration fell back to FP64
+        for (int i = 0; i < cnt; ++i)
+            if (b->stepping[i]) b->fell_back[i] = 1;
     std::vector<int> ref(cnt), cg(cnt);
     std::vector<double> eta(cnt);
     kkt_status rs = kkt_batch_results(b->kkt, nullptr, ref.data(), cg.data(), eta.data(), nullptr);
     if (rs != KKT_OK) return berr(b, rs, "kkt_batch_results");
-    // steps 5-7 per member
+    // steps 5-7 per member: recovery, then line-search rounds in which every
+    // member still searching tries its next step, then the updates
     for (int i = 0; i < cnt; ++i) {
         if (!b->stepping[i]) continue;
         kkt_ipm* p = b->mem[i];
@@ -1172,9 +1337,51 @@ kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* i
         p->cur.refine_iters = ref[i];
         p->cur.cg_iters = cg[i];
         p->cur.bwd_err = eta[i];
-        const kkt_status r = step_end(p, st);
-        if (r != KKT_OK) b->state[i] = r;
-        if (info && p->report) info[i] = p->cur;
+        const kkt_status r = end_issue(p, st);
+        if (r != KKT_OK) stop(i, r);
+    }
+    TRY_B(b, sync());
+    int searching = 0;
+    for (int i = 0; i < cnt; ++i) {
+        b->searching[i] = b->stepping[i];
+        if (!b->stepping[i]) continue;
+        end_search_begin(b->mem[i]);
+        ++searching;
+    }
+    while (searching > 0) {
+        for (int i = 0; i < cnt; ++i) {
+            if (!b->searching[i]) continue;
+            const kkt_status r = trial_issue(b->mem[i], st);
+            if (r != KKT_OK) {
+                stop(i, r);
+                --searching;
+            }
+        }
+        TRY_B(b, sync());
+        for (int i = 0; i < cnt; ++i) {
+            if (!b->searching[i]) continue;
+            const int v = trial_judge(b->mem[i]);
+            if (v > 0) {
+                b->searching[i] = 0;
+                --searching;
+            } else if (v < 0) {
+                stop(i, search_failed(b->mem[i]));
+                --searching;
+            }
+        }
+    }
+    for (int i = 0; i < cnt; ++i)
+        if (b->stepping[i]) accept_issue(b->mem[i], st);
+    for (int i = 0; i < cnt; ++i) {
+        if (!b->stepping[i]) continue;
+        kkt_ipm* p = b->mem[i];
+        const kkt_status r = step_done(p);
+        if (r != KKT_OK) {
+            stop(i, r);
+            continue;
+        }
+        if (info) info[i] = p->cur;
+        if (p->it > p->opt.max_iter) b->state[i] = KKT_ERR_MAXIT;
     }
     return KKT_OK;
 }
@@ -1189,8 +1396,6 @@ kkt_status kkt_ipm_batch_solve(kkt_ipm_batch* b, cudaStream_t st, int* status, i
     for (int k = 0; k <= max_iter + 1; ++k) {
         r = kkt_ipm_batch_step(b, st, info);
         if (r != KKT_OK) break;
-        for (int i = 0; i < b->count; ++i)
-            if (b->state[i] == KKT_OK && b->mem[i]->it > b->mem[i]->opt.max_iter) b->state[i] = KKT_ERR_MAXIT;
     }
     if (r != KKT_OK && r != KKT_CONVERGED) return r;
     kkt_status out = KKT_CONVERGED;

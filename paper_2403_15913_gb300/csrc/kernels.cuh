@@ -79,7 +79,17 @@ struct Plan {
     int* berr;                // bounds-check error word (bounds-check builds)
     int ns, n;                // supernodes, columns
     long long panel;          // panel entries
+    const int* sn_inst;       // batches: instance of every supernode
+    const int* inst_on;       // batches: per-instance switch of the factorisation (NULL: all on)
 };
+
+// A batch instance switched off keeps its panels as the assembly leaves them
+// and takes no factorisation work (the batched IPM switches off members that
+// take no step; their right-hand sides are zero, so their solves give zero
+// whatever the panels hold).
+__device__ __forceinline__ bool sn_on(const Plan& P, int s) {
+    return !P.inst_on || __ldg(P.inst_on + P.sn_inst[s]) != 0;
+}
 
 // ------------------------------------------------------------- assembly
 // Js = J scaled row-wise by sqrt(D) (D > 0 in both schemes), so that every
@@ -326,6 +336,7 @@ factor_level_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    if (!sn_on(P, s)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     const long long lp = P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -443,6 +454,7 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int s = lvl_sn[blockIdx.x];
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    if (!sn_on(P, s)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
@@ -519,6 +531,7 @@ trsm_rows_kernel(Plan P, const int2* __restrict__ tasks, T* __restrict__ Lx,
     const int2 task = tasks[blockIdx.x];
     const int s = task.x;
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    if (!sn_on(P, s)) return;
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x)   // L11(row, col) dinv(col), row > col,
@@ -548,6 +561,7 @@ syrk_stage_kernel(Plan P, const int4* __restrict__ tasks, T* __restrict__ Lx, in
     const int4 t = tasks[blockIdx.x];
     const int s = t.x;
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;
+    if (!sn_on(P, s)) return;
     const int c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     const T* g = Lx + P.sn_lptr[s];
     if (stage) {
@@ -583,6 +597,7 @@ narrow_level_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
     const int rank = (int)cluster.block_rank();
     const int s = lvl_sn[blockIdx.x / kClusterCtas];
     if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) return;   // the whole cluster returns together
+    if (!sn_on(P, s)) return;   // switched-off instance: the whole cluster returns together
     const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s], rb = r - c;
     T* g = Lx + P.sn_lptr[s];
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
@@ -634,6 +649,7 @@ normalize_panels_kernel(Plan P, const int* __restrict__ list, int count, T* __re
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const int s = list[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;
+        if (!sn_on(P, s)) continue;
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         T* A = Lx + P.sn_lptr[s];
         for (int e = threadIdx.x; e < r * c; e += blockDim.x) A[e] *= dinv[f + e / r];
@@ -990,6 +1006,7 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
     for (int q = task_ptr[blockIdx.x]; q < task_ptr[blockIdx.x + 1]; ++q) {
         const int s = task_sn[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
+        if (!sn_on(P, s)) continue;   // uniform over the CTA
         const int f = P.sn_f[s], c = P.sn_c[s], r = P.sn_r[s];
         T* g = Lx + P.sn_lptr[s];
         for (int e = tid; e < r * c; e += nt) sm[e] = __ldcg(g + e);

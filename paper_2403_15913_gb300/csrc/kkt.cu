@@ -138,6 +138,7 @@ struct kkt_ctx {
     const double* f_C = nullptr;   // dual block of the target system (device) or NULL
     DevBuf<double> d_Cbuf;
     bool device_ready = false;   // false for host-only analyses
+    int analysed_precision = 0;  // opt.precision at the analysis (its storage exists)
     // device address of the allocation-free backsolve's static scratch,
     // looked up when the context is set up (null with noalloc_err set if
     // the lookup failed)
@@ -168,6 +169,10 @@ struct kkt_ctx {
     int nch_xy = 0, nch_x = 0, nch_y = 0;
     int* d_chy_ptr = nullptr;
     int* d_col_inst = nullptr;   // instance of every permuted column (nb > 1)
+    int* d_sn_inst = nullptr;    // instance of every supernode (nb > 1)
+    int* d_inst_on = nullptr;    // per-instance factorisation switch (nb > 1; all on by default)
+    int* h_inst_on = nullptr;    // pinned: the switch kkt_batch_set_active gave
+    bool inst_on_pending = false;   // h_inst_on not yet copied to d_inst_on
     double* d_knorm = nullptr;   // ||K_orig,i||_inf per instance
     double* d_red = nullptr;     // residual maxima, 3 per instance
     int* d_act = nullptr;        // instances whose refinement still runs
@@ -774,6 +779,12 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             col_inst[j] = (int)(std::upper_bound(c->h_xoff.begin(), c->h_xoff.end(), v) - c->h_xoff.begin()) - 1;
         }
         TRY(upload(c, &c->d_col_inst, col_inst));
+        std::vector<int> sn_inst(ns);
+        for (int s = 0; s < ns; ++s) sn_inst[s] = col_inst[S.sn_ptr[s]];
+        TRY(upload(c, &c->d_sn_inst, sn_inst));
+        TRY(upload(c, &c->d_inst_on, std::vector<int>(nb, 1)));
+        CUDA_TRY(c, cudaMallocHost((void**)&c->h_inst_on, (size_t)nb * sizeof(int)));
+        for (int i = 0; i < nb; ++i) c->h_inst_on[i] = 1;
         TRY(alloc(c, &c->d_dvec, n));
         TRY(alloc(c, &c->d_dval, nb));
     }
@@ -819,7 +830,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     CUDA_TRY(c, cudaMemset(c->d_berr, 0, sizeof(int)));
     c->plan = Plan{d_sn_f, d_sn_c, d_sn_r, d_sn_lptr, d_sn_rptr, d_rows,
                    d_seg_ptr, d_seg_t, d_seg_a, d_seg_b, d_seg_map, d_relmap, d_rmask,
-                   c->d_berr, ns, n, c->panel};
+                   c->d_berr, ns, n, c->panel, c->d_sn_inst, c->d_inst_on};
     TRY(upload(c, &c->d_lvl_sn, c->h_lvl_sn));
     TRY(upload(c, &c->d_trsm_tasks, trsm_tasks));
     TRY(upload(c, &c->d_task_ptr, task_ptr));
@@ -875,6 +886,9 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     }
     TRY(upload(c, &c->d_syrk_tasks, syrk_tasks));
     TRY(alloc(c, &c->d_dinv, n));
+    // zero: a batch instance switched off before its first factorisation
+    // solves with these pivots (times a zero right-hand side)
+    CUDA_TRY(c, cudaMemset(c->d_dinv, 0, (size_t)n * sizeof(double)));
     TRY(upload(c, &c->d_perm, S.perm));
     TRY(upload(c, &c->d_iperm, S.iperm));
     TRY(upload(c, &c->d_k_slot, k_slot));
@@ -911,6 +925,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     if (c->opt.precision == 1) {
         TRY(alloc(c, &c->d_Lx32, (size_t)c->panel));
         TRY(alloc(c, &c->d_dinv32, n));
+        CUDA_TRY(c, cudaMemset(c->d_dinv32, 0, (size_t)n * sizeof(float)));
         TRY(alloc(c, &c->w_xp32, n));
     }
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_cg, 2 * sizeof(int)));
@@ -1441,6 +1456,11 @@ kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx,
 
 template <typename T>
 kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
+    if (c->inst_on_pending) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_inst_on, c->h_inst_on, (size_t)c->nb * sizeof(int), cudaMemcpyHostToDevice,
+                                    st));
+        c->inst_on_pending = false;
+    }
     const int sp_a = span_begin(c, 0, st);
     CUDA_TRY(c, cudaMemsetAsync(Lx, 0, (size_t)c->panel * sizeof(T), st));
     assemble_kernel<T><<<grid_for(c->nk), kThreads, 0, st>>>(c->nk, c->d_k_slot, c->d_k_sptr, c->d_k_src,
@@ -1675,6 +1695,7 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
         }
     }
     c->device_ready = device;
+    c->analysed_precision = c->opt.precision;
     *out = c;
     return KKT_OK;
 }
@@ -1909,6 +1930,24 @@ kkt_status kkt_autotune_batch(int count, const int* n, const int* m, const int* 
     }
     *best = won;
     if (best_ms) *best_ms = best_t;
+    return KKT_OK;
+}
+
+kkt_status kkt_set_precision(kkt_ctx* c, int precision) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->device_ready) return set_err(c, KKT_ERR_STATE, "no device context");
+    if (precision != 0 && precision != c->analysed_precision)
+        return set_err(c, KKT_ERR_ARG, "precision must be 0 or the one the context was analysed with");
+    c->opt.precision = precision;
+    return KKT_OK;
+}
+
+kkt_status kkt_batch_set_active(kkt_ctx* c, const int* active) {
+    if (!c) return KKT_ERR_ARG;
+    if (!c->device_ready) return set_err(c, KKT_ERR_STATE, "no device context");
+    if (c->nb < 2) return active ? set_err(c, KKT_ERR_ARG, "not a batch context") : KKT_OK;
+    for (int i = 0; i < c->nb; ++i) c->h_inst_on[i] = active ? (active[i] != 0) : 1;
+    c->inst_on_pending = true;
     return KKT_OK;
 }
 
@@ -2428,6 +2467,11 @@ kkt_status capture_step_body(kkt_ctx* c, const double* W, const double* J, const
                                                       c->f_sigma, 0.0, c->f_dvec, c->f_C, c->d_knorm);
     CUDA_TRY(c, cudaEventRecord(c->ev_side, c->side));
     const long long f0 = c->stats.factor_launches;
+    // the instance switch is read from pinned memory at every replay
+    if (nb > 1)
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_inst_on, c->h_inst_on, (size_t)nb * sizeof(int), cudaMemcpyHostToDevice,
+                                    st));
+    c->inst_on_pending = false;
     TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, 0.0, st));
     c->step_fl = c->stats.factor_launches - f0;
     CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev_side, 0));
@@ -2830,6 +2874,7 @@ void kkt_destroy(kkt_ctx* c) {
     if (c->h_act) cudaFreeHost(c->h_act);
     if (c->h_int) cudaFreeHost(c->h_int);
     if (c->h_flow_err) cudaFreeHost(c->h_flow_err);
+    if (c->h_inst_on) cudaFreeHost(c->h_inst_on);
     delete c;
 }
 

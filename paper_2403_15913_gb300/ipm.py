@@ -176,6 +176,25 @@ class IPMBatch:
             raise KKTError(st, nat.lib().kkt_ipm_batch_last_error(self._h).decode())
         return status, iters
 
+    def start_member(self, i):
+        """Continuous batching: member i (initialised since it last stopped)
+        joins the following steps."""
+        st = nat.lib().kkt_ipm_batch_start_member(self._h, int(i))
+        if st != nat.KKT_OK:
+            raise KKTError(st, nat.lib().kkt_ipm_batch_last_error(self._h).decode())
+
+    def member_status(self, i):
+        """(status, iterations) of member i: status 0 while it iterates."""
+        s = np.zeros(1, np.int32)
+        it = np.zeros(1, np.int32)
+        nat.lib().kkt_ipm_batch_member_status(self._h, int(i), nat.ptr_i32(s), nat.ptr_i32(it))
+        return int(s[0]), int(it[0])
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        nat.lib().kkt_ipm_batch_device_bytes(self._h, ctypes.byref(b))
+        return b.value
+
     def info(self, i):
         return self.infos[i].as_dict()
 

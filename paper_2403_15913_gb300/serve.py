@@ -12,11 +12,13 @@ from .solver import KKTError
 
 
 class NMPCServer:
-    """Concurrent receding-horizon solves of many column-model clients."""
+    """Concurrent receding-horizon solves of many column-model clients
+    (batch > 0: cohorts of up to `batch` clients share one batched IPM whose
+    iterations factorise the union of their KKT systems once)."""
 
     def __init__(self, slots=8, hbm_budget_gb=40.0, scheme="lifted", precision=0, gamma=1e7, tol=1e-8,
                  max_iter=200, mu_init=0.1, warm_start=True, warm_mu=1e-4, warm_recenter=True,
-                 device=None):
+                 batch=0, device=None):
         import torch
         L = nat.lib()
         o = nat.ServerOptions()
@@ -27,6 +29,7 @@ class NMPCServer:
         o.max_iter, o.mu_init, o.warm_start = int(max_iter), float(mu_init), int(bool(warm_start))
         o.warm_mu = float(warm_mu)
         o.warm_recenter = int(bool(warm_recenter))
+        o.batch = int(batch)
         dev = torch.cuda.current_device() if device is None else int(device)
         h = ctypes.c_void_p()
         st = L.kkt_server_create(ctypes.byref(o), dev, ctypes.byref(h))

@@ -205,3 +205,49 @@ def test_autotuned_partition_solves_batch():
     for i, (p, pt, W, J) in enumerate(batch):
         assert oracle_eta(p, W, J, pt.sigma, 10.0, xs[i], ys[i], pt.rx, pt.ry) <= 1e-10
 
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_switched_off_instance_is_skipped_and_solves_to_zero(precision):
+    """kkt_batch_set_active: with instance 1 of three switched off, the
+    factorisation does no work for it (and does not fail on its values,
+    which have a negative diagonal), its zero right-hand side solves to
+    zero, and instances 0 and 2 get the answers they get alone (the step
+    agreement bar, 1e-8 relative); switched back on, instance 1 solves like
+    alone too."""
+    torch = torch_cuda()
+    import ctypes
+    from paper_2403_15913_gb300 import _native as nat
+    batch = make_batch([(8, 10), (16, 25), (8, 30)], seed0=20)
+    ref = [run_alone(p, pt, W, J, 10.0, precision=precision)[1:] for p, pt, W, J in batch]
+    s = batch_solver(batch, precision=precision)
+    L = nat.lib()
+    Wv = cat(torch, [W[2] for _, _, W, _ in batch])
+    Jv = cat(torch, [J[2] for _, _, _, J in batch])
+    sig = [pt.sigma.copy() for _, pt, _, _ in batch]
+    good_sig = cat(torch, sig)
+    sig[1][:] = -1.0                      # instance 1 would fail its first pivot
+    bad_sig = cat(torch, sig)
+    rx = [pt.rx.copy() for _, pt, _, _ in batch]
+    ry = [pt.ry.copy() for _, pt, _, _ in batch]
+    rx1, ry1 = [a.copy() for a in rx], [a.copy() for a in ry]
+    rx1[1][:] = 0.0
+    ry1[1][:] = 0.0
+    xo, yo = s.layout()
+    for on, sv, (bx, by) in (([1, 0, 1], bad_sig, (rx1, ry1)), ([1, 1, 1], good_sig, (rx, ry))):
+        act = np.array(on, np.int32)
+        assert L.kkt_batch_set_active(s._ctx, nat.ptr_i32(act)) == 0
+        assert s.factor_batch(Wv, Jv, sv, None, np.full(3, 10.0)) == 0
+        dx = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        dy = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+        assert s.solve(cat(torch, bx), cat(torch, by), dx, dy) == 0
+        for i in range(3):
+            xi = dx[xo[i]:xo[i + 1]].cpu().numpy()
+            yi = dy[yo[i]:yo[i + 1]].cpu().numpy()
+            if on[i]:
+                v, r = np.concatenate([xi, yi]), np.concatenate(ref[i])
+                assert np.max(np.abs(v - r)) <= 1e-8 * np.max(np.abs(r)), i
+            else:
+                assert not np.any(xi) and not np.any(yi)
+    assert L.kkt_batch_set_active(s._ctx, None) == 0
+    s.close()

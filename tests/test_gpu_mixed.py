@@ -262,3 +262,32 @@ def test_df64_ipm_matches_fp64_ipm():
     assert abs(out[2][0] - out[0][0]) <= 1
     assert abs(out[2][1] - out[0][1]) <= 1e-8 * abs(out[0][1])
     assert np.max(np.abs(out[2][2] - out[0][2])) <= 1e-6
+
+
+def test_set_precision_switches_between_the_analysed_and_fp64():
+    """kkt_set_precision: an FP32-analysed context factorises in FP64 after
+    kkt_set_precision(0) (no reduced-precision factor counted, the FP64
+    backward error) and in FP32 again after kkt_set_precision(1); an FP64
+    context accepts only 0."""
+    torch = torch_cuda()
+    from paper_2403_15913_gb300 import _native as nat
+    p, pt, W, J = instance(16, 30, 4, sigma_range=(1e-2, 1e2))
+    s = solver_for(p, W, J, scheme="lifted", precision=1, **OPTS)
+    L = nat.lib()
+    dx = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
+    vals = (to_dev(torch, W[2]), to_dev(torch, J[2]), to_dev(torch, pt.sigma))
+    for prec, want in ((0, 0), (1, 1), (0, 0)):
+        assert L.kkt_set_precision(s._ctx, prec) == 0
+        s.reset_stats()
+        assert s.factor(*vals, None, 10.0) == 0
+        assert s.solve(to_dev(torch, pt.rx), to_dev(torch, pt.ry), dx, dy) == 0
+        assert s.stats()["fp32_factors"] == want
+        assert s.info.status_detail == want
+        assert oracle_eta(p, W, J, pt.sigma, 10.0, dx.cpu().numpy(), dy.cpu().numpy(), pt.rx, pt.ry) <= 1e-10
+    assert L.kkt_set_precision(s._ctx, 2) == nat.KKT_ERR_ARG
+    s.close()
+    s64 = solver_for(p, W, J, scheme="lifted", **OPTS)
+    assert L.kkt_set_precision(s64._ctx, 1) == nat.KKT_ERR_ARG
+    assert L.kkt_set_precision(s64._ctx, 0) == 0
+    s64.close()

@@ -452,6 +452,28 @@ def run_ours(args, ws, rank, local):
     st = st.as_dict()
     ms = across_ranks(ms, "max", dist)
     ipm.set_profiling(False)
+    # with the one-graph step (FP64 supernodal factor) the refinement loop is
+    # timed as a whole inside the graph: K^{-1} itself is timed here, on the
+    # factor the last iteration left, through kkt_backsolve (gather, forward
+    # and backward solves, scatter), CUDA events on the launching stream
+    kinv_direct = None
+    if st["graph_steps"] > 0:
+        bvec = torch.randn(p.n, dtype=torch.float64, device="cuda")
+        xvec = torch.empty_like(bvec)
+        kms = []
+        for rep in range(13):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = nat.lib().kkt_backsolve(kctx, ctypes.c_void_p(bvec.data_ptr()), ctypes.c_void_p(xvec.data_ptr()),
+                                         ctypes.c_void_p(stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rc != nat.KKT_OK:
+                raise RuntimeError(f"kkt_backsolve failed with status {rc}")
+            if rep >= 3:
+                kms.append(e0.elapsed_time(e1))
+        kinv_direct = statistics.median(kms)
 
     # ---- end to end through the host-buffer C ABI: whole cold solves of the
     # same column submitted to a one-slot server (kkt_server_submit with the
@@ -482,7 +504,7 @@ def run_ours(args, ws, rank, local):
         return
     fcalls = max(1, st["factor_calls"])
     factor_ms = st["factor_ms"] / fcalls
-    kinv_ms = st["solve_ms"] / max(1, st["kinv_calls"])
+    kinv_ms = kinv_direct if kinv_direct is not None else st["solve_ms"] / max(1, st["kinv_calls"])
     f32 = args.precision == "fp32"
     peak, peak_src = alu_peak(local, f32)
     roof = {"kernel": ("block cyclic reduction (bcr_elim/bcr_update kernels)" if args.solver == "bcr" else
@@ -513,7 +535,9 @@ def run_ours(args, ws, rank, local):
                                 "factor": factor_ms, "kinv": kinv_ms,
                                 "assemble": st["assemble_ms"] / fcalls,
                                 "factor_calls_per_step": st["factor_calls"] / n_steps,
-                                "kinv_per_step": st["kinv_calls"] / n_steps},
+                                "kinv_per_step": st["kinv_calls"] / n_steps,
+                                "graph_steps_per_step": st["graph_steps"] / n_steps,
+                                "refinement_ms": (st["solve_ms"] / n_steps) if st["graph_steps"] > 0 else None},
                    "max_bwd_err": max(i["bwd_err"] for i in infos),
                    "refine_iters": [i["refine_iters"] for i in infos][:6],
                    "cg_iters": [i["cg_iters"] for i in infos][:6],

@@ -395,6 +395,7 @@ struct kkt_ipm {
     int it = 0;
     int launches = 0;   // kernels launched by the driver in the current step
     bool started = false;
+    bool graph_step = false;   // FP64 supernodal context: step 4 is one kkt_factor_solve graph launch
     cudaEvent_t ev[4] = {};
     // the iteration in progress: its report, the objective at its start,
     // and whether the report is complete (a result to hand back)
@@ -541,6 +542,7 @@ kkt_status create_impl(const double* params, const kkt_options* kopt, const kkt_
             delete p;
             return stt;
         }
+        p->graph_step = ko.precision == 0 && ko.solver == 0;
     }
     // CSC of J for J^T y
     std::vector<int> cp(n + 1, 0), ri(p->nnzJ), idx(p->nnzJ);
@@ -711,7 +713,10 @@ kkt_status begin_finish(kkt_ipm* p, cudaStream_t st) {
 }
 
 // Step 4 with the context's own KKT system: factor with the inertia-
-// correction ladder, then the refined solve.
+// correction ladder, then the refined solve -- with the FP64 supernodal
+// factor both as one graph launch (kkt_factor_solve: the refinement sweeps
+// run as a conditional loop on the device, one host wait), otherwise as
+// kkt_factor then kkt_solve.
 kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
     kkt_ipm_info& inf = p->cur;
     const int rel = p->opt.relaxed;
@@ -720,8 +725,12 @@ kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
     double delta = 0.0;
     kkt_status fs;
     while (true) {
-        fs = kkt_factor(p->kkt, p->Wv, p->Jv, p->sigma, rel ? p->D : nullptr, delta, st, &ki);
-        if (fs == KKT_OK) break;
+        if (p->graph_step)
+            fs = kkt_factor_solve(p->kkt, p->Wv, p->Jv, p->sigma, rel ? p->D : nullptr, &delta, p->rx, p->ry,
+                                  p->dx, p->dy, st, &ki);
+        else
+            fs = kkt_factor(p->kkt, p->Wv, p->Jv, p->sigma, rel ? p->D : nullptr, delta, st, &ki);
+        if (fs == KKT_OK || (p->graph_step && (fs == KKT_ERR_MAXIT || fs == KKT_ERR_STALL))) break;
         if (fs != KKT_ERR_NOT_SPD) return ierr(p, fs, std::string("kkt_factor: ") + kkt_last_error(p->kkt));
         if (delta == 0.0)
             delta = p->delta_last == 0.0 ? kDeltaW0 : std::max(kDeltaMin, kKappaWMinus * p->delta_last);
@@ -731,9 +740,11 @@ kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
     }
     if (delta > 0) p->delta_last = delta;
     inf.delta_x = delta;
-    kkt_status ss = kkt_solve(p->kkt, p->rx, p->ry, p->dx, p->dy, nullptr, st, &ki);
-    if (ss != KKT_OK && ss != KKT_ERR_MAXIT && ss != KKT_ERR_STALL)
-        return ierr(p, ss, std::string("kkt_solve: ") + kkt_last_error(p->kkt));
+    if (!p->graph_step) {
+        kkt_status ss = kkt_solve(p->kkt, p->rx, p->ry, p->dx, p->dy, nullptr, st, &ki);
+        if (ss != KKT_OK && ss != KKT_ERR_MAXIT && ss != KKT_ERR_STALL)
+            return ierr(p, ss, std::string("kkt_solve: ") + kkt_last_error(p->kkt));
+    }
     inf.refine_iters = ki.refine_iters;
     inf.cg_iters = ki.cg_iters;
     inf.bwd_err = ki.bwd_err;

@@ -224,7 +224,7 @@ struct kkt_ctx {
     cudaGraphExec_t step_exec = nullptr;
     const void* step_key[9] = {};
     cudaStream_t cap[3] = {};
-    cudaEvent_t step_ev[3] = {};
+    cudaEvent_t step_ev[4] = {};   // start, factor end, end, assembly end (factor kernels start)
     int* d_rst = nullptr;       // 4 per instance (state, stalled, sweeps, CG iterations)
     double* d_reta = nullptr;   // 2 per instance (eta, previous eta)
     int* d_rctl = nullptr;      // next sweep, CG iterations run
@@ -1454,8 +1454,11 @@ kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx,
     return KKT_OK;
 }
 
+// after_assembly (captured graphs only): an external event recorded between
+// the assembly and the factor kernels, for the graph's phase times
 template <typename T>
-kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st) {
+kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cudaStream_t st,
+                                  cudaEvent_t after_assembly = nullptr) {
     if (c->inst_on_pending) {
         CUDA_TRY(c, cudaMemcpyAsync(c->d_inst_on, c->h_inst_on, (size_t)c->nb * sizeof(int), cudaMemcpyHostToDevice,
                                     st));
@@ -1467,6 +1470,7 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
                                                              c->f_W, c->v_Js, c->f_sigma, delta_x,
                                                              c->f_dvec, Lx, c->panel, c->d_berr);
     span_end(c, sp_a, st);
+    if (after_assembly) CUDA_TRY(c, cudaEventRecordWithFlags(after_assembly, st, cudaEventRecordExternal));
     CUDA_TRY(c, cudaMemsetAsync(c->d_fail, 0x7f, (size_t)c->nb * sizeof(int), st));
     const FailSink fs{c->d_fail, c->nb > 1 ? c->d_col_inst : nullptr};
     const int sp_f = span_begin(c, 1, st);
@@ -2472,7 +2476,7 @@ kkt_status capture_step_body(kkt_ctx* c, const double* W, const double* J, const
         CUDA_TRY(c, cudaMemcpyAsync(c->d_inst_on, c->h_inst_on, (size_t)nb * sizeof(int), cudaMemcpyHostToDevice,
                                     st));
     c->inst_on_pending = false;
-    TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, 0.0, st));
+    TRY(enqueue_numeric_factor<double>(c, c->d_Lx, c->d_dinv, 0.0, st, c->step_ev[3]));
     c->step_fl = c->stats.factor_launches - f0;
     CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev_side, 0));
     CUDA_TRY(c, cudaEventRecordWithFlags(c->step_ev[1], st, cudaEventRecordExternal));
@@ -2635,7 +2639,9 @@ kkt_status factor_solve_impl(kkt_ctx* c, const double* d_Wval, const double* d_J
     c->stats.kinv_calls += c->opt.scheme == KKT_LIFTED ? sweeps : 2LL * sweeps + cgits;
     if (c->profiling) {
         float a = 0.f, b = 0.f;
-        if (cudaEventElapsedTime(&a, c->step_ev[0], c->step_ev[1]) == cudaSuccess) c->stats.factor_ms += a;
+        float a0 = 0;
+        if (cudaEventElapsedTime(&a0, c->step_ev[0], c->step_ev[3]) == cudaSuccess) c->stats.assemble_ms += a0;
+        if (cudaEventElapsedTime(&a, c->step_ev[3], c->step_ev[1]) == cudaSuccess) c->stats.factor_ms += a;
         if (cudaEventElapsedTime(&b, c->step_ev[1], c->step_ev[2]) == cudaSuccess) c->stats.solve_ms += b;
     }
     int nfail = 0, first_fail = -1, refine_max = 0, cg_total = 0;

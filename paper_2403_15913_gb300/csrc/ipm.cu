@@ -297,10 +297,13 @@ recover_kernel(int n, int m, int relaxed, Bounds B, double mu, double tau,
     store_partials<3>(v, ops, part, count, out);
 }
 
-__global__ void trial_kernel(int n, int m, int relaxed, double alpha, const double* __restrict__ x,
-                             const double* __restrict__ dx, const double* __restrict__ s,
-                             const double* __restrict__ ds, double* __restrict__ xt,
-                             double* __restrict__ st) {
+// Trial point at step alpha, or at *alpha_dev when it is given (the first
+// trial: the fraction-to-the-boundary step the recovery left on the device).
+__global__ void trial_kernel(int n, int m, int relaxed, double alpha, const double* __restrict__ alpha_dev,
+                             const double* __restrict__ x, const double* __restrict__ dx,
+                             const double* __restrict__ s, const double* __restrict__ ds,
+                             double* __restrict__ xt, double* __restrict__ st) {
+    if (alpha_dev) alpha = *alpha_dev;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) xt[i] = x[i] + alpha * dx[i];
         else if (relaxed) st[i - n] = s[i - n] + alpha * ds[i - n];
@@ -407,6 +410,7 @@ struct kkt_ipm {
     // trial step and the trials made
     double a_pr = 0, a_du = 0, dphi = 0, th = 0, ph = 0, alpha = 0;
     int ls = 0;
+    int trial_slot = 0;   // red[] slot of the trial being judged
 };
 
 namespace {
@@ -752,13 +756,32 @@ kkt_status step_kkt(kkt_ipm* p, cudaStream_t st) {
 }
 
 // Steps 5-7, split the same way: end_issue enqueues the recovery with the
-// fraction-to-the-boundary steps and the directional derivative (red[0..2])
-// and the measures at the current point (red[3..4]); end_search_begin reads
-// them and starts the filter line search.  Each trial enqueues its point,
-// model values, measures (red[0..1]) and objective (red[2]) (trial_issue)
-// and is judged after the synchronisation (trial_judge: 1 accepted, 0 try
-// the halved step, -1 no trial left); accept_issue enqueues the update, and
-// step_done closes the iteration once the stream has completed it.
+// fraction-to-the-boundary steps and the directional derivative (red[0..2]),
+// the measures at the current point (red[3..4]) and the first trial of the
+// line search, whose step alpha_pr the recovery leaves in red[0] (its
+// measures in red[5..6], its objective in red[7]); end_search_begin reads
+// them and starts the filter line search.  Each further trial enqueues its
+// point, model values, measures (red[0..1]) and objective (red[2])
+// (trial_issue); a trial is judged after the synchronisation (trial_judge:
+// 1 accepted, 0 try the halved step, -1 no trial left); accept_issue
+// enqueues the update, and step_done closes the iteration once the stream
+// has completed it.
+constexpr int kFirstTrial = 5;   // red[] slot of the first trial's measures
+
+// point, model values, measures into red[slot], red[slot + 1] and objective
+// into red[slot + 2] of the trial at step alpha (or *alpha_dev)
+kkt_status trial_enqueue(kkt_ipm* p, cudaStream_t st, const double* alpha_dev, int slot) {
+    const int n = p->n, m = p->m;
+    const int rel = p->opt.relaxed;
+    trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, p->alpha, alpha_dev, p->x, p->dx, p->s, p->ds,
+                                                      p->xt, p->st);
+    p->launches += 1;
+    ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
+    p->launches += 1;
+    measures(p, p->xt, p->st, p->ct, st, slot);
+    return objective(p, p->xt, st, slot + 2);
+}
+
 kkt_status end_issue(kkt_ipm* p, cudaStream_t st) {
     const int n = p->n, m = p->m;
     const int rel = p->opt.relaxed;
@@ -772,7 +795,8 @@ kkt_status end_issue(kkt_ipm* p, cudaStream_t st) {
                                        p->dvu, p->part, p->count, p->red);
     p->launches += 1;
     measures(p, p->x, p->s, p->c, st, 3);
-    return fetch_red(p, 5, st);
+    ITRY(trial_enqueue(p, st, p->red, kFirstTrial));
+    return fetch_red(p, kFirstTrial + 3, st);
 }
 
 void end_search_begin(kkt_ipm* p) {
@@ -783,26 +807,20 @@ void end_search_begin(kkt_ipm* p) {
     p->th = h[3];
     p->ph = p->fval - p->mu * h[4];
     p->alpha = p->a_pr;
-    p->ls = 0;
+    p->ls = 1;   // the first trial is in flight with the recovery
+    p->trial_slot = kFirstTrial;
 }
 
-// 6. filter line search: one trial step
+// 6. filter line search: the next trial step (after the first)
 kkt_status trial_issue(kkt_ipm* p, cudaStream_t st) {
-    const int n = p->n, m = p->m;
-    const int rel = p->opt.relaxed;
     ++p->ls;
-    trial_kernel<<<grid((long long)n + m), kT, 0, st>>>(n, m, rel, p->alpha, p->x, p->dx, p->s, p->ds,
-                                                      p->xt, p->st);
-    p->launches += 1;
-    ITRY(kktgb::tray_eval(p->params, p->x0v, p->xt, nullptr, 1.0, nullptr, nullptr, p->ct, nullptr, nullptr, st));
-    p->launches += 1;
-    measures(p, p->xt, p->st, p->ct, st, 0);
-    ITRY(objective(p, p->xt, st, 2));
+    p->trial_slot = 0;
+    ITRY(trial_enqueue(p, st, nullptr, 0));
     return fetch_red(p, 3, st);
 }
 
 int trial_judge(kkt_ipm* p) {
-    const double* h = p->h_red;
+    const double* h = p->h_red + p->trial_slot;
     const double tht = h[0], pht = h[2] - p->mu * h[1];
     const double th = p->th, ph = p->ph, alpha = p->alpha, dphi = p->dphi;
     bool ok = tht <= p->theta_max;
@@ -879,11 +897,11 @@ kkt_status step_end(kkt_ipm* p, cudaStream_t st) {
     ICUDA(p, cudaStreamSynchronize(st));
     end_search_begin(p);
     while (true) {
-        ITRY(trial_issue(p, st));
-        ICUDA(p, cudaStreamSynchronize(st));
         const int v = trial_judge(p);
         if (v > 0) break;
         if (v < 0) return search_failed(p);
+        ITRY(trial_issue(p, st));
+        ICUDA(p, cudaStreamSynchronize(st));
     }
     accept_issue(p, st);
     return step_done(p);
@@ -1360,15 +1378,7 @@ kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* i
         ++searching;
     }
     while (searching > 0) {
-        for (int i = 0; i < cnt; ++i) {
-            if (!b->searching[i]) continue;
-            const kkt_status r = trial_issue(b->mem[i], st);
-            if (r != KKT_OK) {
-                stop(i, r);
-                --searching;
-            }
-        }
-        TRY_B(b, sync());
+        // judge the trials in flight (the first came with the recovery)
         for (int i = 0; i < cnt; ++i) {
             if (!b->searching[i]) continue;
             const int v = trial_judge(b->mem[i]);
@@ -1380,6 +1390,16 @@ kkt_status kkt_ipm_batch_step(kkt_ipm_batch* b, cudaStream_t st, kkt_ipm_info* i
                 --searching;
             }
         }
+        if (searching == 0) break;
+        for (int i = 0; i < cnt; ++i) {
+            if (!b->searching[i]) continue;
+            const kkt_status r = trial_issue(b->mem[i], st);
+            if (r != KKT_OK) {
+                stop(i, r);
+                --searching;
+            }
+        }
+        TRY_B(b, sync());
     }
     for (int i = 0; i < cnt; ++i)
         if (b->stepping[i]) accept_issue(b->mem[i], st);

@@ -2601,8 +2601,8 @@ kkt_status factor_solve_impl(kkt_ctx* c, const double* d_Wval, const double* d_J
         if (!(std::isfinite(delta_x[i]) && delta_x[i] >= 0))
             return set_err(c, KKT_ERR_ARG, "bad delta_x of instance " + std::to_string(i));
     if (!c->hp_delta) CUDA_TRY(c, cudaMallocHost((void**)&c->hp_delta, (size_t)nb * sizeof(double)));
-    // the launch below reads hp_delta: no earlier replay may still be in flight
-    CUDA_TRY(c, cudaStreamSynchronize(st));
+    // the launch below reads hp_delta; no earlier replay is in flight, since
+    // every call waits for its own replay before it returns
     for (int i = 0; i < nb; ++i) c->hp_delta[i] = delta_x[i];
     c->factored = false;
     const bool hasD = c->opt.scheme == KKT_LIFTED && d_D;

@@ -90,8 +90,8 @@ typedef struct {
                             1: against C = D^{-1} (relaxed problem, Lifted
                             only)                                             */
     int subtree_cols;    /* subtrees of the supernodal tree with at most this
-                            many columns are factorised and solved by one
-                            CTA each (48); 0 disables                         */
+                            many columns (and at most 1024) are factorised
+                            and solved by one CTA each (48); 0 disables       */
     int precision;       /* 0: factor in FP64 (default).  1: factor in FP32,
                             2: in double-float (pairs of FP32 numbers, ~48
                             significand bits, on the FP32 pipe), and refine

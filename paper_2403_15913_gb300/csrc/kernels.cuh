@@ -1020,13 +1020,35 @@ factor_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __res
     }
 }
 
+// The columns of a subtree task form one range [lo, lo + w) (a subtree is
+// contiguous in postorder), and during a triangular solve only the task's
+// own supernodes write into it: the task keeps that slice of x in shared
+// memory (xs), updates inside the task are plain shared-memory adds in the
+// order the supernodes come, and only the rows above the task go to global
+// memory (atomics in the forward pass, reads in the backward pass).  No
+// device-wide fence between the task's supernodes; the slice is written
+// back at the end.  Returns w (0: the task list failed a bounds check).
+__device__ __forceinline__ int task_range(const Plan& P, const int* __restrict__ task_sn, int q0, int q1,
+                                          int& lo) {
+    if (q1 <= q0) return 0;
+    const int sa = task_sn[q0], sb = task_sn[q1 - 1];
+    if (!kkt_in(P.berr, sa >= 0 && sa < P.ns && sb >= 0 && sb < P.ns, kBcSupernode)) return 0;
+    lo = P.sn_f[sa];
+    return P.sn_f[sb] + P.sn_c[sb] - lo;
+}
+
 // Forward substitution over the supernodes task_sn[q0 .. q1) of one subtree
-// task, in postorder (D: shared memory for the c x c diagonal block).
+// task, in postorder (D: shared memory for the c x c diagonal block, xs:
+// for the task's slice of x).
 template <typename T>
 __device__ __forceinline__ void forward_subtree_task(const Plan& P, const int* __restrict__ task_sn, int q0,
                                                      int q1, const T* __restrict__ Lx, T* __restrict__ x, T* D,
-                                                     T* z) {
+                                                     T* z, T* xs) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    int lo = 0;
+    const int w = task_range(P, task_sn, q0, q1, lo);
+    if (w == 0) return;
+    for (int e = tid; e < w; e += nt) xs[e] = __ldcg(x + lo + e);
     for (int q = q0; q < q1; ++q) {
         const int s = task_sn[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
@@ -1036,11 +1058,12 @@ __device__ __forceinline__ void forward_subtree_task(const Plan& P, const int* _
         __syncthreads();
         if (tid < 32) {
             const int lane = tid;
-            T z0 = lane < c ? __ldcg(x + f + lane) : 0.0;
-            T z1 = lane + 32 < c ? __ldcg(x + f + lane + 32) : 0.0;
+            T* xf = xs + (f - lo);
+            T z0 = lane < c ? xf[lane] : T(0.0);
+            T z1 = lane + 32 < c ? xf[lane + 32] : T(0.0);
             warp_lower_solve(D, c, c, lane, z0, z1);   // unit lower triangular (normalised factor)
-            if (lane < c) { z[lane] = z0; x[f + lane] = z0; }
-            if (lane + 32 < c) { z[lane + 32] = z1; x[f + lane + 32] = z1; }
+            if (lane < c) { z[lane] = z0; xf[lane] = z0; }
+            if (lane + 32 < c) { z[lane + 32] = z1; xf[lane + 32] = z1; }
         }
         __syncthreads();
         const int* rows = P.rows + P.sn_rptr[s];
@@ -1048,38 +1071,47 @@ __device__ __forceinline__ void forward_subtree_task(const Plan& P, const int* _
             T sum = 0.0;
             for (int k = 0; k < c; ++k) sum = fma(A[c + i + (long long)k * r], z[k], sum);
             const int rw = rows[c + i];
-            if (kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow)) atomicAdd(x + rw, -sum);
+            if (rw >= lo && rw < lo + w)
+                xs[rw - lo] -= sum;   // rows of one supernode are distinct: no two threads meet
+            else if (kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow))
+                atomicAdd(x + rw, -sum);
         }
-        __threadfence();
         __syncthreads();
     }
+    for (int e = tid; e < w; e += nt) x[lo + e] = xs[e];
 }
 
 // Forward substitution over a subtree task (supernodes in postorder).
+// Shared memory: the widest diagonal block (dsz elements), then the slice.
 template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 forward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
                        const T* __restrict__ Lx, const T* __restrict__ dinv,
-                       T* __restrict__ x,
+                       T* __restrict__ x, int dsz,
     const int* __restrict__ active) {
     pdl_launch_dependents();   // the first staged level may stage its panels during the last wave
     KKT_RETURN_IF_INACTIVE(active);
     __shared__ T z[64];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* D = reinterpret_cast<T*>(smem_raw);   // diagonal block of the current supernode
-    forward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, x, D, z);
+    forward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, x, D, z, D + dsz);
 }
 
 // Backward substitution over the supernodes task_sn[q0 .. q1) of one subtree
 // task, in reverse postorder (dyn: shared memory for the diagonal block and
-// x of the rows below; part: one row of 64 per warp).
+// x of the rows below; xs: the task's slice of x; part: one row of 64 per
+// warp).
 template <typename T>
 __device__ __forceinline__ void backward_subtree_task(const Plan& P, const int* __restrict__ task_sn, int q0,
                                                       int q1, const T* __restrict__ Lx,
                                                       const T* __restrict__ dinv, T* __restrict__ x, T* dyn,
-                                                      T (*part)[64]) {
+                                                      T (*part)[64], T* xs) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    int lo = 0;
+    const int w = task_range(P, task_sn, q0, q1, lo);
+    if (w == 0) return;
+    for (int e = tid; e < w; e += nt) xs[e] = __ldcg(x + lo + e);
     for (int q = q1 - 1; q >= q0; --q) {
         const int s = task_sn[q];
         if (!kkt_in(P.berr, s >= 0 && s < P.ns, kBcSupernode)) continue;   // uniform over the CTA
@@ -1089,10 +1121,12 @@ __device__ __forceinline__ void backward_subtree_task(const Plan& P, const int* 
         const int rb = r - c;
         T* D = dyn;
         T* xb = dyn + c * c;
+        T* xf = xs + (f - lo);
         for (int e = tid; e < c * c; e += nt) D[e] = A[(e % c) + (long long)(e / c) * r];
         for (int i = tid; i < rb; i += nt) {
             const int rw = rows[c + i];
-            xb[i] = kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? __ldcg(x + rw) : T(0.0);
+            xb[i] = rw >= lo && rw < lo + w ? xs[rw - lo]
+                    : kkt_in(P.berr, rw >= 0 && rw < P.n, kBcSolveRow) ? __ldcg(x + rw) : T(0.0);
         }
         __syncthreads();
         if (c <= 32) {
@@ -1112,14 +1146,13 @@ __device__ __forceinline__ void backward_subtree_task(const Plan& P, const int* 
                 T t0 = 0.0, t1 = 0.0;
                 if (lane < c) {
                     t0 = part[0][lane];
-                    for (int w = 1; w < nw; ++w) t0 += part[w][lane];
+                    for (int w2 = 1; w2 < nw; ++w2) t0 += part[w2][lane];
                     const T di = dinv[f + lane];
-                    t0 = fma(__ldcg(x + f + lane) * di, di, -t0);   // u / l^2 - L21^T w
+                    t0 = fma(xf[lane] * di, di, -t0);   // u / l^2 - L21^T w
                 }
                 warp_upper_solve(D, c, c, lane, t0, t1);
-                if (lane < c) x[f + lane] = t0;
+                if (lane < c) xf[lane] = t0;
             }
-            __threadfence();
             __syncthreads();
             continue;
         }
@@ -1134,19 +1167,19 @@ __device__ __forceinline__ void backward_subtree_task(const Plan& P, const int* 
         __syncthreads();
         if (tid < 32) {
             T t0 = 0.0, t1 = 0.0;
-            for (int w = 0; w < nw; ++w) { t0 += part[w][lane]; t1 += part[w][lane + 32]; }
+            for (int w2 = 0; w2 < nw; ++w2) { t0 += part[w2][lane]; t1 += part[w2][lane + 32]; }
             // L^T w = z with L = Lhat diag(l): Lhat^T w = z / l = u / l^2
             const T di0 = lane < c ? dinv[f + lane] : 0.0;
             const T di1 = lane + 32 < c ? dinv[f + lane + 32] : 0.0;
-            t0 = lane < c ? __ldcg(x + f + lane) * di0 * di0 - t0 : 0.0;
-            t1 = lane + 32 < c ? __ldcg(x + f + lane + 32) * di1 * di1 - t1 : 0.0;
+            t0 = lane < c ? xf[lane] * di0 * di0 - t0 : 0.0;
+            t1 = lane + 32 < c ? xf[lane + 32] * di1 * di1 - t1 : 0.0;
             warp_upper_solve(D, c, c, lane, t0, t1);   // unit upper triangular
-            if (lane < c) x[f + lane] = t0;
-            if (lane + 32 < c) x[f + lane + 32] = t1;
+            if (lane < c) xf[lane] = t0;
+            if (lane + 32 < c) xf[lane + 32] = t1;
         }
-        __threadfence();
         __syncthreads();
     }
+    for (int e = tid; e < w; e += nt) x[lo + e] = xs[e];
 }
 
 // Backward substitution over a subtree task (supernodes in reverse postorder).
@@ -1154,13 +1187,14 @@ template <typename T>
 __global__ void __launch_bounds__(kSubtreeThreads)
 backward_subtree_kernel(Plan P, const int* __restrict__ task_ptr, const int* __restrict__ task_sn,
                         const T* __restrict__ Lx, const T* __restrict__ dinv,
-                        T* __restrict__ x,
+                        T* __restrict__ x, int dsz,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
     __shared__ T part[kSubtreeThreads / 32][64];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* dyn = reinterpret_cast<T*>(smem_raw);   // [diagonal block | x of the rows below]
-    backward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, dinv, x, dyn, part);
+    T* dyn = reinterpret_cast<T*>(smem_raw);   // [diagonal block | x of the rows below] (dsz), then the slice
+    backward_subtree_task(P, task_sn, task_ptr[blockIdx.x], task_ptr[blockIdx.x + 1], Lx, dinv, x, dyn, part,
+                          dyn + dsz);
 }
 
 // ------------------------------------------------------------- dataflow solves
@@ -1192,6 +1226,7 @@ struct Flow {
     int* herr;           // mapped host word: a wait gave up
     int first, nitems;   // the items [first, nitems) take part (first > 0: the subtree tasks run
                          // in their own launches, before the forward and after the backward)
+    int task_xs_fwd, task_xs_bwd;   // shared-memory offset (elements) of a task's slice of x
 };
 constexpr int kFlowThreads = 128;
 constexpr int kFlowSpinLimit = 1 << 24;
@@ -1264,7 +1299,7 @@ forward_flow_kernel(Plan P, Flow F, const int* __restrict__ task_ptr, const int*
         const int it = F.item[i];
         if (it < 0) {
             const int b = -it - 1;
-            forward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, x, S, z);
+            forward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, x, S, z, S + F.task_xs_fwd);
         } else if (kkt_in(P.berr, it < P.ns, kBcSupernode)) {
             const int c = P.sn_c[it], r = P.sn_r[it], ld = staged_ld(r);
             stage_panel(Lx + P.sn_lptr[it], c, r, ld, S);
@@ -1308,7 +1343,8 @@ backward_flow_kernel(Plan P, Flow F, const int* __restrict__ task_ptr, const int
             const int b = -it - 1;
             if (tid == 0 && up >= 0) flow_wait(F.done + up, epoch, F.herr);
             __syncthreads();
-            backward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, dinv, x, S, part);
+            backward_subtree_task(P, task_sn, task_ptr[b], task_ptr[b + 1], Lx, dinv, x, S, part,
+                                  S + F.task_xs_bwd);
         } else if (kkt_in(P.berr, it < P.ns, kBcSupernode)) {
             const int c = P.sn_c[it], r = P.sn_r[it], ld = staged_ld(r);
             T* xb = S + (size_t)ld * c;

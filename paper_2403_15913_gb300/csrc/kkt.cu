@@ -89,6 +89,7 @@ struct kkt_ctx {
     int n_norm_fused = 0;
     int* d_norm_list_fused = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
+    long long task_max_cols = 0;   // widest column range of a subtree task (its slice of x in the solves)
     // dataflow triangular solves (staged_solve = 2): work items in
     // topological order, the item each one feeds and its number of feeders,
     // arrival counters, epochs and tickets; the mapped host word a wait that
@@ -556,6 +557,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     std::vector<int> sub_cols(ns, 0);
     std::vector<char> small_ok(ns, 1);
     const long long kTaskPanelCap = 6144;   // panel entries kept in the task CTA's smem
+    const int kTaskColsCap = 1024;          // columns of a task (its slice of x in the solves' smem)
     for (int s = 0; s < ns; ++s) {
         sub_cols[s] += sn_c[s];
         if ((long long)sn_r[s] * sn_c[s] > kTaskPanelCap) small_ok[s] = 0;
@@ -567,7 +569,8 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     }
     std::vector<char> in_task(ns, 0);
     for (int s = 0; s < ns; ++s)
-        in_task[s] = c->opt.subtree_cols > 0 && sub_cols[s] <= c->opt.subtree_cols && small_ok[s];
+        in_task[s] = c->opt.subtree_cols > 0 && sub_cols[s] <= std::min(c->opt.subtree_cols, kTaskColsCap) &&
+                     small_ok[s];
     std::vector<int> task_of(ns, -1), task_root;
     for (int s = ns - 1; s >= 0; --s) {
         if (!in_task[s]) continue;
@@ -595,6 +598,16 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
                 c->task_max_ccrb = std::max(c->task_max_ccrb,
                                             (long long)sn_c[s] * sn_c[s] + sn_r[s] - sn_c[s]);
             }
+    }
+    // a task's columns are one range (a subtree in postorder): the solves
+    // keep that slice of x in shared memory
+    for (int b = 0; b < c->ntasks; ++b) {
+        const int q0 = task_ptr[b], q1 = task_ptr[b + 1];
+        long long cols = 0;
+        for (int q = q0; q < q1; ++q) cols += sn_c[task_sn[q]];
+        const long long w = (long long)sn_f[task_sn[q1 - 1]] + sn_c[task_sn[q1 - 1]] - sn_f[task_sn[q0]];
+        if (q1 <= q0 || w != cols) return set_err(c, KKT_ERR_INTERNAL, "subtree task columns are not contiguous");
+        c->task_max_cols = std::max(c->task_max_cols, w);
     }
     std::vector<int> level(ns, 0);
     for (int s = 0; s < ns; ++s) {
@@ -858,8 +871,8 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             nchild[up[i]]++;
             if (item[i] >= 0) nchild_lv[up[i]]++;
         }
-        c->flow_fwd_elems = c->task_max_cc;
-        c->flow_bwd_elems = c->task_max_ccrb;
+        c->flow_fwd_elems = c->task_max_cc + c->task_max_cols;
+        c->flow_bwd_elems = c->task_max_ccrb + c->task_max_cols;
         c->flow_bwd_ints = 0;
         for (int s : c->h_lvl_sn) {
             const long long ldc = (long long)staged_ld(sn_r[s]) * sn_c[s], rb = sn_r[s] - sn_c[s];
@@ -964,6 +977,10 @@ void set_backward_smem_limit() {
                          kBackwardSmemBytes);
     cudaFuncSetAttribute(forward_level_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kStagedSmemBytes);
+    // subtree tasks: diagonal block (and rows below) of <= 6144 entries plus
+    // the task's slice of x (<= 1024 columns)
+    cudaFuncSetAttribute(forward_subtree_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(backward_subtree_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(backward_level_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kStagedSmemBytes);
 }
@@ -1015,7 +1032,8 @@ bool flow_levels_only(const kkt_ctx* c) { return c->opt.staged_solve == 3 && c->
 Flow flow_of(const kkt_ctx* c) {
     const bool lv = flow_levels_only(c);
     return Flow{c->d_flow_item, c->d_flow_up, lv ? c->d_flow_nchild_lv : c->d_flow_nchild, c->d_flow_cnt,
-                c->d_flow_done, c->d_flow_ctrl, c->d_flow_err, lv ? c->ntasks : 0, c->flow_items};
+                c->d_flow_done, c->d_flow_ctrl, c->d_flow_err, lv ? c->ntasks : 0, c->flow_items,
+                (int)c->task_max_cc, (int)c->task_max_ccrb};
 }
 
 // Dataflow solves are used with staged_solve = 2 (3: levels only) when the
@@ -1070,8 +1088,9 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
         const Flow F = flow_of(c);
         const bool tasks = flow_levels_only(c);
         if (tasks)
-            forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
-                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+            forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads,
+                                        (size_t)(c->task_max_cc + c->task_max_cols) * sizeof(T), st>>>(
+                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, (int)c->task_max_cc, active);
         if (F.nitems > F.first) {
             forward_flow_kernel<T><<<c->flow_grid[p][0], kFlowThreads, flow_fwd_bytes<T>(c), st>>>(
                 c->plan, F, c->d_task_ptr, c->d_task_sn, Lx, xp, active);
@@ -1079,13 +1098,15 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
                 c->plan, F, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
         }
         if (tasks)
-            backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(T), st>>>(
-                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+            backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads,
+                                         (size_t)(c->task_max_ccrb + c->task_max_cols) * sizeof(T), st>>>(
+                c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, (int)c->task_max_ccrb, active);
         return;
     }
     if (c->ntasks > 0)
-        forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_cc * sizeof(T), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+        forward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads,
+                                    (size_t)(c->task_max_cc + c->task_max_cols) * sizeof(T), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, (int)c->task_max_cc, active);
     // Levels with more supernodes than 256-thread CTAs keep resident at once
     // (six per SM by registers) run 128-thread CTAs with the diagonal block
     // sized for the level's widest supernode: one wave instead of two.
@@ -1132,8 +1153,9 @@ void enqueue_triangular_solves(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cu
             backward_level_kernel<T, false, false><<<cnt, nt, sm, st>>>(c->plan, lsn, Lx, dinv, xp, dsz, active);
     }
     if (c->ntasks > 0)
-        backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads, (size_t)c->task_max_ccrb * sizeof(T), st>>>(
-            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, active);
+        backward_subtree_kernel<T><<<c->ntasks, kSubtreeThreads,
+                                     (size_t)(c->task_max_ccrb + c->task_max_cols) * sizeof(T), st>>>(
+            c->plan, c->d_task_ptr, c->d_task_sn, Lx, dinv, xp, (int)c->task_max_ccrb, active);
 }
 
 void enqueue_triangular_solves(kkt_ctx* c, double* xp, cudaStream_t st, const int* active) {

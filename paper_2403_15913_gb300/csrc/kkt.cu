@@ -646,7 +646,22 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
     c->lvl_syrk_ptr.assign(nlev + 1, 0);
     for (int l = 0; l < nlev; ++l) {
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
-        c->lvl_split[l] = cnt < kSplitLevel;
+        // Split launches spread a supernode over many CTAs.  They serve levels
+        // with fewer supernodes than SMs can hold, and levels where one
+        // supernode would straggle: with one CTA per supernode the largest
+        // panel runs on one SM (two FP64 FMAs a clock), so when its panel
+        // work exceeds twice the level's average work per SM it alone would
+        // set the level's time (a few separators among many tiny supernodes).
+        double fl_max = 0.0, fl_sum = 0.0;
+        for (int q = c->h_lvl_ptr[l]; q < c->h_lvl_ptr[l + 1]; ++q) {
+            const int s = c->h_lvl_sn[q];
+            const double cc = sn_c[s], rr = sn_r[s];
+            // sum over the columns j < c of (r - j)^2: the panel's FMA count x 2
+            const double f = cc * rr * rr - rr * cc * (cc - 1.0) + (cc - 1.0) * cc * (2.0 * cc - 1.0) / 6.0;
+            fl_max = std::max(fl_max, f);
+            fl_sum += f;
+        }
+        c->lvl_split[l] = cnt < kSplitLevel || fl_max > 2.0 * fl_sum / kNumSMs;
         c->lvl_fused[l] = c->lvl_split[l] && c->lvl_max_c[l] <= kFusedMaxC && c->lvl_max_rb[l] <= kFusedMaxRb;
         if (c->lvl_split[l]) {
             // SYRK tasks: chunks of the packed lower triangle of each

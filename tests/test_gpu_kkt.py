@@ -79,6 +79,10 @@ def _dense_factor_parity(p, pt, W, J, delta_x, D, opts):
     (32, 40, dict(leaf_size=64, relax_cols=48, relax_zeros=1024, max_width=64)),
     (7, 13, dict(leaf_size=16, relax_cols=16, relax_zeros=40, max_width=8)),
     (32, 20, dict(leaf_size=64, relax_cols=0, relax_zeros=0, max_width=64)),
+    # 64-column separators: the split levels (diagonal block, lanes-over-rows
+    # TRSM, SYRK) and the narrow-level cluster kernel
+    (64, 24, OPTS),
+    (64, 100, OPTS),
 ])
 def test_factor_matches_oracle(k, T, opts):
     p, pt, W, J = instance(k, T, seed=1, sigma_range=(1e-2, 1e2))

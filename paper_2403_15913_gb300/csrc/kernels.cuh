@@ -391,18 +391,21 @@ __device__ __forceinline__ void square_factor(T* A, int f, int c, FailSink fail,
     }
 }
 
-// Cholesky of a square c x c block, c <= 32, with look-ahead: warp 0 holds
-// the critical path (lanes = rows): at step j it applies column j to column
-// j + 1, takes the pivot (every lane computes the same reciprocal square
-// root, so the broadcast costs one shuffle), scales and publishes column
-// j + 1, while warps 1-3 apply column j to the columns beyond j + 1 (pairs
-// from the column-descending table, active pairs a prefix).  One barrier per
-// column; warps 4 and up only join the barriers, so no update instruction
-// competes with warp 0 for its sub-partition's FP64 unit.
+// Cholesky of a square c x c block, c <= 64, with look-ahead: warp 0 holds
+// the critical path (lanes = rows, two per lane when c > 32): at step j it
+// applies column j to column j + 1, takes the pivot (every lane computes the
+// same reciprocal square root, so the broadcast costs one shuffle), scales
+// and publishes column j + 1, while warps 1-3 apply column j to the columns
+// beyond j + 1 (pairs from the column-descending table, active pairs a
+// prefix).  One barrier per column; warps 4 and up only join the barriers,
+// so no update instruction competes with warp 0 for its sub-partition's FP64
+// unit.  Every entry receives the updates of columns 0, 1, ... in order with
+// the same FMAs as square_factor, so the result is the same.
 template <typename T>
 __device__ __forceinline__ void square_factor_lookahead(T* A, int f, int c, FailSink fail, T* dinv) {
-    __shared__ short2 tab[32 * 31 / 2];
+    __shared__ short2 tab[64 * 63 / 2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool two = c > 32;   // a second row per lane of warp 0 (uniform)
     for (int e = tid; e < c * c; e += blockDim.x) {
         const int ii = e % c, kk = e / c;
         if (kk >= 1 && ii >= kk) tab[(c - 1 - kk) * (c - kk) / 2 + (ii - kk)] = make_short2((short)ii, (short)kk);
@@ -417,16 +420,24 @@ __device__ __forceinline__ void square_factor_lookahead(T* A, int f, int c, Fail
         const T inv = pivot_rsqrt(d);
         if (lane == 0) dinv[f] = inv;
         if (lane > 0 && lane < c) A[lane] = a * inv;
+        if (two && lane + 32 < c) A[lane + 32] *= inv;
     }
     __syncthreads();
     for (int j = 0; j + 1 < c; ++j) {
         const T* colj = A + j * c;
         if (warp == 0) {
             T* col1 = A + (j + 1) * c;
+            const T cj1 = colj[j + 1];
             const bool below = lane > j && lane < c;
             T a = below ? col1[lane] : T(0.0);
-            a = fma(-(below ? colj[lane] : T(0.0)), colj[j + 1], a);
-            T d = __shfl_sync(0xffffffffu, a, j + 1);
+            a = fma(-(below ? colj[lane] : T(0.0)), cj1, a);
+            T a2 = T(0.0);
+            if (two) {
+                const bool below2 = lane + 32 > j && lane + 32 < c;
+                a2 = below2 ? col1[lane + 32] : T(0.0);
+                a2 = fma(-(below2 ? colj[lane + 32] : T(0.0)), cj1, a2);
+            }
+            T d = j + 1 < 32 ? __shfl_sync(0xffffffffu, a, j + 1) : __shfl_sync(0xffffffffu, a2, j + 1 - 32);
             if (!pivot_ok(d)) {
                 if (lane == 0) fail.report(f + j + 1);
                 d = 1.0;
@@ -434,6 +445,7 @@ __device__ __forceinline__ void square_factor_lookahead(T* A, int f, int c, Fail
             const T inv = pivot_rsqrt(d);
             if (lane == 0) dinv[f + j + 1] = inv;
             if (lane > j + 1 && lane < c) col1[lane] = a * inv;
+            if (two && lane + 32 > j + 1 && lane + 32 < c) col1[lane + 32] = a2 * inv;
         } else if (warp < 4) {
             const int active = (c - 2 - j) * (c - 1 - j) / 2;
             for (int e = tid - 32; e < active; e += 96) {
@@ -459,7 +471,7 @@ potrf_diag_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restrict__ Lx,
     T* g = Lx + P.sn_lptr[s];
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) sm[e] = g[(e % c) + (long long)(e / c) * r];
     __syncthreads();
-    if (c <= 32) square_factor_lookahead(sm, f, c, fail, dinv);
+    if (c <= 64) square_factor_lookahead(sm, f, c, fail, dinv);
     else square_factor(sm, f, c, fail, dinv);
     // the unused upper triangle receives the transpose of L11 diag(dinv)
     // (column-scaled by the reciprocal pivots), once, for the TRSM CTAs
@@ -605,7 +617,7 @@ narrow_level_cluster_kernel(Plan P, const int* __restrict__ lvl_sn, T* __restric
     if (rank == 0) {
         for (int e = tid; e < c * c; e += nt) sm[e] = g[(e % c) + (long long)(e / c) * r];
         __syncthreads();
-        if (c <= 32) square_factor_lookahead(sm, f, c, fail, dinv);
+        if (c <= 64) square_factor_lookahead(sm, f, c, fail, dinv);
         else square_factor(sm, f, c, fail, dinv);
         for (int e = tid; e < c * c; e += nt) {   // transpose of L11 diag(dinv) above the diagonal
             const int row = e % c, col = e / c;

@@ -1397,6 +1397,37 @@ __global__ void scatter_kernel(int n, const int* __restrict__ idx, const Tin* __
 }
 
 // ------------------------------------------------------------- sparse BLAS
+// (J^T (Dscale o a_y))_i over the column i of J (Dscale NULL -> Dconst):
+// entries in batches -- index loads, then value loads, then the FMAs
+__device__ __forceinline__ double jt_row_dot(int i, const int* __restrict__ jt_ptr,
+                                             const int* __restrict__ jt_row, const int* __restrict__ jt_idx,
+                                             const double* __restrict__ J, const double* __restrict__ ay,
+                                             const double* __restrict__ Dscale, double Dconst) {
+    double s = 0.0;
+    const int q0 = jt_ptr[i], q1 = jt_ptr[i + 1];
+    for (int q = q0; q < q1; q += kGatherBatch) {
+        int ri[kGatherBatch], ii[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const bool ok = q + u < q1;
+            ri[u] = ok ? jt_row[q + u] : 0;
+            ii[u] = ok ? jt_idx[q + u] : 0;
+        }
+        double jv[kGatherBatch], dv[kGatherBatch], yv[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const bool ok = q + u < q1;
+            jv[u] = ok ? J[ii[u]] : 0.0;
+            dv[u] = ok && Dscale ? Dscale[ri[u]] : Dconst;
+            yv[u] = ok ? ay[ri[u]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u)
+            if (q + u < q1) s = fma(jv[u] * dv[u], yv[u], s);
+    }
+    return s;
+}
+
 // out_x = a_x + alpha * J^T (Dscale o a_y)    (Dscale NULL -> Dconst)
 __global__ void jt_axpy_kernel(int n, const int* __restrict__ jt_ptr, const int* __restrict__ jt_row,
                                const int* __restrict__ jt_idx, const double* __restrict__ J,
@@ -1405,31 +1436,52 @@ __global__ void jt_axpy_kernel(int n, const int* __restrict__ jt_ptr, const int*
                                double* __restrict__ out,
     const int* __restrict__ active) {
     KKT_RETURN_IF_INACTIVE(active);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        // entries in batches: index loads, then value loads, then the FMAs
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (ax ? ax[i] : 0.0) + alpha * jt_row_dot(i, jt_ptr, jt_row, jt_idx, J, ay, Dscale, Dconst);
+}
+
+// The CG iteration's J^T p written straight into the permuted vector of the
+// solves: xp[i] = (J^T p)_{perm[i]} (the values jt_axpy_kernel and a gather
+// would give, without the intermediate vector and the extra launch).
+template <typename T>
+__global__ void jt_gather_kernel(int n, const int* __restrict__ perm, const int* __restrict__ jt_ptr,
+                                 const int* __restrict__ jt_row, const int* __restrict__ jt_idx,
+                                 const double* __restrict__ J, const double* __restrict__ p,
+                                 T* __restrict__ xp, const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        xp[i] = (T)(0.0 + 1.0 * jt_row_dot(perm[i], jt_ptr, jt_row, jt_idx, J, p, nullptr, 1.0));
+}
+
+// ... and J K^{-1} J^T p read from the permuted solution: out_r = (J x)_r
+// with x_v = xp[iperm[v]] (the values a scatter and j_apply_kernel would
+// give, in the same order).
+template <typename T>
+__global__ void j_apply_perm_kernel(int m, const int* __restrict__ j_ptr, const int* __restrict__ j_col,
+                                    const double* __restrict__ J, const int* __restrict__ iperm,
+                                    const T* __restrict__ xp, double* __restrict__ out,
+                                    const int* __restrict__ active) {
+    KKT_RETURN_IF_INACTIVE(active);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const int q0 = j_ptr[r], q1 = j_ptr[r + 1];
         double s = 0.0;
-        const int q0 = jt_ptr[i], q1 = jt_ptr[i + 1];
         for (int q = q0; q < q1; q += kGatherBatch) {
-            int ri[kGatherBatch], ii[kGatherBatch];
+            int ic[kGatherBatch];
+            double a[kGatherBatch];
 #pragma unroll
             for (int u = 0; u < kGatherBatch; ++u) {
                 const bool ok = q + u < q1;
-                ri[u] = ok ? jt_row[q + u] : 0;
-                ii[u] = ok ? jt_idx[q + u] : 0;
+                ic[u] = ok ? iperm[j_col[q + u]] : 0;
+                a[u] = ok ? J[q + u] : 0.0;
             }
-            double jv[kGatherBatch], dv[kGatherBatch], yv[kGatherBatch];
+            double b[kGatherBatch];
 #pragma unroll
-            for (int u = 0; u < kGatherBatch; ++u) {
-                const bool ok = q + u < q1;
-                jv[u] = ok ? J[ii[u]] : 0.0;
-                dv[u] = ok && Dscale ? Dscale[ri[u]] : Dconst;
-                yv[u] = ok ? ay[ri[u]] : 0.0;
-            }
+            for (int u = 0; u < kGatherBatch; ++u) b[u] = q + u < q1 ? (double)xp[ic[u]] : 0.0;
 #pragma unroll
             for (int u = 0; u < kGatherBatch; ++u)
-                if (q + u < q1) s = fma(jv[u] * dv[u], yv[u], s);
+                if (q + u < q1) s = fma(a[u], b[u], s);
         }
-        out[i] = (ax ? ax[i] : 0.0) + alpha * s;
+        out[r] = 1.0 * s;
     }
 }
 

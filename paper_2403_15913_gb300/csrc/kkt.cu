@@ -1281,17 +1281,21 @@ template <typename T>
 void enqueue_cg_iteration(kkt_ctx* c, const T* Lx, const T* dinv, T* xp, cudaStream_t st) {
     const int n = c->n, m = c->m;
     const int* act = c->d_cg;
-    jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->v_J,
-                                                     nullptr, c->w_p, nullptr, 1.0, 1.0, c->w_tn, act);
     if (c->opt.solver == 1) {
+        jt_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx, c->v_J,
+                                                         nullptr, c->w_p, nullptr, 1.0, 1.0, c->w_tn, act);
         enqueue_bcr_solve(c, c->w_tn, st, act);
+        j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
+                                                         nullptr, nullptr, 1.0, c->w_sp, act);
     } else {
-        gather_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->w_tn, xp, act);
+        // J^T p into the permuted vector, the solves, J x from it: the
+        // permutations folded into the products
+        jt_gather_kernel<T><<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, c->d_jt_ptr, c->d_jt_row, c->d_jt_idx,
+                                                              c->v_J, c->w_p, xp, act);
         enqueue_triangular_solves<T>(c, Lx, dinv, xp, st, act);
-        scatter_kernel<<<grid_for(n), kThreads, 0, st>>>(n, c->d_perm, xp, c->w_tn, act);
+        j_apply_perm_kernel<T><<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->d_iperm,
+                                                                 xp, c->w_sp, act);
     }
-    j_apply_kernel<<<grid_for(m), kThreads, 0, st>>>(m, c->d_j_ptr, c->d_j_col, c->v_J, c->w_tn,
-                                                     nullptr, nullptr, 1.0, c->w_sp, act);
     seg_dot(c, c->w_p, c->w_sp, 2, st, act);
     if (c->nch_y > 0)
         cg_update_xr_kernel<<<c->nch_y, kThreads, 0, st>>>(c->d_ch_y, c->d_cgs, c->d_cgi, c->w_p, c->w_sp,

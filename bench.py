@@ -53,7 +53,7 @@ PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 # in this file together with the SHA-256 of the kernel sources it measured;
 # when the sources differ the counters are stale and roofline.traffic is null
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "factor_dram_traffic.txt")
-TRAFFIC_SOURCES = ("kernels.cuh", "kkt.cu", "fp64_lean.cuh", "sparse_dot.cuh")
+TRAFFIC_SOURCES = ("kernels.cuh", "fused_factor.cuh", "kkt.cu", "fp64_lean.cuh", "sparse_dot.cuh")
 
 
 def kernel_source_digest():

@@ -190,3 +190,25 @@ def test_member_joining_a_running_batch_follows_the_single_ipm():
         assert np.max(np.abs(b.members[i].get()[0].cpu().numpy() - g.get()[0].cpu().numpy())) <= 1e-6
         g.close()
     b.close()
+
+
+def test_batched_hykkt_server_follows_the_per_instance_server():
+    """HyKKT in batched serving (CG per instance on the union's factor):
+    each request takes the per-instance server's iterations to its optimum."""
+    torch_cuda()
+    from paper_2403_15913_gb300 import NMPCServer
+    rng = np.random.default_rng(13)
+    params = _clients(rng, 5)
+    x0s = [x0_for(p.k, 40 + i) for i, p in enumerate(params)]
+    out = {}
+    for name, kw in (("single", dict(slots=2)), ("batched", dict(slots=2, batch=3))):
+        s = NMPCServer(scheme="hykkt", **kw)
+        cl = [s.add_client(p.as_array()) for p in params]
+        tk = [s.submit(cl[i], x0s[i], keep_solution=True) for i in range(5)]
+        out[name] = [s.wait(t, want_solution=True) for t in tk]
+        s.close()
+    for (ra, xa), (rb, xb) in zip(out["single"], out["batched"]):
+        assert ra["status"] == 1 and rb["status"] == 1
+        assert ra["iters"] == rb["iters"], (ra["iters"], rb["iters"])
+        assert abs(ra["objective"] - rb["objective"]) <= 1e-8 * abs(ra["objective"])
+        assert np.max(np.abs(xa - xb)) <= 1e-6

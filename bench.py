@@ -141,6 +141,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="batch workload: pick the supernode partition with kkt_autotune_batch first")
     ap.add_argument("--sigma", default="1e-6,1e6", help="kkt workload: Sigma_x range")
+    ap.add_argument("--staged-solve", type=int, default=None,
+                    help="triangular solve variant (kkt_options.staged_solve; default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="batch workload: kkt_factor_batch + kkt_solve instead of the one-graph step")
@@ -386,9 +388,10 @@ def run_ours(args, ws, rank, local):
     # replicas: every rank solves its own instance (horizon-shifted start)
     p = TrayParams(k=args.k, T=args.T)
     t0 = time.perf_counter()
+    extra = {} if args.staged_solve is None else {"staged_solve": args.staged_solve}
     ipm = IPMSolver(p.as_array(), scheme=args.scheme, gamma=args.gamma, max_cg=500,
                     precision=PREC[args.precision],
-                    solver=1 if args.solver == "bcr" else 0, block=2 * args.k + 1)
+                    solver=1 if args.solver == "bcr" else 0, block=2 * args.k + 1, **extra)
     t_analyse = time.perf_counter() - t0
     kctx = nat.lib().kkt_ipm_kkt(ipm._h)
     ns, nnzL, panel, rows, lev, fl = (ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(),

@@ -86,6 +86,10 @@ struct kkt_ctx {
     // levels factorised by factor_fused_kernel (FP64 and FP32 panels), and
     // the normalisation list that leaves their supernodes out
     std::vector<char> lvl_fused;
+    // co-resident clusters of factor_fused_cluster_kernel for K = 2, 4, 8
+    // CTAs (index log2 K; 0 = not queried): a level takes K only if all its
+    // clusters run in one wave
+    int fused_clusters[4] = {0, 0, 0, 0};
     int n_norm_fused = 0;
     int* d_norm_list_fused = nullptr;
     long long task_max_rc = 0, task_max_cc = 0, task_max_ccrb = 0;
@@ -1460,13 +1464,20 @@ constexpr bool kFusedType = std::is_same<T, double>::value || std::is_same<T, fl
 
 // One split level of supernodes with <= 32 columns and <= 128 rows below:
 // one CTA per supernode when the level fills the SMs, otherwise a cluster of
-// K = 2, 4 or 8 CTAs per supernode sharing its rows and Schur pairs.
+// K = 2, 4 or 8 CTAs per supernode sharing its rows and Schur pairs, K the
+// largest for which the level's clusters are resident at once (clusters of
+// 8 one-per-SM CTAs: 15 at a time on GB300, so a level of 16 supernodes
+// takes K = 4 in one wave rather than K = 8 in two).
 template <typename T>
 kkt_status launch_fused_level(kkt_ctx* c, int l, int cnt, const int* lsn, T* Lx, FailSink fs, T* dinv,
                               cudaStream_t st) {
     const size_t mc = (size_t)c->lvl_max_c[l], mrb = (size_t)c->lvl_max_rb[l];
     int K = 1;
-    while (K < kFusedClusterMax && (long long)cnt * K * 2 <= kNumSMs) K *= 2;
+    while (K < kFusedClusterMax && (long long)cnt * K * 2 <= kNumSMs) {
+        const int q = c->fused_clusters[K == 1 ? 1 : K == 2 ? 2 : 3];
+        if (q > 0 && cnt > q) break;   // clusters of 2K CTAs would not all be resident at once
+        K *= 2;
+    }
     if (K == 1) {
         const size_t fsm = ((size_t)c->lvl_max_rc[l] + mrb * mc) * sizeof(T);
         if (cnt <= kNumSMs)   // one CTA per SM: the chain keeps its sub-partition's FP64 unit to itself
@@ -1717,6 +1728,24 @@ kkt_status finish_ctx(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             cudaFuncSetAttribute(factor_fused_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb);
             cudaFuncSetAttribute(factor_fused_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb);
             cudaFuncSetAttribute(factor_fused_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fcb);
+            for (int q = 1; q <= 3; ++q) {   // launches of 1 CTA per SM (kOneCtaPerSmBytes), K = 2^q
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(kNumSMs << q), 1, 1);
+                cfg.blockDim = dim3(kFusedThreads, 1, 1);
+                cfg.dynamicSmemBytes = kOneCtaPerSmBytes;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 1u << q;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int nc = 0;
+                if (cudaOccupancyMaxActiveClusters(&nc, factor_fused_cluster_kernel<double>, &cfg) == cudaSuccess)
+                    c->fused_clusters[q] = nc;
+                else
+                    cudaGetLastError();   // unknown: the SM-count rule alone
+            }
         }
         cudaFuncSetAttribute(syrk_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);
         cudaFuncSetAttribute(syrk_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSyrkStageBytes);

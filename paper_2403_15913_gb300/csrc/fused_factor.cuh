@@ -1,6 +1,7 @@
 // Fused factorisation of a tree level whose supernodes have at most 32
-// columns and at most 128 rows below the diagonal block (the separators at
-// the top of the nested-dissection tree: one stage's compositions each).
+// columns and at most 128 rows below the diagonal block (in the tray column
+// every level above the subtree tasks: the wide levels of small
+// separators and the top levels, one stage's compositions each).
 //
 // One launch per level instead of three (diagonal block, rows below, Schur
 // update), and a pivot chain about half as long.  The numbers are those of

@@ -83,8 +83,10 @@ struct kkt_ctx {
     int* d_task_sn = nullptr;
     int n_norm = 0;               // supernodes normalised after the factorisation
     int* d_norm_list = nullptr;
-    // levels factorised by factor_fused_kernel (FP64 and FP32 panels), and
-    // the normalisation list that leaves their supernodes out
+    // levels factorised by the fused kernels (FP64 and FP32 panels; every
+    // level of supernodes with <= kFusedMaxC columns and <= kFusedMaxRb rows
+    // below, wide or split), and the normalisation list that leaves their
+    // supernodes out
     std::vector<char> lvl_fused;
     // co-resident clusters of factor_fused_cluster_kernel for K = 2, 4, 8
     // CTAs (index log2 K; 0 = not queried): a level takes K only if all its
@@ -666,7 +668,7 @@ kkt_status build_plan(kkt_ctx* c, const int* W_colptr, const int* W_rowind, cons
             fl_sum += f;
         }
         c->lvl_split[l] = cnt < kSplitLevel || fl_max > 2.0 * fl_sum / kNumSMs;
-        c->lvl_fused[l] = c->lvl_split[l] && c->lvl_max_c[l] <= kFusedMaxC && c->lvl_max_rb[l] <= kFusedMaxRb;
+        c->lvl_fused[l] = c->lvl_max_c[l] <= kFusedMaxC && c->lvl_max_rb[l] <= kFusedMaxRb;
         if (c->lvl_split[l]) {
             // SYRK tasks: chunks of the packed lower triangle of each
             // supernode, sized so the level gives about four CTAs per SM
@@ -1538,7 +1540,15 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
     for (int l = 0; l < c->nlev; ++l) {
         const int cnt = c->h_lvl_ptr[l + 1] - c->h_lvl_ptr[l];
         const int* lsn = c->d_lvl_sn + c->h_lvl_ptr[l];
+        if constexpr (kFusedType<T>) {
+            if (c->lvl_fused[l]) {
+                TRY(launch_fused_level<T>(c, l, cnt, lsn, Lx, fs, dinv, st));
+                continue;
+            }
+        }
         if (!c->lvl_split[l]) {
+            // (Levels the fused kernel does not take: double-float panels,
+            // or supernodes wider than 32 columns / 128 rows below.)
             // At 60 registers a thread, 256-thread CTAs fit four to an SM: a
             // level of 600-1200 narrow supernodes (c <= 32) takes two waves,
             // where 128-thread CTAs (same warps per SM, twice the supernodes
@@ -1548,12 +1558,6 @@ kkt_status enqueue_numeric_factor(kkt_ctx* c, T* Lx, T* dinv, double delta_x, cu
             factor_level_kernel<T><<<cnt, half ? kThreads / 2 : kThreads, (size_t)need * sizeof(T), st>>>(
                 c->plan, lsn, Lx, fs, need, dinv);
             continue;
-        }
-        if constexpr (kFusedType<T>) {
-            if (c->lvl_fused[l]) {
-                TRY(launch_fused_level<T>(c, l, cnt, lsn, Lx, fs, dinv, st));
-                continue;
-            }
         }
         const size_t dsm = (size_t)c->lvl_max_c[l] * c->lvl_max_c[l] * sizeof(T);
         // the small top levels: one cluster launch instead of three launches

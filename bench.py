@@ -53,6 +53,11 @@ PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 # in this file together with the SHA-256 of the kernel sources it measured;
 # when the sources differ the counters are stale and roofline.traffic is null
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "factor_dram_traffic.txt")
+# Supernode partition of every workload (the library's defaults; the oracle
+# baselines analyse with the same ordering options)
+PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=64)
+SUBTREE_COLS = 32
+
 TRAFFIC_SOURCES = ("kernels.cuh", "fused_factor.cuh", "kkt.cu", "fp64_lean.cuh", "sparse_dot.cuh")
 
 
@@ -274,8 +279,7 @@ def _oracle_ipm_worker(k, T, scheme, n_warm, n_timed, barrier, out_q):
     x0 = ipm_start(p)
     W = otray.hessian_lower_csc(p, x0, np.zeros(p.m))
     J = otray.jacobian_csr(p, x0)
-    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=64, relax_cols=32,
-                           relax_zeros=128, max_width=64)
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **PARTITION)
 
     def fresh():
         lin = oipm.KKTLinearSolver(scheme, p.n, p.m, None, None, sym=sym, gamma=1e4)
@@ -579,8 +583,7 @@ def oracle_kkt_sample(k, T_sample, scheme, sig, gamma, budget_s):
     pt = kkt_point(p, 0, sig)
     W = otray.hessian_lower_csc(p, pt.w, pt.lam)
     J = otray.jacobian_csr(p, pt.w)
-    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], leaf_size=64, relax_cols=32,
-                           relax_zeros=128, max_width=64)
+    sym = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **PARTITION)
     n_done, t = 0, 0.0
     while t < budget_s or n_done == 0:
         t0 = time.perf_counter()
@@ -626,9 +629,8 @@ def run_kkt(args, ws, rank, local):
     dy = torch.zeros(p.m, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
-                relax_zeros=128, max_width=64, solver=1 if args.solver == "bcr" else 0,
-                block=2 * args.k + 1)
+    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, subtree_cols=SUBTREE_COLS,
+                solver=1 if args.solver == "bcr" else 0, block=2 * args.k + 1, **PARTITION)
 
     def make(prec):
         t0 = time.perf_counter()
@@ -794,8 +796,7 @@ def run_batch(args, ws, rank, local):
     pats = [tm.pattern() for tm in models]
     pts = [kkt_point(p, args.seed + 17 * i + 100000 * rank, sig) for i, p in enumerate(params)]
     stream = torch.cuda.current_stream()
-    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, leaf_size=64, relax_cols=32,
-                relax_zeros=128, max_width=64)
+    opts = dict(scheme=args.scheme, gamma=args.gamma, max_cg=500, subtree_cols=SUBTREE_COLS, **PARTITION)
     prec = PREC[args.precision]
     tuned = None
     if args.autotune:

@@ -72,7 +72,7 @@ typedef struct {
     int scheme;          /* KKT_LIFTED or KKT_HYKKT                            */
     /* symbolic analysis (pinned nested dissection, Sec. V-B) */
     int leaf_size;       /* ND components this small are ordered by minimum
-                            degree (default 64)                               */
+                            degree (default 8)                                */
     int relax_cols;      /* relaxed amalgamation: max merged width (32);
                             0 keeps fundamental supernodes                    */
     int relax_zeros;     /* max explicit zeros in a merged panel (128)        */
@@ -91,7 +91,7 @@ typedef struct {
                             only)                                             */
     int subtree_cols;    /* subtrees of the supernodal tree with at most this
                             many columns (and at most 1024) are factorised
-                            and solved by one CTA each (48); 0 disables       */
+                            and solved by one CTA each (32); 0 disables       */
     int precision;       /* 0: factor in FP64 (default).  1: factor in FP32,
                             2: in double-float (pairs of FP32 numbers, ~48
                             significand bits, on the FP32 pipe), and refine

@@ -1598,7 +1598,7 @@ extern "C" {
 void kkt_default_options(kkt_options* o) {
     if (!o) return;
     o->scheme = KKT_LIFTED;
-    o->leaf_size = 64;
+    o->leaf_size = 8;
     o->relax_cols = 32;
     o->relax_zeros = 128;
     o->max_width = 64;
@@ -1609,7 +1609,7 @@ void kkt_default_options(kkt_options* o) {
     o->max_refine = 20;
     o->max_cg = 200;
     o->target_relaxed = 0;
-    o->subtree_cols = 48;
+    o->subtree_cols = 32;
     o->precision = 0;
     o->solver = 0;
     o->block = 0;

@@ -219,14 +219,18 @@ def test_device_analysis_without_a_gpu_returns_a_status(nat):
     assert e.value.status == nat.KKT_ERR_CUDA
 
 
-def _bench_column_parity(nat, T):
+# the library's default partition (kkt_default_options), written out for the oracle
+DEFAULT_PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=64)
+
+
+def _bench_column_parity(nat, T, opts=None):
     from paper_2403_15913_gb300 import KKTSolver
     p = TrayParams(k=32, T=T)
     pt = kkt_point(p, 0)
     W = tray.hessian_lower_csc(p, pt.w, pt.lam)
     J = tray.jacobian_csr(p, pt.w)
-    o = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **OPTS[0])
-    s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], host_only=True, **OPTS[0])
+    o = symbolic.analyse(p.n, W[0], W[1], J[0], J[1], **(opts or DEFAULT_PARTITION))
+    s = KKTSolver(p.n, p.m, W[0], W[1], J[0], J[1], host_only=True, **(opts or {}))
     g = s.symbolic()
     assert np.array_equal(g["perm"], o.perm)
     assert np.array_equal(g["parent"], o.parent)
@@ -238,16 +242,19 @@ def _bench_column_parity(nat, T):
     s.close()
 
 
-def test_symbolic_bit_exact_benchmark_column(nat):
+@pytest.mark.parametrize("opts", [None, OPTS[0]], ids=["defaults", "leaf64"])
+def test_symbolic_bit_exact_benchmark_column(nat, opts):
     """The benchmark's column (32 trays, T = 5000: n = 325,065) with the
-    library's default options: the threaded nested dissection and the
-    threaded adjacency build give the oracle's analysis bit for bit."""
-    _bench_column_parity(nat, 5000)
+    library's default options (no options passed; the oracle gets them
+    written out) and with ND leaves of 64: the threaded nested dissection
+    and the threaded adjacency build give the oracle's analysis bit for
+    bit."""
+    _bench_column_parity(nat, 5000, opts)
 
 
 @pytest.mark.slow
 def test_symbolic_bit_exact_largest_column(nat):
     """The mixed-precision workload's column (32 trays, T = 20000: n =
-    1,300,065), bit for bit against the oracle (about two minutes of
-    oracle time)."""
+    1,300,065) with the default options, bit for bit against the oracle
+    (about two minutes of oracle time)."""
     _bench_column_parity(nat, 20000)

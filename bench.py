@@ -55,7 +55,7 @@ PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "factor_dram_traffic.txt")
 # Supernode partition of every workload (the library's defaults; the oracle
 # baselines analyse with the same ordering options)
-PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=64)
+PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=32)
 SUBTREE_COLS = 32
 
 TRAFFIC_SOURCES = ("kernels.cuh", "fused_factor.cuh", "kkt.cu", "fp64_lean.cuh", "sparse_dot.cuh")

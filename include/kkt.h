@@ -76,7 +76,7 @@ typedef struct {
     int relax_cols;      /* relaxed amalgamation: max merged width (32);
                             0 keeps fundamental supernodes                    */
     int relax_zeros;     /* max explicit zeros in a merged panel (128)        */
-    int max_width;       /* supernodes wider than this are cut (64);
+    int max_width;       /* supernodes wider than this are cut (32);
                             0 or anything above 64 means 64                   */
     /* numerics */
     double delta;        /* Lifted-KKT: D = 1/delta when factor gets D = NULL

@@ -1601,7 +1601,7 @@ void kkt_default_options(kkt_options* o) {
     o->leaf_size = 8;
     o->relax_cols = 32;
     o->relax_zeros = 128;
-    o->max_width = 64;
+    o->max_width = 32;
     o->delta = 1e-8;
     o->gamma = 1e4;
     o->tol_refine = 1e-10;

@@ -220,7 +220,7 @@ def test_device_analysis_without_a_gpu_returns_a_status(nat):
 
 
 # the library's default partition (kkt_default_options), written out for the oracle
-DEFAULT_PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=64)
+DEFAULT_PARTITION = dict(leaf_size=8, relax_cols=32, relax_zeros=128, max_width=32)
 
 
 def _bench_column_parity(nat, T, opts=None):

@@ -187,18 +187,35 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
+        self.skip = 0
         self.path = os.path.join(tempfile.gettempdir(), f"kkt_bench_clocks_{os.getpid()}.csv")
 
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return [ln for ln in f.read().split("\n") if ln.count(",") >= 8]
+        except OSError:
+            return []
+
     def start(self):
+        """Start sampling every 50 ms and return once the first sample is
+        written (at most 3 s), so that the samples taken after start()
+        returns fall inside the caller's timed region; those are the ones
+        stop() reports."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and not self._lines():
+            time.sleep(0.01)
+        self.skip = len(self._lines())
 
     def stop(self):
         if self.proc is None:
@@ -211,7 +228,9 @@ class ClockSampler:
         self.f.close()
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = self._lines()
+        inside = lines[self.skip:] or lines   # a region shorter than one interval: the nearest samples
+        for line in inside:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue

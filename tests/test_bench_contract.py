@@ -41,3 +41,19 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_benchmark_partition_is_the_library_default():
+    """The benchmark's supernode partition (used by its GPU workloads and
+    by the oracle baselines' analysis) is the library's default one, so the
+    IPM workload (library defaults) and the KKT / batch workloads (explicit
+    options) run the same partition."""
+    sys.path.insert(0, ROOT)
+    import ctypes
+    import bench
+    from paper_2403_15913_gb300 import _native as nat
+    o = nat.Options()
+    nat.lib().kkt_default_options(ctypes.byref(o))
+    for key, val in bench.PARTITION.items():
+        assert getattr(o, key) == val, key
+    assert o.subtree_cols == bench.SUBTREE_COLS
